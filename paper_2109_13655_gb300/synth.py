@@ -1,0 +1,206 @@
+"""Seeded synthetic inputs for the interior-SVD workloads.
+
+This module only builds inputs: sparse matrices, seed blocks and intervals.
+It holds none of the contour-integral method's arithmetic. The CUDA path and
+the CPU oracle both draw their inputs from here, so that they see the same
+numbers.
+
+Workload shapes follow the paper's experiments (Sec. 4) and the configured
+synthetic stand-ins:
+
+* ``random_sparse``     -- m x n CSR, k distinct uniform-random columns per
+                           row, N(0,1) values (the 2000 x 1000 case).
+* ``block_permuted``    -- dense blocks on a block diagonal with random row and
+                           column permutations; its spectrum is the union of
+                           the blocks' spectra, so it is known exactly.
+* ``model_problem``     -- the Experiment II model problems
+                           A = U diag(sigma) V^T, m = 1000, n = 200 (Sec. 4.2).
+* ``gaussian_block``    -- the real Gaussian input block V_in (n x L).
+* ``window_interval``   -- an interval [a, b] whose endpoints sit at gap
+                           midpoints of a known descending spectrum.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+
+@dataclass
+class CSR:
+    """A real sparse matrix in compressed-sparse-row form.
+
+    rowptr: int64[m+1], colidx: int32[nnz] (strictly increasing per row),
+    vals: float64[nnz].
+    """
+
+    m: int
+    n: int
+    rowptr: np.ndarray
+    colidx: np.ndarray
+    vals: np.ndarray
+
+    @property
+    def nnz(self) -> int:
+        return int(self.rowptr[-1])
+
+    def to_dense(self) -> np.ndarray:
+        d = np.zeros((self.m, self.n))
+        rows = np.repeat(np.arange(self.m), np.diff(self.rowptr))
+        d[rows, self.colidx] = self.vals
+        return d
+
+
+def csr_from_coo(m: int, n: int, rows, cols, vals) -> CSR:
+    """Sort COO triplets by (row, col) and compress. Duplicates are rejected."""
+    rows = np.asarray(rows, dtype=np.int64)
+    cols = np.asarray(cols, dtype=np.int64)
+    vals = np.asarray(vals, dtype=np.float64)
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    if rows.size > 1:
+        dup = (rows[1:] == rows[:-1]) & (cols[1:] == cols[:-1])
+        if dup.any():
+            raise ValueError("duplicate (row, col) entries")
+    rowptr = np.zeros(m + 1, dtype=np.int64)
+    np.add.at(rowptr, rows + 1, 1)
+    rowptr = np.cumsum(rowptr)
+    return CSR(m, n, rowptr, cols.astype(np.int32), vals)
+
+
+def csr_from_dense(d: np.ndarray) -> CSR:
+    """Every entry of a dense matrix stored explicitly (zeros included)."""
+    m, n = d.shape
+    rowptr = np.arange(0, m * n + 1, n, dtype=np.int64)
+    colidx = np.tile(np.arange(n, dtype=np.int32), m)
+    return CSR(m, n, rowptr, colidx, np.ascontiguousarray(d, dtype=np.float64).ravel())
+
+
+def transpose(A: CSR) -> CSR:
+    rows = np.repeat(np.arange(A.m, dtype=np.int64), np.diff(A.rowptr))
+    return csr_from_coo(A.n, A.m, A.colidx, rows, A.vals)
+
+
+def _distinct_columns(rng: np.random.Generator, m: int, n: int, k: int) -> np.ndarray:
+    """k distinct columns per row, uniform without replacement, sorted."""
+    if k > n:
+        raise ValueError("k > n")
+    cols = np.sort(rng.integers(0, n, size=(m, k)), axis=1)
+    while True:
+        bad = np.nonzero((np.diff(cols, axis=1) == 0).any(axis=1))[0]
+        if bad.size == 0:
+            return cols
+        cols[bad] = np.sort(rng.integers(0, n, size=(bad.size, k)), axis=1)
+
+
+def random_sparse(m: int = 2000, n: int = 1000, k: int = 8, seed: int = 0) -> CSR:
+    """m x n CSR with k distinct uniform-random columns per row, N(0,1) values."""
+    rng = np.random.default_rng(seed)
+    cols = _distinct_columns(rng, m, n, k)
+    vals = rng.standard_normal(m * k)
+    rowptr = np.arange(0, m * k + 1, k, dtype=np.int64)
+    return CSR(m, n, rowptr, cols.ravel().astype(np.int32), vals)
+
+
+def bf16_round(x: np.ndarray) -> np.ndarray:
+    """Round float64 values to the nearest bfloat16-representable value (ties to even)."""
+    f = np.asarray(x, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+@dataclass
+class BlockPermuted:
+    """A block-diagonal matrix hidden by random row/column permutations.
+
+    Block b occupies rows row_perm[b*bm:(b+1)*bm] and columns
+    col_perm[b*bn:(b+1)*bn]; ``blocks[b]`` holds its dense values.
+    """
+
+    A: CSR
+    blocks: np.ndarray      # (nb, bm, bn)
+    row_perm: np.ndarray    # (nb*bm,)
+    col_perm: np.ndarray    # (nb*bn,)
+
+    def block_sigmas(self) -> np.ndarray:
+        """Singular values of every block, shape (nb, min(bm, bn)), descending.
+
+        The matrix's spectrum is the union of these values (the permutations
+        are orthogonal), which is what makes the construction's spectrum known.
+        """
+        return np.linalg.svd(self.blocks, compute_uv=False)
+
+    def sigmas_desc(self) -> np.ndarray:
+        return np.sort(self.block_sigmas().ravel())[::-1]
+
+
+def block_permuted(nb: int, bm: int, bn: int, seed: int, dist: str = "normal") -> BlockPermuted:
+    """nb dense bm x bn blocks, permuted. dist: 'normal' N(0,1) or 'uniform_bf16'
+    U(-1,1) rounded to bf16-representable values."""
+    rng = np.random.default_rng(seed)
+    if dist == "normal":
+        blocks = rng.standard_normal((nb, bm, bn))
+    elif dist == "uniform_bf16":
+        blocks = bf16_round(rng.uniform(-1.0, 1.0, size=(nb, bm, bn)))
+    else:
+        raise ValueError(dist)
+    row_perm = rng.permutation(nb * bm)
+    col_perm = rng.permutation(nb * bn)
+    bi, ii, jj = np.meshgrid(np.arange(nb), np.arange(bm), np.arange(bn), indexing="ij")
+    rows = row_perm[bi * bm + ii].ravel()
+    cols = col_perm[bi * bn + jj].ravel()
+    A = csr_from_coo(nb * bm, nb * bn, rows, cols, blocks.ravel())
+    return BlockPermuted(A, blocks, row_perm, col_perm)
+
+
+def _haar_orthonormal(rng: np.random.Generator, rows: int, cols: int) -> np.ndarray:
+    q, r = np.linalg.qr(rng.standard_normal((rows, cols)))
+    return q * np.sign(np.diag(r))
+
+
+def model_problem(which: int, m: int = 1000, n: int = 200, seed: int = 7):
+    """Experiment II (Sec. 4.2): A = U diag(sigma) V^T with random orthogonal U, V.
+
+    which=1: sigma = 0.005, 0.015, ..., 1.995 (uniform, Eq. model1).
+    which=2: sigma = 10^-10.0, 10^-9.95, ..., 10^-0.05 (log-uniform, Eq. model2).
+    Returns (dense A, sigma ascending).
+    """
+    rng = np.random.default_rng(seed)
+    if which == 1:
+        sig = 0.005 + 0.01 * np.arange(n)
+    elif which == 2:
+        sig = 10.0 ** (-10.0 + 0.05 * np.arange(n))
+    else:
+        raise ValueError(which)
+    U = _haar_orthonormal(rng, m, n)
+    V = _haar_orthonormal(rng, n, n)
+    return (U * sig) @ V.T, sig
+
+
+def gaussian_block(n: int, L: int, seed: int) -> np.ndarray:
+    """Real N(0,1) input block V_in, n x L, row-major float64."""
+    return np.random.default_rng(seed).standard_normal((n, L))
+
+
+def window_interval(sig_desc: np.ndarray, first: int, count: int,
+                    min_rel_gap: float = 0.0, max_shift: int = 0):
+    """Interval holding sig_desc[first:first+count] (0-based, descending order).
+
+    a and b are the midpoints of the gaps just outside the window. With
+    min_rel_gap > 0 the window start moves by at most max_shift positions
+    (nearest first) until both bounding gaps are >= min_rel_gap * sigma.
+    Returns (a, b, first).
+    """
+    s = np.asarray(sig_desc, dtype=np.float64)
+    for d in sorted(range(-max_shift, max_shift + 1), key=lambda x: (abs(x), x)):
+        f = first + d
+        if f < 1 or f + count >= s.size:
+            continue
+        hi_gap = s[f - 1] - s[f]
+        lo_gap = s[f + count - 1] - s[f + count]
+        if hi_gap >= min_rel_gap * s[f - 1] and lo_gap >= min_rel_gap * s[f + count - 1]:
+            b = 0.5 * (s[f - 1] + s[f])
+            a = 0.5 * (s[f + count - 1] + s[f + count])
+            return float(a), float(b), f
+    raise ValueError("no window with the requested gaps")

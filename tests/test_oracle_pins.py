@@ -1,0 +1,331 @@
+"""Pins for the CPU oracle: each check compares it with something other than itself.
+
+* the quadrature exactness condition (Eq. cond, Sec. 3.2),
+* the conjugate-symmetry halving against the full N-point sum (Sec. 3.1),
+* Prop. 1 (S_k = (A^T A)^k S_0, linear variant),
+* closed-form moments from a dense SVD (first equality of Prop. 1; Sec. 3.3 for NT),
+* the contour-integral limit of Thm. 1 (spectral projector) for both variants,
+* the Exp I filter statements (tests/golden/exp1_filter.txt),
+* triplets against numpy's dense SVD, and the Exp II model problems (Sec. 4.2),
+* the spurious index tau on the 2000 x 1000 workload (Sec. 3.4.2).
+
+The mutation tests at the end plant plausible mistakes in the oracle and
+check that at least one of these pins fails.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle import cmsvd_oracle as O
+from paper_2109_13655_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------------------- helpers
+def _svd_matrix(sig, m, seed):
+    """Dense m x n matrix with prescribed singular values and Haar singular vectors."""
+    rng = np.random.default_rng(seed)
+    n = len(sig)
+    U, _ = np.linalg.qr(rng.standard_normal((m, n)))
+    V, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    return (U * sig) @ V.T
+
+
+def exactness_error(N, a=0.8, b=1.2, variant="linear"):
+    """max_k<=N-2 |sum_{j=1}^N omega_j m_j^k| / sum|omega_j| and the k=N-1 value."""
+    q = O.quadrature(a, b, N, variant, full=True)
+    w = q.weight if variant == "linear" else q.weight / np.exp(q.node)  # omega_j
+    scale = np.sum(np.abs(w))
+    errs = [abs(np.sum(w * q.scaled ** k)) / scale for k in range(N - 1)]
+    last = abs(np.sum(w * q.scaled ** (N - 1))) / scale
+    return max(errs), last
+
+
+def halving_error(variant="linear"):
+    """2 Re sum_{j<=N/2} vs the full sum over j = 1..N (both through the direct solves)."""
+    A = synth.random_sparse(40, 20, 5, seed=11)
+    V = synth.gaussian_block(20, 3, 12)
+    s = np.linalg.svd(A.to_dense(), compute_uv=False)
+    a, b = 0.5 * (s[5] + s[6]), 0.5 * (s[1] + s[2])
+    N, M = 16, 3
+    solver = O.ShiftedSolver(A)
+    half = O.moments(solver, O.quadrature(a, b, N, variant), V, M)
+    qf = O.quadrature(a, b, N, variant, full=True)
+    full = []
+    for k in range(M):
+        acc = np.zeros(V.shape, dtype=complex)
+        for j in range(N):
+            acc += qf.weight[j] * qf.scaled[j] ** k * solver.solve(qf.shift[j], V)
+        full.append(acc)
+    full = np.concatenate(full, axis=1)
+    return np.max(np.abs(half - full)) / np.max(np.abs(full)), np.max(np.abs(full.imag)) / np.max(np.abs(full))
+
+
+def closed_form_error(variant="linear", ell=1):
+    """S^ from direct solves vs sum_i c_k(sigma_i) f(sigma_i)^(ell-1) v_i v_i^T V_in from numpy's SVD."""
+    A = synth.random_sparse(60, 30, 6, seed=21)
+    Ad = A.to_dense()
+    _, s, Vt = np.linalg.svd(Ad, full_matrices=False)
+    a, b = 0.5 * (s[9] + s[10]), 0.5 * (s[3] + s[4])
+    N, M, L = 16, 4, 4
+    Vin = synth.gaussian_block(30, L, 22)
+    q = O.quadrature(a, b, N, variant)
+    S = O.moments(O.ShiftedSolver(A), q, Vin, M, ell=ell)
+    C = Vt @ Vin                    # v_i^T V_in
+    ref = []
+    for k in range(M):
+        c = O.moment_filter(s, q, k) * O.filter_value(s, q) ** (ell - 1)
+        ref.append(Vt.T @ (c[:, None] * C))
+    ref = np.concatenate(ref, axis=1)
+    return np.max(np.abs(S - ref)) / np.max(np.abs(ref))
+
+
+def prop1_error(scaled=True):
+    """Prop. 1: S_k = (A^T A)^k S_0 (literal z^k) or ((A^T A - gamma)/rho)^k S_0 (scaled)."""
+    A = synth.random_sparse(50, 25, 6, seed=31)
+    H = A.to_dense().T @ A.to_dense()
+    s = np.sqrt(np.linalg.eigvalsh(H))[::-1]
+    a, b = 0.5 * (s[7] + s[8]), 0.5 * (s[2] + s[3])
+    N, M, L = 8, 7, 3                  # k up to N-1
+    Vin = synth.gaussian_block(25, L, 32)
+    q = O.quadrature(a, b, N)
+    S = O.moments(O.ShiftedSolver(A), q, Vin, M, scaled=scaled)
+    T = (H - q.gamma * np.eye(25)) / q.rho if scaled else H
+    S0 = S[:, :L]
+    err = 0.0
+    for k in range(1, M):
+        pred = np.linalg.matrix_power(T, k) @ S0
+        err = max(err, np.max(np.abs(S[:, k * L:(k + 1) * L] - pred)) / np.max(np.abs(pred)))
+    return err
+
+
+def contour_limit_error(variant="linear"):
+    """Thm. 1 / Sec. 3.3: as N grows, S_k -> sum_{sigma_i in [a,b]} x_i^k v_i v_i^T V_in,
+    x_i = (sigma_i^2 - gamma)/rho (linear) or (log sigma_i^2 - gamma)/rho (NT)."""
+    sig = np.array([3.0, 2.2, 1.6, 1.5, 1.4, 1.0, 0.6, 0.3, 0.1, 0.05])
+    Ad = _svd_matrix(sig, 16, 41)
+    _, s, Vt = np.linalg.svd(Ad, full_matrices=False)
+    a, b = 1.2, 1.9                     # holds 1.6, 1.5, 1.4
+    N, M, L = 512, 3, 2
+    Vin = synth.gaussian_block(10, L, 42)
+    q = O.quadrature(a, b, N, variant, alpha=1.0)
+    S = O.moments(O.ShiftedSolver(Ad), q, Vin, M)
+    inside = (s >= a) & (s <= b)
+    x = (s ** 2 - q.gamma) / q.rho if variant == "linear" else (np.log(s ** 2) - q.gamma) / q.rho
+    ref = np.concatenate([Vt[inside].T @ ((x[inside] ** k)[:, None] * (Vt[inside] @ Vin)) for k in range(M)], axis=1)
+    return np.max(np.abs(S - ref)) / np.max(np.abs(ref))
+
+
+def dense_triplet_errors(variant="linear", ell=1, m=120, n=60, first=20, count=6, seed=51):
+    """Triplets of the oracle vs numpy's dense SVD on a small sparse matrix."""
+    A = synth.random_sparse(m, n, 6, seed=seed)
+    Ad = A.to_dense()
+    U, s, Vt = np.linalg.svd(Ad, full_matrices=False)
+    a, b, _ = synth.window_interval(s, first, count)
+    Vin = synth.gaussian_block(n, 8, seed + 1)
+    r = O.solve_interval(A, a, b, 32, 8, 4, Vin, ell=ell, variant=variant, norm_A=s[0])
+    truth = s[first:first + count][::-1]
+    if r.sigma.size != count:
+        return r.sigma.size, np.inf, np.inf, np.inf
+    sig_err = np.max(np.abs(r.sigma - truth) / truth)
+    vt = Vt[first:first + count][::-1]
+    cosv = np.abs(np.sum(vt.T * r.V, axis=0))
+    return r.sigma.size, sig_err, float(np.max(1 - cosv)), float(np.max(r.res_u))
+
+
+# ----------------------------------------------------------------------------- pins
+@pytest.mark.parametrize("N", [8, 16, 32, 64])
+def test_quadrature_exactness_condition(N):
+    """Eq. cond: sum_j omega_j z_j^k = 0 for k = 0..N-2 (checked on the scaled nodes,
+    which span the same polynomials). At k = N-1 the trapezoidal sum picks up the
+    e^{+-iN theta} Fourier terms: writing cos + i alpha sin = c1 e^{i theta} + c2 e^{-i theta}
+    with c1 = (1+alpha)/2, c2 = (1-alpha)/2 and sum_j e^{iN theta_j} = -N, it equals
+    -rho (c1^N - c2^N), which is nonzero."""
+    err, last = exactness_error(N)
+    assert err < 1e-14
+    q = O.quadrature(0.8, 1.2, N, full=True)
+    c1, c2 = (1 + q.alpha) / 2, (1 - q.alpha) / 2
+    expect = q.rho * (c1 ** N - c2 ** N) / np.sum(np.abs(q.weight))
+    assert abs(last - expect) <= 1e-14 + 1e-9 * expect
+    if N <= 32:
+        assert expect > 1e-12
+
+
+def test_quadrature_literal_exactness():
+    """Eq. cond in the literal form sum_j omega_j z_j^k for moderate |z|."""
+    N = 16
+    q = O.quadrature(0.8, 1.2, N, "linear", full=True)
+    for k in range(N - 1):
+        terms = q.weight * q.node ** k
+        assert abs(np.sum(terms)) <= 1e-13 * np.sum(np.abs(terms))
+
+
+def test_quadrature_conjugate_pairs():
+    """(z_j, omega_j) and (z_{N+1-j}, omega_{N+1-j}) are complex conjugates (Sec. 3.1, pairing reading)."""
+    q = O.quadrature(1.0, 2.0, 16, full=True)
+    assert np.allclose(q.node[::-1], np.conj(q.node), rtol=0, atol=1e-15)
+    assert np.allclose(q.weight[::-1], np.conj(q.weight), rtol=0, atol=1e-15)
+    assert np.all(q.node[:8].imag > 0)
+
+
+@pytest.mark.parametrize("variant", ["linear", "nt"])
+def test_halving_matches_full_sum(variant):
+    err, imag = halving_error(variant)
+    assert err < 1e-12
+    assert imag < 1e-12          # the full sum is real (Sec. 3.1)
+
+
+def test_prop1_linear_scaled():
+    assert prop1_error(scaled=True) < 1e-9
+
+
+def test_prop1_linear_literal():
+    assert prop1_error(scaled=False) < 1e-8
+
+
+@pytest.mark.parametrize("variant", ["linear", "nt"])
+@pytest.mark.parametrize("ell", [1, 2])
+def test_closed_form_moments(variant, ell):
+    assert closed_form_error(variant, ell) < 1e-11
+
+
+@pytest.mark.parametrize("variant", ["linear", "nt"])
+def test_contour_integral_limit(variant):
+    assert contour_limit_error(variant) < 1e-10
+
+
+def test_filter_values_exp1():
+    rows = []
+    with open(os.path.join(GOLDEN, "exp1_filter.txt")) as fh:
+        for line in fh:
+            line = line.split("#")[0].split()
+            if line:
+                rows.append(line)
+    assert len(rows) >= 10
+    for a, b, variant, sig, lo, hi in rows:
+        q = O.quadrature(float(a), float(b), 32, variant)
+        val = abs(float(O.filter_value(float(sig), q)))
+        assert float(lo) <= val <= float(hi), (a, b, variant, sig, val)
+
+
+@pytest.mark.parametrize("variant,ell", [("linear", 1), ("nt", 1), ("linear", 2)])
+def test_triplets_match_dense_svd(variant, ell):
+    count, sig_err, vec_err, res = dense_triplet_errors(variant, ell)
+    assert count == 6
+    assert sig_err < 1e-12
+    assert vec_err < 1e-10
+    assert res < 1e-10
+
+
+def test_exterior_interval():
+    A = synth.random_sparse(100, 50, 6, seed=61)
+    s = np.linalg.svd(A.to_dense(), compute_uv=False)
+    a, b = 0.5 * (s[7] + s[8]), 1.01 * s[0]
+    Vin = synth.gaussian_block(50, 8, 62)
+    r = O.solve_interval(A, a, b, 32, 8, 4, Vin, norm_A=s[0])
+    assert r.sigma.size == 8
+    assert np.max(np.abs(r.sigma - s[:8][::-1]) / s[:8][::-1]) < 1e-12
+
+
+def test_two_sided_identity():
+    """A v = sigma u holds by construction of the two-sided projection (Sec. 3.4.1)."""
+    A = synth.random_sparse(120, 60, 6, seed=51)
+    s = np.linalg.svd(A.to_dense(), compute_uv=False)
+    a, b, _ = synth.window_interval(s, 20, 6)
+    r = O.solve_interval(A, a, b, 32, 8, 4, synth.gaussian_block(60, 8, 52), norm_A=s[0])
+    assert np.max(r.res_v) < 1e-14
+    # the returned bases are orthonormal
+    assert np.max(np.abs(r.U.T @ r.U - np.eye(6))) < 1e-12
+    assert np.max(np.abs(r.V.T @ r.V - np.eye(6))) < 1e-12
+
+
+def test_model_problems_exp2():
+    """Sec. 4.2: 40 triplets each; model 1 accurate for both variants; on model 2
+    the NT variant is accurate and the linear one is not."""
+    Vin = synth.gaussian_block(200, 20, 3)
+    A1, s1 = synth.model_problem(1)
+    truth1 = s1[(s1 >= 0.8) & (s1 <= 1.2)]
+    assert truth1.size == 40
+    for variant in ("linear", "nt"):
+        r = O.solve_interval(A1, 0.8, 1.2, 32, 20, 4, Vin, variant=variant, norm_A=s1.max())
+        assert r.sigma.size == 40
+        assert np.max(np.abs(r.sigma - truth1) / truth1) < 1e-13
+    # model 2, interval endpoints moved to gap midpoints (endpoint reading): 40 values
+    a, b = 10 ** -3.025, 10 ** -1.025
+    A2, s2 = synth.model_problem(2)
+    truth2 = s2[(s2 >= a) & (s2 <= b)]
+    assert truth2.size == 40
+    rn = O.solve_interval(A2, a, b, 32, 20, 4, Vin, variant="nt", norm_A=s2.max())
+    assert rn.sigma.size == 40
+    assert np.max(np.abs(rn.sigma - truth2) / truth2) < 1e-13
+    rl = O.solve_interval(A2, a, b, 32, 20, 4, Vin, variant="linear", norm_A=s2.max())
+    assert rl.sigma.size < 40
+
+
+def test_c1_tau_detects_spurious():
+    """2000 x 1000, 8 nnz/row, sigma ranked 400-419: 20 found; one Ritz value in
+    [a, b] is spurious (tiny tau, large residual) and tau removes it (Sec. 3.4.2)."""
+    A = synth.random_sparse(2000, 1000, 8, seed=0)
+    s = np.linalg.svd(A.to_dense(), compute_uv=False)
+    a, b, _ = synth.window_interval(s, 400, 20)
+    Vin = synth.gaussian_block(1000, 16, 1)
+    r = O.solve_interval(A, a, b, 16, 16, 4, Vin, norm_A=s[0])
+    truth = s[400:420][::-1]
+    assert r.sigma.size == 20
+    assert np.max(np.abs(r.sigma - truth) / truth) < 1e-13
+    inside = (r.all_phi >= a) & (r.all_phi <= b)
+    spurious = inside & (r.all_tau < 1e-8)
+    assert spurious.sum() >= 1
+    assert np.all(r.all_res[spurious] > 1e-6)
+    assert np.all(r.all_tau[inside & ~spurious] > 1e-3)
+
+
+# ----------------------------------------------------------------------------- mutations
+def _mutant_quadrature(kind):
+    orig = O.quadrature
+
+    def q(a, b, N, variant="linear", alpha=0.1, full=False):
+        r = orig(a, b, N, variant, alpha, full)
+        if kind == "no_alpha_in_weight":
+            r.weight = r.weight / (alpha * np.cos(r.theta) + 1j * np.sin(r.theta)) * (np.cos(r.theta) + 1j * np.sin(r.theta))
+        elif kind == "psi_without_exp" and variant == "nt":
+            r.weight = r.weight / np.exp(r.node)
+        elif kind == "theta_without_half":
+            th = r.theta + np.pi / N
+            r.node = r.gamma + r.rho * (np.cos(th) + 1j * alpha * np.sin(th))
+            r.shift = r.node if variant == "linear" else np.exp(r.node)
+        return r
+    return q
+
+
+@pytest.mark.parametrize("kind,check", [
+    ("no_alpha_in_weight", lambda: exactness_error(16)[0] > 1e-6),
+    ("psi_without_exp", lambda: contour_limit_error("nt") > 1e-3),
+    ("theta_without_half", lambda: closed_form_error("linear") > 1e-6 or halving_error()[1] > 1e-6),
+])
+def test_mutation_quadrature_caught(monkeypatch, kind, check):
+    monkeypatch.setattr(O, "quadrature", _mutant_quadrature(kind))
+    assert check()
+
+
+def test_mutation_shift_sign_caught(monkeypatch):
+    orig = O.ShiftedSolver.solve
+    monkeypatch.setattr(O.ShiftedSolver, "solve", lambda self, s, X: -orig(self, s, X))
+    assert closed_form_error("linear") > 1.0
+
+
+def test_mutation_dropped_factor_two_caught(monkeypatch):
+    orig = O.moments
+
+    def half(solver, q, V, M, ell=1, scaled=True, extra=0):
+        return 0.5 * orig(solver, q, V, M, ell, scaled, extra)
+    monkeypatch.setattr(O, "moments", half)
+    assert closed_form_error("linear") > 0.1
+
+
+def test_mutation_moment_index_caught(monkeypatch):
+    """Using the literal node instead of the scaled one in one factor breaks Prop. 1 (scaled form)."""
+    monkeypatch.setattr(O, "moment_factor", lambda q, k, scaled=True: q.node ** k)
+    assert prop1_error(scaled=True) > 1e-3
