@@ -1,0 +1,204 @@
+/*
+ * cmsvd -- complex moment-based interior SVD on one GPU (C ABI).
+ *
+ * Computes the singular triplets (sigma_i, u_i, v_i) of a real sparse m x n
+ * matrix A whose singular values lie in [a, b] (problem statement, Sec. 1,
+ * Eq. psvd), with the block SS-SVD method (Alg. 1) or its variant with the
+ * nonlinear transformation z = exp(t) (Alg. 2).
+ *
+ * Conventions for every call:
+ *   - Every call returns an int status (cmsvd_status); 0 is success. No C++
+ *     exception crosses this boundary. cmsvd_last_error() gives a message.
+ *   - "device" pointers are CUDA device addresses on the context's device;
+ *     "host" pointers are ordinary host memory. Calls marked "any" accept
+ *     either (the copy direction is inferred by CUDA unified addressing).
+ *   - Dense blocks are row-major with the leading dimension equal to the
+ *     number of columns unless stated otherwise. Triplet outputs are
+ *     column-major (one contiguous vector per triplet).
+ *   - All work of one context is ordered on that context's stream. Calls that
+ *     return host-visible values synchronize that stream before returning.
+ *   - The library owns the objects it creates (context, matrix, result) until
+ *     the matching destroy call. It never frees caller memory.
+ */
+#ifndef CMSVD_H
+#define CMSVD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum cmsvd_status {
+    CMSVD_OK = 0,
+    CMSVD_INVALID_ARG = 1,          /* a parameter is out of range (message says which) */
+    CMSVD_INVALID_MATRIX = 2,       /* CSR structure or values rejected by validation */
+    CMSVD_OUT_OF_MEMORY = 3,        /* a library allocation failed */
+    CMSVD_WORKSPACE_TOO_SMALL = 4,  /* ws_bytes below cmsvd_workspace_size() */
+    CMSVD_NOT_CONVERGED = 5,        /* a shifted solve hit max_iter; the result is still returned */
+    CMSVD_BREAKDOWN = 6,            /* NaN/Inf in a recurrence or a non-positive Cholesky pivot */
+    CMSVD_SUBSPACE_SATURATED = 7,   /* warning: numerical rank of S^ equals L*M (Thm. 1: t may exceed L*M) */
+    CMSVD_CUDA_ERROR = 8,           /* a CUDA runtime call failed */
+    CMSVD_NOT_SUPPORTED = 9         /* valid request outside what this build implements */
+} cmsvd_status;
+
+typedef enum cmsvd_variant {
+    CMSVD_LINEAR = 0,   /* Alg. 1: shifts z_j on the ellipse around [a^2, b^2] */
+    CMSVD_NT = 1        /* Alg. 2: shifts exp(t_j), t_j on the ellipse around [2 ln a, 2 ln b]; needs a > 0 */
+} cmsvd_variant;
+
+typedef enum cmsvd_solver {
+    CMSVD_SOLVER_AUTO = 0,    /* DIRECT when every connected component of A^T A is small, else KRYLOV */
+    CMSVD_SOLVER_KRYLOV = 1,  /* shifted COCG in two-pass Lanczos form, all shifts share one Krylov space */
+    CMSVD_SOLVER_DIRECT = 2   /* exact complex LDL^T on each connected component (the paper's direct solve) */
+} cmsvd_solver;
+
+typedef enum cmsvd_precision {
+    CMSVD_FP64 = 0,       /* every step in FP64 */
+    CMSVD_MIXED = 1       /* reserved for the reduced-precision Krylov path */
+} cmsvd_precision;
+
+/* Method parameters. Names follow Alg. 1 / Alg. 2 and Sec. 4. */
+typedef struct cmsvd_params {
+    int32_t N;            /* quadrature points, even, 2..128 (N/2 systems are solved, Sec. 3.1) */
+    int32_t L;            /* columns of V_in, 1..128 */
+    int32_t M;            /* moments, 1 <= M <= N-1 (Prop. 1); L*M <= 512 */
+    int32_t ell;          /* iteration technique count (Eqs. iter1-iter2), >= 1 */
+    double delta;         /* rank threshold, relative to the largest singular value of S^ (default 1e-12) */
+    double eps_tau;       /* spurious threshold on tau_i / sigma_S,1 (Sec. 3.4.2; default 1e-8) */
+    double alpha;         /* ellipse aspect ratio (Sec. 4; default 0.1) */
+    int32_t variant;      /* cmsvd_variant */
+    int32_t solver;       /* cmsvd_solver */
+    int32_t precision;    /* cmsvd_precision */
+    int32_t max_iter;     /* Krylov iteration limit per pass (default 20000) */
+    double tol_solve;     /* relative residual of every shifted solve, Krylov solver (default 1e-12) */
+    double tol_triplet;   /* keep a triplet when ||A^T u - sigma v|| / ||A||_2 <= tol_triplet (default 1e-10) */
+    double norm_A;        /* ||A||_2 if known; <= 0 lets the library estimate it by Lanczos */
+    int32_t check_every;  /* Krylov iterations between host convergence checks (default 48) */
+    int32_t direct_max_block; /* AUTO picks DIRECT when the largest component has at most this many columns (default 32) */
+} cmsvd_params;
+
+/* Per-solve statistics. */
+typedef struct cmsvd_stats {
+    int64_t found;            /* t^, number of returned triplets */
+    int64_t in_interval;      /* Ritz values phi_i in [a, b] before the tau and residual tests */
+    int64_t rank;             /* columns kept by the delta truncation (Alg. 1 step 3) */
+    int64_t krylov_iters;     /* Lanczos steps of the last filter application (0 for DIRECT) */
+    int64_t max_component;    /* largest connected component of A^T A (DIRECT only) */
+    int32_t solver_used;      /* cmsvd_solver actually run */
+    int32_t converged;        /* 1 when every shifted solve met tol_solve */
+    double norm_A;            /* ||A||_2 used for the residual normalisation */
+    double sigma_S1;          /* largest singular value of S^ */
+    double max_res_u;         /* max over returned triplets of ||A^T u - sigma v|| / ||A||_2 */
+    double max_res_v;         /* max over returned triplets of ||A v - sigma u|| / ||A||_2 */
+    double ms_solve;          /* Alg. 1 steps 1-2 (shifted solves + moments), GPU time */
+    double ms_truncate;       /* step 3 */
+    double ms_qr;             /* step 4 */
+    double ms_ritz;           /* step 5, selection and residuals */
+} cmsvd_stats;
+
+typedef struct cmsvd_context cmsvd_context;
+typedef struct cmsvd_matrix cmsvd_matrix;
+typedef struct cmsvd_result cmsvd_result;
+
+/* Static text for a status code. */
+const char* cmsvd_status_string(int status);
+/* Message of the last failing call on this thread (static storage, overwritten by the next failure). */
+const char* cmsvd_last_error(void);
+/* Fill *p with the defaults listed in cmsvd_params. Returns CMSVD_INVALID_ARG for NULL. */
+int cmsvd_params_default(cmsvd_params* p);
+
+/*
+ * Context: binds the current CUDA device and a caller stream (cudaStream_t
+ * passed as void*; NULL means the legacy default stream). The stream is
+ * borrowed, not owned. The library also creates one internal stream of its
+ * own for graph capture; work on it is ordered after and before the caller's
+ * stream by events, so callers only ever synchronize their own stream.
+ */
+int cmsvd_context_create(void* stream, cmsvd_context** out);
+int cmsvd_context_destroy(cmsvd_context* ctx);   /* NULL is accepted */
+
+/*
+ * Sparse matrix A (m x n, m >= 1, n >= 1) in CSR form. rowptr: int64[m+1],
+ * colidx: int32[nnz], vals: float64[nnz]; where = 0 for host arrays, 1 for
+ * device arrays. The library copies them into its own device memory (the
+ * caller keeps ownership of its arrays), validates them on the device
+ * (rowptr monotone from 0 to nnz, columns strictly increasing within a row
+ * and in [0, n), values finite: otherwise CMSVD_INVALID_MATRIX and *out is
+ * NULL), and builds the CSR of A^T. The paper assumes m >= n (Sec. 1); m < n
+ * is accepted and simply means A^T A is rank deficient.
+ */
+int cmsvd_csr_create(cmsvd_context* ctx, int64_t m, int64_t n, int64_t nnz,
+                     const int64_t* rowptr, const int32_t* colidx, const double* vals,
+                     int where, cmsvd_matrix** out);
+int cmsvd_csr_destroy(cmsvd_matrix* A);          /* NULL is accepted */
+/* Dimensions of A. */
+int cmsvd_csr_shape(const cmsvd_matrix* A, int64_t* m, int64_t* n, int64_t* nnz);
+
+/*
+ * Y = A X (transpose = 0, X n x L, Y m x L) or Y = A^T X (transpose = 1,
+ * X m x L, Y n x L); device pointers, row-major with leading dimensions
+ * ldx >= L and ldy >= L. This is the H X = A^T (A X) building block of every
+ * shifted solve (Alg. 1 steps 1-2) and of A V~ (step 4).
+ */
+int cmsvd_spmm(cmsvd_matrix* A, int transpose, int64_t L, const double* X, int64_t ldx,
+               double* Y, int64_t ldy);
+
+/*
+ * Quadrature of Sec. 4 for j = 1..N/2 (the points with Im > 0, Sec. 3.1),
+ * computed on the device. Outputs are host arrays of N/2 complex values,
+ * interleaved (re, im): shift[j] = z_j (linear) or exp(t_j) (NT);
+ * weight[j] = omega_j (linear) or psi_j (NT); scaled[j] = (z_j - gamma)/rho
+ * (or (t_j - gamma)/rho), the node used for the moment weights. Any output
+ * may be NULL.
+ */
+int cmsvd_quadrature(cmsvd_context* ctx, double a, double b, int32_t N, int32_t variant,
+                     double alpha, double* shift, double* weight, double* scaled);
+
+/* Device workspace (bytes) that cmsvd_moments / cmsvd_solve_interval need for A and *p. */
+int cmsvd_workspace_size(const cmsvd_matrix* A, const cmsvd_params* p, size_t* bytes);
+
+/*
+ * Moment block of Alg. 1/2 steps 1-2 (with the halving of Sec. 3.1):
+ *   S_k = 2 Re sum_{j<=N/2} w_j ((node_j - gamma)/rho)^k (s_j I - A^T A)^{-1} S_0^(ell-1),
+ * k = 0..M (M+1 blocks: the last one is the S_M block of S_+, Sec. 3.4.1).
+ * V_in: device, n x L. S_out: device, n x L(M+1) row-major, column m*L + l.
+ * The moment weights use the scaled node (a reading of Eq. for S^_k that spans
+ * the same column space; see the design notes). Returns CMSVD_NOT_CONVERGED
+ * (with S_out filled) when a Krylov solve hit max_iter.
+ */
+int cmsvd_moments(cmsvd_matrix* A, double a, double b, const cmsvd_params* p,
+                  const double* V_in, double* S_out, void* workspace, size_t ws_bytes,
+                  cmsvd_stats* stats);
+
+/*
+ * Whole method, Alg. 1 (variant LINEAR) or Alg. 2 (variant NT): moments, rank
+ * truncation with delta (step 3), QR of A V~ (step 4), SVD of B and Ritz
+ * triplets (step 5), the tau test (Sec. 3.4.2) and exact residuals.
+ * V_in: device n x L (caller-drawn, e.g. Gaussian). workspace: device,
+ * >= cmsvd_workspace_size bytes, caller-owned; the result's arrays live in it,
+ * so it must outlive the result. *out receives a library-owned result (also
+ * on CMSVD_NOT_CONVERGED and CMSVD_SUBSPACE_SATURATED).
+ */
+int cmsvd_solve_interval(cmsvd_matrix* A, double a, double b, const cmsvd_params* p,
+                         const double* V_in, void* workspace, size_t ws_bytes,
+                         cmsvd_result** out);
+
+/* Number of triplets found (t^). */
+int cmsvd_result_count(const cmsvd_result* r, int64_t* t);
+/*
+ * Copy the triplets (any memory; each pointer may be NULL): sigma[t] ascending;
+ * U m x t and V n x t column-major; res_u[t] = ||A^T u - sigma v|| / ||A||_2;
+ * res_v[t] = ||A v - sigma u|| / ||A||_2; tau[t] = tau_i / sigma_S,1.
+ * Signs: the largest-magnitude entry of each v (first on ties) is positive.
+ */
+int cmsvd_result_copy(const cmsvd_result* r, double* sigma, double* U, double* V,
+                      double* res_u, double* res_v, double* tau);
+int cmsvd_result_stats(const cmsvd_result* r, cmsvd_stats* stats);
+int cmsvd_result_destroy(cmsvd_result* r);       /* NULL is accepted */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CMSVD_H */

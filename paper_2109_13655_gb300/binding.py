@@ -1,0 +1,309 @@
+"""ctypes binding of libcmsvd.so (include/cmsvd.h): argument marshalling only.
+
+Every computation happens in the CUDA library. PyTorch supplies device memory
+and the stream; tensors are passed as raw device pointers. If the library is
+missing, ``lib()`` raises: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcmsvd.so")
+
+OK, INVALID_ARG, INVALID_MATRIX, OUT_OF_MEMORY, WORKSPACE_TOO_SMALL, NOT_CONVERGED, BREAKDOWN, \
+    SUBSPACE_SATURATED, CUDA_ERROR, NOT_SUPPORTED = range(10)
+LINEAR, NT = 0, 1
+SOLVER_AUTO, SOLVER_KRYLOV, SOLVER_DIRECT = 0, 1, 2
+FP64, MIXED = 0, 1
+VARIANTS = {"linear": LINEAR, "nt": NT}
+SOLVERS = {"auto": SOLVER_AUTO, "krylov": SOLVER_KRYLOV, "direct": SOLVER_DIRECT}
+
+
+class cmsvd_params(C.Structure):
+    _fields_ = [("N", C.c_int32), ("L", C.c_int32), ("M", C.c_int32), ("ell", C.c_int32),
+                ("delta", C.c_double), ("eps_tau", C.c_double), ("alpha", C.c_double),
+                ("variant", C.c_int32), ("solver", C.c_int32), ("precision", C.c_int32),
+                ("max_iter", C.c_int32), ("tol_solve", C.c_double), ("tol_triplet", C.c_double),
+                ("norm_A", C.c_double), ("check_every", C.c_int32), ("direct_max_block", C.c_int32)]
+
+
+class cmsvd_stats(C.Structure):
+    _fields_ = [("found", C.c_int64), ("in_interval", C.c_int64), ("rank", C.c_int64),
+                ("krylov_iters", C.c_int64), ("max_component", C.c_int64),
+                ("solver_used", C.c_int32), ("converged", C.c_int32),
+                ("norm_A", C.c_double), ("sigma_S1", C.c_double), ("max_res_u", C.c_double),
+                ("max_res_v", C.c_double), ("ms_solve", C.c_double), ("ms_truncate", C.c_double),
+                ("ms_qr", C.c_double), ("ms_ritz", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = C.c_void_p
+_I64 = C.c_int64
+_SIGS = {
+    "cmsvd_status_string": (C.c_char_p, [C.c_int]),
+    "cmsvd_last_error": (C.c_char_p, []),
+    "cmsvd_params_default": (C.c_int, [C.POINTER(cmsvd_params)]),
+    "cmsvd_context_create": (C.c_int, [_P, C.POINTER(_P)]),
+    "cmsvd_context_destroy": (C.c_int, [_P]),
+    "cmsvd_csr_create": (C.c_int, [_P, _I64, _I64, _I64, _P, _P, _P, C.c_int, C.POINTER(_P)]),
+    "cmsvd_csr_destroy": (C.c_int, [_P]),
+    "cmsvd_csr_shape": (C.c_int, [_P, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I64)]),
+    "cmsvd_spmm": (C.c_int, [_P, C.c_int, _I64, _P, _I64, _P, _I64]),
+    "cmsvd_quadrature": (C.c_int, [_P, C.c_double, C.c_double, C.c_int32, C.c_int32, C.c_double, _P, _P, _P]),
+    "cmsvd_workspace_size": (C.c_int, [_P, C.POINTER(cmsvd_params), C.POINTER(C.c_size_t)]),
+    "cmsvd_moments": (C.c_int, [_P, C.c_double, C.c_double, C.POINTER(cmsvd_params), _P, _P, _P, C.c_size_t,
+                                C.POINTER(cmsvd_stats)]),
+    "cmsvd_solve_interval": (C.c_int, [_P, C.c_double, C.c_double, C.POINTER(cmsvd_params), _P, _P, C.c_size_t,
+                                       C.POINTER(_P)]),
+    "cmsvd_result_count": (C.c_int, [_P, C.POINTER(_I64)]),
+    "cmsvd_result_copy": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "cmsvd_result_stats": (C.c_int, [_P, C.POINTER(cmsvd_stats)]),
+    "cmsvd_result_destroy": (C.c_int, [_P]),
+}
+EXPORTED = tuple(_SIGS)
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load libcmsvd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                               "(there is no CPU fallback)")
+        h = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(h, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = h
+    return _lib
+
+
+class CmsvdError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = lib().cmsvd_last_error().decode(errors="replace")
+        name = lib().cmsvd_status_string(status).decode()
+        super().__init__(f"{where}: {name} ({status}): {msg}")
+
+
+def _check(status: int, where: str, allow=()) -> int:
+    if status != OK and status not in allow:
+        raise CmsvdError(status, where)
+    return status
+
+
+def _ptr(t) -> int:
+    """Device or host address of a torch tensor or numpy array (must be contiguous)."""
+    if isinstance(t, np.ndarray):
+        assert t.flags["C_CONTIGUOUS"]
+        return t.ctypes.data
+    assert t.is_contiguous()
+    return t.data_ptr()
+
+
+def params(**kw) -> cmsvd_params:
+    """cmsvd_params with the library defaults, overridden by keyword arguments.
+    variant / solver accept the strings of VARIANTS / SOLVERS."""
+    p = cmsvd_params()
+    _check(lib().cmsvd_params_default(C.byref(p)), "cmsvd_params_default")
+    for k, v in kw.items():
+        if k == "variant" and isinstance(v, str):
+            v = VARIANTS[v]
+        if k == "solver" and isinstance(v, str):
+            v = SOLVERS[v]
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+# ----------------------------------------------------------------------------- raw entry points
+def cmsvd_context_create(stream: int = 0) -> int:
+    h = _P()
+    _check(lib().cmsvd_context_create(_P(stream), C.byref(h)), "cmsvd_context_create")
+    return h.value
+
+
+def cmsvd_context_destroy(ctx: int) -> None:
+    _check(lib().cmsvd_context_destroy(_P(ctx)), "cmsvd_context_destroy")
+
+
+def cmsvd_csr_create(ctx: int, m: int, n: int, rowptr, colidx, vals) -> int:
+    """rowptr int64[m+1], colidx int32[nnz], vals float64[nnz]: numpy (host) or torch CUDA tensors."""
+    on_dev = 0 if isinstance(rowptr, np.ndarray) else 1
+    if on_dev == 0:
+        rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+        colidx = np.ascontiguousarray(colidx, dtype=np.int32)
+        vals = np.ascontiguousarray(vals, dtype=np.float64)
+    nnz = int(rowptr[-1])
+    h = _P()
+    _check(lib().cmsvd_csr_create(_P(ctx), m, n, nnz, _ptr(rowptr), _ptr(colidx) if nnz else None,
+                                  _ptr(vals) if nnz else None, on_dev, C.byref(h)), "cmsvd_csr_create")
+    return h.value
+
+
+def cmsvd_csr_destroy(A: int) -> None:
+    _check(lib().cmsvd_csr_destroy(_P(A)), "cmsvd_csr_destroy")
+
+
+def cmsvd_csr_shape(A: int):
+    m, n, z = _I64(), _I64(), _I64()
+    _check(lib().cmsvd_csr_shape(_P(A), C.byref(m), C.byref(n), C.byref(z)), "cmsvd_csr_shape")
+    return m.value, n.value, z.value
+
+
+def cmsvd_spmm(A: int, transpose: bool, X, Y) -> None:
+    """Y = A X (or A^T X); X, Y float64 CUDA tensors, row-major blocks."""
+    L = X.shape[1]
+    _check(lib().cmsvd_spmm(_P(A), int(transpose), L, _ptr(X), X.stride(0), _ptr(Y), Y.stride(0)), "cmsvd_spmm")
+
+
+def cmsvd_quadrature(ctx: int, a: float, b: float, N: int, variant="linear", alpha: float = 0.1):
+    """(shift, weight, scaled) for j = 1..N/2 as complex128 numpy arrays."""
+    J = N // 2
+    out = [np.zeros(2 * J) for _ in range(3)]
+    v = VARIANTS[variant] if isinstance(variant, str) else variant
+    _check(lib().cmsvd_quadrature(_P(ctx), a, b, N, v, alpha, *(o.ctypes.data for o in out)), "cmsvd_quadrature")
+    return tuple(o[0::2] + 1j * o[1::2] for o in out)
+
+
+def cmsvd_workspace_size(A: int, p: cmsvd_params) -> int:
+    n = C.c_size_t()
+    _check(lib().cmsvd_workspace_size(_P(A), C.byref(p), C.byref(n)), "cmsvd_workspace_size")
+    return n.value
+
+
+def cmsvd_moments(A: int, a: float, b: float, p: cmsvd_params, V_in, S_out, workspace) -> tuple[int, dict]:
+    st = cmsvd_stats()
+    s = lib().cmsvd_moments(_P(A), a, b, C.byref(p), _ptr(V_in), _ptr(S_out), _ptr(workspace),
+                            workspace.numel() * workspace.element_size(), C.byref(st))
+    _check(s, "cmsvd_moments", allow=(NOT_CONVERGED,))
+    return s, st.as_dict()
+
+
+def cmsvd_solve_interval(A: int, a: float, b: float, p: cmsvd_params, V_in, workspace) -> tuple[int, int]:
+    r = _P()
+    s = lib().cmsvd_solve_interval(_P(A), a, b, C.byref(p), _ptr(V_in), _ptr(workspace),
+                                   workspace.numel() * workspace.element_size(), C.byref(r))
+    _check(s, "cmsvd_solve_interval", allow=(NOT_CONVERGED, SUBSPACE_SATURATED))
+    return s, r.value
+
+
+def cmsvd_result_count(r: int) -> int:
+    t = _I64()
+    _check(lib().cmsvd_result_count(_P(r), C.byref(t)), "cmsvd_result_count")
+    return t.value
+
+
+def cmsvd_result_copy(r: int, sigma=None, U=None, V=None, res_u=None, res_v=None, tau=None) -> None:
+    args = [_P(_ptr(x)) if x is not None else None for x in (sigma, U, V, res_u, res_v, tau)]
+    _check(lib().cmsvd_result_copy(_P(r), *args), "cmsvd_result_copy")
+
+
+def cmsvd_result_stats(r: int) -> dict:
+    st = cmsvd_stats()
+    _check(lib().cmsvd_result_stats(_P(r), C.byref(st)), "cmsvd_result_stats")
+    return st.as_dict()
+
+
+def cmsvd_result_destroy(r: int) -> None:
+    _check(lib().cmsvd_result_destroy(_P(r)), "cmsvd_result_destroy")
+
+
+# ----------------------------------------------------------------------------- convenience
+@dataclass
+class Triplets:
+    sigma: np.ndarray
+    U: np.ndarray          # m x t
+    V: np.ndarray          # n x t
+    res_u: np.ndarray
+    res_v: np.ndarray
+    tau: np.ndarray
+    stats: dict
+    status: int
+
+
+class Context:
+    """A cmsvd context bound to torch's current CUDA stream (or a given one)."""
+
+    def __init__(self, stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self.handle = cmsvd_context_create(stream.cuda_stream)
+
+    def close(self):
+        if self.handle:
+            cmsvd_context_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Matrix:
+    """A CSR matrix resident on the device (library-owned copy)."""
+
+    def __init__(self, ctx: Context, m: int, n: int, rowptr, colidx, vals):
+        self.ctx = ctx
+        self.m, self.n = m, n
+        self.handle = cmsvd_csr_create(ctx.handle, m, n, rowptr, colidx, vals)
+
+    @classmethod
+    def from_csr(cls, ctx: Context, A) -> "Matrix":
+        return cls(ctx, A.m, A.n, A.rowptr, A.colidx, A.vals)
+
+    def close(self):
+        if self.handle:
+            cmsvd_csr_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace(self, p: cmsvd_params):
+        import torch
+        return torch.empty(cmsvd_workspace_size(self.handle, p), dtype=torch.uint8, device="cuda")
+
+    def spmm(self, X, transpose: bool = False):
+        import torch
+        rows = self.n if transpose else self.m
+        Y = torch.empty((rows, X.shape[1]), dtype=torch.float64, device=X.device)
+        cmsvd_spmm(self.handle, transpose, X, Y)
+        return Y
+
+    def moments(self, a, b, p: cmsvd_params, V_in, workspace=None):
+        import torch
+        ws = workspace if workspace is not None else self.workspace(p)
+        S = torch.empty((self.n, p.L * (p.M + 1)), dtype=torch.float64, device=V_in.device)
+        status, st = cmsvd_moments(self.handle, a, b, p, V_in, S, ws)
+        return S, status, st
+
+    def solve_interval(self, a, b, p: cmsvd_params, V_in, workspace=None) -> Triplets:
+        ws = workspace if workspace is not None else self.workspace(p)
+        status, r = cmsvd_solve_interval(self.handle, a, b, p, V_in, ws)
+        try:
+            t = cmsvd_result_count(r)
+            out = [np.zeros(t), np.zeros((t, self.m)), np.zeros((t, self.n)), np.zeros(t), np.zeros(t), np.zeros(t)]
+            cmsvd_result_copy(r, *out)
+            st = cmsvd_result_stats(r)
+        finally:
+            cmsvd_result_destroy(r)
+        return Triplets(out[0], out[1].T.copy(), out[2].T.copy(), out[3], out[4], out[5], st, status)

@@ -1,0 +1,258 @@
+// CSR storage of A and A^T, validation, and the SpMM Y = A X that every
+// shifted solve (Alg. 1 steps 1-2, as H X = A^T (A X)) and step 4 (A V~) use.
+#include "internal.cuh"
+#include <cstdarg>
+#include <cstdio>
+
+namespace cmsvd {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+const char* last_error() { return g_err; }
+
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+    set_error("%s failed: %s (%s:%d)", what, cudaGetErrorString(e), file, line);
+    return e == cudaErrorMemoryAllocation ? CMSVD_OUT_OF_MEMORY : CMSVD_CUDA_ERROR;
+}
+
+static int grid_for(int64_t work, int per_block, int cap) {
+    int64_t g = (work + per_block - 1) / per_block;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+// ----------------------------------------------------------------------------- validation
+// bad bits: 1 rowptr range, 2 column out of range, 4 columns not strictly increasing,
+// 8 non-finite value, 16 rowptr[0] != 0 or rowptr[m] != nnz
+__global__ void k_validate(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                           const double* __restrict__ vals, int64_t m, int64_t n, int64_t nnz, int* bad) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i0 == 0 && (rowptr[0] != 0 || rowptr[m] != nnz)) atomicOr(bad, 16);
+    int local = 0;
+    for (int64_t i = i0; i < m; i += stride) {
+        int64_t s = rowptr[i], e = rowptr[i + 1];
+        if (s < 0 || e < s || e > nnz) { local |= 1; continue; }
+        int32_t prev = -1;
+        for (int64_t p = s; p < e; ++p) {
+            int32_t c = colidx[p];
+            if (c < 0 || c >= n) local |= 2;
+            if (c <= prev) local |= 4;
+            prev = c;
+            if (!isfinite(vals[p])) local |= 8;
+        }
+    }
+    if (local) atomicOr(bad, local);
+}
+
+int csr_upload_validate(cmsvd_context* ctx, int64_t m, int64_t n, int64_t nnz, const int64_t* rowptr,
+                        const int32_t* colidx, const double* vals, int where, Csr* out) {
+    cudaStream_t s = ctx->s;
+    Csr A;
+    A.m = m; A.n = n; A.nnz = nnz;
+    CM_CUDA(cudaMalloc(&A.rowptr, sizeof(int64_t) * (m + 1)));
+    if (cudaMalloc(&A.colidx, sizeof(int32_t) * (nnz > 0 ? nnz : 1)) != cudaSuccess ||
+        cudaMalloc(&A.vals, sizeof(double) * (nnz > 0 ? nnz : 1)) != cudaSuccess) {
+        csr_free(&A);
+        set_error("out of device memory for a CSR with %lld nonzeros", (long long)nnz);
+        return CMSVD_OUT_OF_MEMORY;
+    }
+    cudaMemcpyKind kind = where ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    int st = CMSVD_OK;
+    auto chk = [&](cudaError_t e, const char* w) { if (e != cudaSuccess && st == CMSVD_OK) st = cuda_fail(e, w, __FILE__, __LINE__); };
+    chk(cudaMemcpyAsync(A.rowptr, rowptr, sizeof(int64_t) * (m + 1), kind, s), "copy rowptr");
+    if (nnz > 0) {
+        chk(cudaMemcpyAsync(A.colidx, colidx, sizeof(int32_t) * nnz, kind, s), "copy colidx");
+        chk(cudaMemcpyAsync(A.vals, vals, sizeof(double) * nnz, kind, s), "copy vals");
+    }
+    int* bad_d = nullptr;
+    chk(cudaMalloc(&bad_d, sizeof(int)), "alloc flag");
+    if (st == CMSVD_OK) {
+        chk(cudaMemsetAsync(bad_d, 0, sizeof(int), s), "memset");
+        k_validate<<<grid_for(m, 256, ctx->sm_count * 8), 256, 0, s>>>(A.rowptr, A.colidx, A.vals, m, n, nnz, bad_d);
+        chk(cudaGetLastError(), "k_validate");
+        chk(cudaMemcpyAsync(ctx->pinned, bad_d, sizeof(int), cudaMemcpyDeviceToHost, s), "copy flag");
+        chk(cudaStreamSynchronize(s), "sync");
+    }
+    if (bad_d) cudaFree(bad_d);
+    if (st != CMSVD_OK) { csr_free(&A); return st; }
+    int bad = ctx->pinned[0];
+    if (bad) {
+        csr_free(&A);
+        set_error("invalid CSR (flags 0x%x: 1 row pointer range, 2 column index range, 4 unsorted or duplicate "
+                  "columns, 8 non-finite value, 16 rowptr ends)", bad);
+        return CMSVD_INVALID_MATRIX;
+    }
+    *out = A;
+    return CMSVD_OK;
+}
+
+void csr_free(Csr* A) {
+    if (A->rowptr) cudaFree(A->rowptr);
+    if (A->colidx) cudaFree(A->colidx);
+    if (A->vals) cudaFree(A->vals);
+    A->rowptr = nullptr; A->colidx = nullptr; A->vals = nullptr;
+}
+
+// ----------------------------------------------------------------------------- transpose
+__global__ void k_col_count(const int32_t* __restrict__ colidx, int64_t nnz, unsigned long long* counts) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += stride)
+        atomicAdd(&counts[colidx[p] + 1], 1ull);
+}
+
+// In-place inclusive scan of len int64 values with one block of 1024 threads.
+__global__ void k_scan_inclusive(int64_t* v, int64_t len) {
+    __shared__ int64_t part[1024];
+    const int t = threadIdx.x;
+    int64_t chunk = (len + 1023) / 1024;
+    int64_t lo = t * chunk, hi = lo + chunk < len ? lo + chunk : len;
+    int64_t sum = 0;
+    for (int64_t i = lo; i < hi; ++i) sum += v[i];
+    part[t] = sum;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        int64_t add = t >= off ? part[t - off] : 0;
+        __syncthreads();
+        part[t] += add;
+        __syncthreads();
+    }
+    int64_t run = t ? part[t - 1] : 0;
+    for (int64_t i = lo; i < hi; ++i) { run += v[i]; v[i] = run; }
+}
+
+__global__ void k_scatter_t(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                            const double* __restrict__ vals, int64_t m, unsigned long long* cursor,
+                            int32_t* __restrict__ tcol, double* __restrict__ tval) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+            unsigned long long pos = atomicAdd(&cursor[colidx[p]], 1ull);
+            tcol[pos] = (int32_t)i;
+            tval[pos] = vals[p];
+        }
+    }
+}
+
+// The scatter order inside a column depends on atomics; sorting each column by
+// row index makes the transpose (and every SpMM with it) deterministic.
+__global__ void k_sort_segments(const int64_t* __restrict__ ptr, int64_t nseg, int32_t* key, double* val) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nseg; c += stride) {
+        int64_t s = ptr[c], e = ptr[c + 1];
+        for (int64_t i = s + 1; i < e; ++i) {
+            int32_t k = key[i];
+            double v = val[i];
+            int64_t j = i - 1;
+            while (j >= s && key[j] > k) { key[j + 1] = key[j]; val[j + 1] = val[j]; --j; }
+            key[j + 1] = k;
+            val[j + 1] = v;
+        }
+    }
+}
+
+int csr_transpose(cmsvd_context* ctx, const Csr& A, Csr* At) {
+    cudaStream_t s = ctx->s;
+    Csr T;
+    T.m = A.n; T.n = A.m; T.nnz = A.nnz;
+    CM_CUDA(cudaMalloc(&T.rowptr, sizeof(int64_t) * (T.m + 1)));
+    if (cudaMalloc(&T.colidx, sizeof(int32_t) * (A.nnz > 0 ? A.nnz : 1)) != cudaSuccess ||
+        cudaMalloc(&T.vals, sizeof(double) * (A.nnz > 0 ? A.nnz : 1)) != cudaSuccess) {
+        csr_free(&T);
+        set_error("out of device memory for the transpose");
+        return CMSVD_OUT_OF_MEMORY;
+    }
+    unsigned long long* cursor = nullptr;
+    if (cudaMalloc(&cursor, sizeof(unsigned long long) * (T.m + 1)) != cudaSuccess) {
+        csr_free(&T);
+        set_error("out of device memory for the transpose cursor");
+        return CMSVD_OUT_OF_MEMORY;
+    }
+    int st = CMSVD_OK;
+    auto chk = [&](cudaError_t e, const char* w) { if (e != cudaSuccess && st == CMSVD_OK) st = cuda_fail(e, w, __FILE__, __LINE__); };
+    chk(cudaMemsetAsync(T.rowptr, 0, sizeof(int64_t) * (T.m + 1), s), "memset");
+    int gcap = ctx->sm_count * 8;
+    k_col_count<<<grid_for(A.nnz, 256, gcap), 256, 0, s>>>(A.colidx, A.nnz, (unsigned long long*)T.rowptr);
+    chk(cudaGetLastError(), "k_col_count");
+    k_scan_inclusive<<<1, 1024, 0, s>>>(T.rowptr, T.m + 1);
+    chk(cudaGetLastError(), "k_scan");
+    chk(cudaMemcpyAsync(cursor, T.rowptr, sizeof(int64_t) * (T.m + 1), cudaMemcpyDeviceToDevice, s), "copy");
+    k_scatter_t<<<grid_for(A.m, 256, gcap), 256, 0, s>>>(A.rowptr, A.colidx, A.vals, A.m, cursor, T.colidx, T.vals);
+    chk(cudaGetLastError(), "k_scatter");
+    k_sort_segments<<<grid_for(T.m, 256, gcap), 256, 0, s>>>(T.rowptr, T.m, T.colidx, T.vals);
+    chk(cudaGetLastError(), "k_sort");
+    chk(cudaStreamSynchronize(s), "sync");
+    cudaFree(cursor);
+    if (st != CMSVD_OK) { csr_free(&T); return st; }
+    *At = T;
+    return CMSVD_OK;
+}
+
+// ----------------------------------------------------------------------------- SpMM
+// One group of LPR lanes per row; lane l owns columns l, l+LPR, ... of the
+// row-major L-column block. The row's (col, val) pairs are loaded cooperatively
+// and broadcast with shuffles, so every nonzero reads one contiguous L-vector of
+// X. Each output element is summed in the row's storage order (deterministic).
+template <int LPR, int CPL>
+__global__ void __launch_bounds__(256) k_spmm(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                                              const double* __restrict__ vals, int64_t rows, int L,
+                                              const double* __restrict__ X, int64_t ldx, double* __restrict__ Y,
+                                              int64_t ldy) {
+    const int lane = threadIdx.x % LPR;
+    const int64_t group = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LPR;
+    const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / LPR;
+    const unsigned mask = LPR == 32 ? 0xffffffffu : (((1u << LPR) - 1u) << ((threadIdx.x & 31) / LPR * LPR));
+    for (int64_t r = group; r < rows; r += ngroups) {
+        const int64_t s = rowptr[r], e = rowptr[r + 1];
+        for (int c0 = 0; c0 < L; c0 += LPR * CPL) {
+            double acc[CPL];
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) acc[q] = 0.0;
+            for (int64_t p0 = s; p0 < e; p0 += LPR) {
+                const int64_t p = p0 + lane;
+                int32_t mc = 0;
+                double mv = 0.0;
+                if (p < e) { mc = colidx[p]; mv = vals[p]; }
+                const int cnt = (int)((e - p0) < LPR ? (e - p0) : LPR);
+                for (int k = 0; k < cnt; ++k) {
+                    const int32_t col = __shfl_sync(mask, mc, k, LPR);
+                    const double v = __shfl_sync(mask, mv, k, LPR);
+                    const double* xr = X + (int64_t)col * ldx + c0 + lane;
+#pragma unroll
+                    for (int q = 0; q < CPL; ++q)
+                        if (c0 + lane + q * LPR < L) acc[q] = __fma_rn(v, __ldg(xr + q * LPR), acc[q]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < CPL; ++q)
+                if (c0 + lane + q * LPR < L) Y[r * ldy + c0 + lane + q * LPR] = acc[q];
+        }
+    }
+}
+
+int spmm(const Csr& A, int L, const double* X, int64_t ldx, double* Y, int64_t ldy, cudaStream_t s) {
+    if (A.m == 0 || L <= 0) return CMSVD_OK;
+    int dev_sms = 152;
+    if (L <= 8) {
+        int rows_per_block = 256 / 8;
+        k_spmm<8, 1><<<grid_for(A.m, rows_per_block, dev_sms * 32), 256, 0, s>>>(A.rowptr, A.colidx, A.vals, A.m, L, X, ldx, Y, ldy);
+    } else if (L <= 16) {
+        int rows_per_block = 256 / 16;
+        k_spmm<16, 1><<<grid_for(A.m, rows_per_block, dev_sms * 32), 256, 0, s>>>(A.rowptr, A.colidx, A.vals, A.m, L, X, ldx, Y, ldy);
+    } else if (L <= 32) {
+        k_spmm<32, 1><<<grid_for(A.m, 8, dev_sms * 32), 256, 0, s>>>(A.rowptr, A.colidx, A.vals, A.m, L, X, ldx, Y, ldy);
+    } else {
+        k_spmm<32, 4><<<grid_for(A.m, 8, dev_sms * 32), 256, 0, s>>>(A.rowptr, A.colidx, A.vals, A.m, L, X, ldx, Y, ldy);
+    }
+    CM_LAUNCH();
+    return CMSVD_OK;
+}
+
+}  // namespace cmsvd

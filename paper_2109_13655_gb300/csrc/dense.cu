@@ -1,0 +1,358 @@
+// Dense FP64 kernels of the Rayleigh-Ritz part (Alg. 1 steps 3-5):
+//   - Gram G = X^T Y of tall-skinny blocks (deterministic split-n reduction),
+//   - Z = X W for tall X and small W,
+//   - shifted CholeskyQR3 (X = Q R) used for the rank truncation of S^ (step 3)
+//     and for qr(A V~) (step 4),
+//   - one-sided Jacobi SVD of a small square matrix (SVD of R in step 3 and of B
+//     in step 5), which keeps the high relative accuracy of small singular values.
+// FP64 on this part runs on the FP64 pipe (no FP64 tensor-core path is used).
+#include "internal.cuh"
+
+namespace cmsvd {
+
+// ----------------------------------------------------------------------------- Gram
+constexpr int GT = 64;   // output tile
+constexpr int GK = 16;   // rows per slab
+
+__global__ void __launch_bounds__(256) k_gram_partial(const double* __restrict__ X, int64_t ldx, int c1,
+                                                      const double* __restrict__ Y, int64_t ldy, int c2, int64_t n,
+                                                      int64_t rows_per_chunk, double* __restrict__ partials) {
+    __shared__ double Xs[GK][GT];
+    __shared__ double Ys[GK][GT];
+    const int ti = blockIdx.x * GT, tj = blockIdx.y * GT;
+    const int64_t r0 = (int64_t)blockIdx.z * rows_per_chunk;
+    const int64_t r1 = r0 + rows_per_chunk < n ? r0 + rows_per_chunk : n;
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int64_t r = r0; r < r1; r += GK) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + 256 * q, rr = e / GT, cc = e % GT;
+            const bool rowok = r + rr < r1;
+            Xs[rr][cc] = (rowok && ti + cc < c1) ? X[(r + rr) * ldx + ti + cc] : 0.0;
+            Ys[rr][cc] = (rowok && tj + cc < c2) ? Y[(r + rr) * ldy + tj + cc] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < GK; ++k) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = Xs[k][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Ys[k][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = __fma_rn(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gi = ti + ty + 16 * i, gj = tj + tx + 16 * j;
+            if (gi < c1 && gj < c2) partials[((size_t)blockIdx.z * c1 + gi) * c2 + gj] = acc[i][j];
+        }
+}
+
+__global__ void k_sum_partials(const double* __restrict__ partials, int nchunks, int64_t count, double* __restrict__ G) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= count) return;
+    double s = 0.0;
+    for (int c = 0; c < nchunks; ++c) s += partials[(size_t)c * count + e];
+    G[e] = s;
+}
+
+static void gram_plan(int c1, int c2, int64_t n, int sm_count, int* nchunks, int64_t* rpc) {
+    const int tiles = ((c1 + GT - 1) / GT) * ((c2 + GT - 1) / GT);
+    int64_t want = (2 * (int64_t)sm_count + tiles - 1) / tiles;
+    int64_t maxc = (n + 63) / 64;
+    if (want > maxc) want = maxc;
+    if (want < 1) want = 1;
+    int64_t r = (n + want - 1) / want;
+    r = (r + GK - 1) / GK * GK;
+    if (r < GK) r = GK;
+    *rpc = r;
+    *nchunks = (int)((n + r - 1) / r);
+    if (*nchunks < 1) *nchunks = 1;
+}
+
+size_t gram_partials_size(int c1, int c2, int64_t n, int sm_count) {
+    int nc;
+    int64_t rpc;
+    gram_plan(c1, c2, n, sm_count, &nc, &rpc);
+    return (size_t)nc * c1 * c2;
+}
+
+int gram(const double* X, int64_t ldx, int c1, const double* Y, int64_t ldy, int c2, int64_t n, double* G,
+         double* partials, size_t partials_cap, int sm_count, cudaStream_t s) {
+    int nc;
+    int64_t rpc;
+    gram_plan(c1, c2, n, sm_count, &nc, &rpc);
+    if ((size_t)nc * c1 * c2 > partials_cap) { set_error("gram scratch too small"); return CMSVD_WORKSPACE_TOO_SMALL; }
+    dim3 grid((c1 + GT - 1) / GT, (c2 + GT - 1) / GT, nc);
+    k_gram_partial<<<grid, 256, 0, s>>>(X, ldx, c1, Y, ldy, c2, n, rpc, partials);
+    CM_LAUNCH();
+    const int64_t cnt = (int64_t)c1 * c2;
+    k_sum_partials<<<(int)((cnt + 255) / 256), 256, 0, s>>>(partials, nc, cnt, G);
+    CM_LAUNCH();
+    return CMSVD_OK;
+}
+
+// ----------------------------------------------------------------------------- Z = X W
+__global__ void __launch_bounds__(256) k_gemm_nn(const double* __restrict__ X, int64_t ldx, const double* __restrict__ W,
+                                                 int64_t ldw, double* __restrict__ Z, int64_t ldz, int64_t n, int c1, int c2) {
+    __shared__ double Xs[GT][GK + 1];
+    __shared__ double Ws[GK][GT];
+    const int64_t r0 = (int64_t)blockIdx.y * GT;
+    const int cc0 = blockIdx.x * GT;
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int k0 = 0; k0 < c1; k0 += GK) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + 256 * q;
+            const int xr = e / GK, xk = e % GK;
+            Xs[xr][xk] = (r0 + xr < n && k0 + xk < c1) ? X[(r0 + xr) * ldx + k0 + xk] : 0.0;
+            const int wk = e / GT, wc = e % GT;
+            Ws[wk][wc] = (k0 + wk < c1 && cc0 + wc < c2) ? W[(int64_t)(k0 + wk) * ldw + cc0 + wc] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < GK; ++k) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = Xs[ty + 16 * i][k];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Ws[k][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = __fma_rn(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int64_t gr = r0 + ty + 16 * i;
+            const int gc = cc0 + tx + 16 * j;
+            if (gr < n && gc < c2) Z[gr * ldz + gc] = acc[i][j];
+        }
+}
+
+int gemm_nn(const double* X, int64_t ldx, const double* W, int64_t ldw, double* Z, int64_t ldz, int64_t n, int c1,
+            int c2, cudaStream_t s) {
+    if (n <= 0 || c2 <= 0) return CMSVD_OK;
+    dim3 grid((c2 + GT - 1) / GT, (unsigned)((n + GT - 1) / GT));
+    k_gemm_nn<<<grid, 256, 0, s>>>(X, ldx, W, ldw, Z, ldz, n, c1, c2);
+    CM_LAUNCH();
+    return CMSVD_OK;
+}
+
+// ----------------------------------------------------------------------------- Cholesky / inverse
+// R (c x c, row-major, upper) with R^T R = G + shift I, where
+// shift = shift_coef * trace(G) (shift_coef = 0: plain Cholesky). One CTA.
+// A pivot that is not positive is replaced by a tiny positive value and flagged.
+__global__ void __launch_bounds__(1024) k_chol(const double* __restrict__ G, int c, double shift_coef, double* __restrict__ R,
+                                               int* flag) {
+    __shared__ double sh_tr, sh_piv;
+    const int t = threadIdx.x, nt = blockDim.x;
+    if (t == 0) {
+        double tr = 0.0;
+        for (int i = 0; i < c; ++i) tr += G[(size_t)i * c + i];
+        sh_tr = tr;
+    }
+    __syncthreads();
+    const double shift = shift_coef * sh_tr;
+    for (int e = t; e < c * c; e += nt) {
+        const int i = e / c, j = e % c;
+        R[e] = j >= i ? G[e] + (i == j ? shift : 0.0) : 0.0;
+    }
+    __syncthreads();
+    for (int k = 0; k < c; ++k) {
+        if (t == 0) {
+            double p = R[(size_t)k * c + k];
+            const double floor_ = 1e-300 + 1e-32 * sh_tr;
+            if (!(p > floor_)) {
+                atomicOr(flag, 1);
+                p = floor_;
+            }
+            p = sqrt(p);
+            R[(size_t)k * c + k] = p;
+            sh_piv = p;
+        }
+        __syncthreads();
+        const double piv = sh_piv;
+        for (int j = k + 1 + t; j < c; j += nt) R[(size_t)k * c + j] /= piv;
+        __syncthreads();
+        const int w = c - k - 1;
+        for (int e = t; e < w * w; e += nt) {
+            const int i = k + 1 + e / w, j = k + 1 + e % w;
+            if (j >= i) R[(size_t)i * c + j] = __fma_rn(-R[(size_t)k * c + i], R[(size_t)k * c + j], R[(size_t)i * c + j]);
+        }
+        __syncthreads();
+    }
+}
+
+// Ri = R^{-1} for upper-triangular R (row-major); one thread per column.
+__global__ void k_trinv(const double* __restrict__ R, int c, double* __restrict__ Ri) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= c) return;
+    for (int i = j + 1; i < c; ++i) Ri[(size_t)i * c + j] = 0.0;
+    Ri[(size_t)j * c + j] = 1.0 / R[(size_t)j * c + j];
+    for (int i = j - 1; i >= 0; --i) {
+        double s = 0.0;
+        for (int k = i + 1; k <= j; ++k) s = __fma_rn(R[(size_t)i * c + k], Ri[(size_t)k * c + j], s);
+        Ri[(size_t)i * c + j] = -s / R[(size_t)i * c + i];
+    }
+}
+
+size_t cholqr_scratch(int c, int64_t n, int sm_count) {
+    return (size_t)n * c + 6 * (size_t)c * c + gram_partials_size(c, c, n, sm_count) + 64;
+}
+
+// Shifted CholeskyQR3: the first pass adds the shift 11 (n c + c (c+1)) u ||X||_F^2 so
+// that it succeeds for numerically rank-deficient X; two plain passes restore
+// orthogonality. X = Q R3 R2 R1.
+int cholqr3(const double* X, int64_t ldx, int64_t n, int c, double* Q, int64_t ldq, double* R, double* scratch,
+            int* flag, int sm_count, cudaStream_t s) {
+    double* T = scratch;
+    double* G = T + (size_t)n * c;
+    double* R1 = G + (size_t)c * c;
+    double* R2 = R1 + (size_t)c * c;
+    double* R3 = R2 + (size_t)c * c;
+    double* Ri = R3 + (size_t)c * c;
+    double* Tm = Ri + (size_t)c * c;
+    double* part = Tm + (size_t)c * c;
+    const size_t pcap = gram_partials_size(c, c, n, sm_count);
+    const double u = 1.1102230246251565e-16;
+    const double shift_coef = 11.0 * ((double)n * c + (double)c * (c + 1)) * u;
+    const int tpb = c < 1024 ? ((c + 31) / 32 * 32) : 1024;
+    // pass 1: X -> Q (shifted)
+    CM_TRY(gram(X, ldx, c, X, ldx, c, n, G, part, pcap, sm_count, s));
+    k_chol<<<1, 1024, 0, s>>>(G, c, shift_coef, R1, flag);
+    CM_LAUNCH();
+    k_trinv<<<(c + tpb - 1) / tpb, tpb, 0, s>>>(R1, c, Ri);
+    CM_LAUNCH();
+    CM_TRY(gemm_nn(X, ldx, Ri, c, Q, ldq, n, c, c, s));
+    // pass 2: Q -> T
+    CM_TRY(gram(Q, ldq, c, Q, ldq, c, n, G, part, pcap, sm_count, s));
+    k_chol<<<1, 1024, 0, s>>>(G, c, 0.0, R2, flag);
+    CM_LAUNCH();
+    k_trinv<<<(c + tpb - 1) / tpb, tpb, 0, s>>>(R2, c, Ri);
+    CM_LAUNCH();
+    CM_TRY(gemm_nn(Q, ldq, Ri, c, T, c, n, c, c, s));
+    // pass 3: T -> Q
+    CM_TRY(gram(T, c, c, T, c, c, n, G, part, pcap, sm_count, s));
+    k_chol<<<1, 1024, 0, s>>>(G, c, 0.0, R3, flag);
+    CM_LAUNCH();
+    k_trinv<<<(c + tpb - 1) / tpb, tpb, 0, s>>>(R3, c, Ri);
+    CM_LAUNCH();
+    CM_TRY(gemm_nn(T, c, Ri, c, Q, ldq, n, c, c, s));
+    // R = R3 R2 R1
+    CM_TRY(gemm_nn(R3, c, R2, c, Tm, c, c, c, c, s));
+    CM_TRY(gemm_nn(Tm, c, R1, c, R, c, c, c, c, s));
+    return CMSVD_OK;
+}
+
+// ----------------------------------------------------------------------------- one-sided Jacobi SVD
+// Columns of Xc (column-major c x c, a copy of B) are rotated pairwise until
+// mutually orthogonal (Hestenes). Round-robin ordering; one warp per pair.
+__global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ Bm, int c, double* __restrict__ Xc,
+                                                 double* __restrict__ V, double* __restrict__ sv, int* __restrict__ perm) {
+    __shared__ int rotated;
+    const int t = threadIdx.x, nt = blockDim.x;
+    const int lane = t & 31, warp = t >> 5, nwarps = nt >> 5;
+    for (int e = t; e < c * c; e += nt) {
+        const int i = e / c, j = e % c;          // B row-major (i, j) -> Xc column j, row i
+        Xc[(size_t)j * c + i] = Bm[e];
+        V[e] = (i == j) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    const int np = (c + 1) / 2 * 2;               // players (one dummy when c is odd)
+    const double tol = fmax(1e-15, c * 2.220446049250313e-16);
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        if (t == 0) rotated = 0;
+        __syncthreads();
+        for (int round = 0; round < np - 1; ++round) {
+            for (int k = warp; k < np / 2; k += nwarps) {
+                int p, q;
+                if (k == 0) { p = round; q = np - 1; }
+                else { p = (round + k) % (np - 1); q = (round - k + (np - 1)) % (np - 1); }
+                if (p >= c || q >= c) continue;
+                if (p > q) { int tmp = p; p = q; q = tmp; }
+                double* xp = Xc + (size_t)p * c;
+                double* xq = Xc + (size_t)q * c;
+                double al = 0.0, be = 0.0, ga = 0.0;
+                for (int i = lane; i < c; i += 32) {
+                    const double a = xp[i], b = xq[i];
+                    al = __fma_rn(a, a, al);
+                    be = __fma_rn(b, b, be);
+                    ga = __fma_rn(a, b, ga);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    al += __shfl_xor_sync(0xffffffffu, al, o);
+                    be += __shfl_xor_sync(0xffffffffu, be, o);
+                    ga += __shfl_xor_sync(0xffffffffu, ga, o);
+                }
+                if (fabs(ga) > tol * sqrt(al * be) && al > 0.0 && be > 0.0) {
+                    const double zeta = (be - al) / (2.0 * ga);
+                    const double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                    const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
+                    double* vp = V + (size_t)p * c;
+                    double* vq = V + (size_t)q * c;
+                    for (int i = lane; i < c; i += 32) {
+                        const double a = xp[i], b = xq[i];
+                        xp[i] = cs * a - sn * b;
+                        xq[i] = sn * a + cs * b;
+                        const double va = vp[i], vb = vq[i];
+                        vp[i] = cs * va - sn * vb;
+                        vq[i] = sn * va + cs * vb;
+                    }
+                    if (lane == 0) rotated = 1;
+                }
+            }
+            __syncthreads();
+        }
+        if (!rotated) break;
+        __syncthreads();
+    }
+    // column norms, then descending order (stable) by one thread
+    for (int j = warp; j < c; j += nwarps) {
+        double s2 = 0.0;
+        for (int i = lane; i < c; i += 32) s2 = __fma_rn(Xc[(size_t)j * c + i], Xc[(size_t)j * c + i], s2);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        if (lane == 0) sv[j] = sqrt(s2);
+    }
+    __syncthreads();
+    if (t == 0) {
+        for (int i = 0; i < c; ++i) perm[i] = i;
+        for (int i = 1; i < c; ++i) {
+            const int key = perm[i];
+            int j = i - 1;
+            while (j >= 0 && sv[perm[j]] < sv[key]) { perm[j + 1] = perm[j]; --j; }
+            perm[j + 1] = key;
+        }
+    }
+}
+
+int jacobi_svd(const double* Bm, int c, double* Xc, double* V, double* sv, int* perm, cudaStream_t s) {
+    k_jacobi<<<1, 1024, 0, s>>>(Bm, c, Xc, V, sv, perm);
+    CM_LAUNCH();
+    return CMSVD_OK;
+}
+
+}  // namespace cmsvd

@@ -1,0 +1,144 @@
+// Internal declarations shared by the CUDA translation units of libcmsvd.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include <cstring>
+#include "cmsvd.h"
+
+namespace cmsvd {
+
+// ----------------------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define CM_CUDA(call)                                                              \
+    do {                                                                           \
+        cudaError_t e__ = (call);                                                  \
+        if (e__ != cudaSuccess) return ::cmsvd::cuda_fail(e__, #call, __FILE__, __LINE__); \
+    } while (0)
+#define CM_LAUNCH() CM_CUDA(cudaGetLastError())
+#define CM_TRY(expr)                                                               \
+    do {                                                                           \
+        int s__ = (expr);                                                          \
+        if (s__ != CMSVD_OK) return s__;                                           \
+    } while (0)
+
+// ----------------------------------------------------------------------------- objects
+struct Csr {
+    int64_t m = 0, n = 0, nnz = 0;
+    int64_t* rowptr = nullptr;   // device, m+1
+    int32_t* colidx = nullptr;   // device, nnz
+    double* vals = nullptr;      // device, nnz
+};
+
+struct Components {             // connected components of the column graph (A^T A)
+    bool ready = false;
+    int64_t count = 0;
+    int64_t max_size = 0;
+    // columns grouped by component, components grouped by size (device)
+    int64_t n_groups = 0;
+    int32_t* group_size = nullptr;      // host copy [n_groups]
+    int64_t* group_count = nullptr;     // host [n_groups]
+    int64_t* group_col_off = nullptr;   // host [n_groups] offset into cols[]
+    int32_t* cols = nullptr;            // device [n], columns ordered by (group, component, local)
+    int64_t* comp_row_ptr = nullptr;    // device [count+1], rows of each component (CSR rows of A)
+    int32_t* comp_rows = nullptr;       // device [rows with entries]
+    int64_t* comp_first = nullptr;      // host [count+1] first column slot of each component in cols[]
+    int64_t* comp_first_dev = nullptr;  // device copy
+    int32_t* col_local = nullptr;       // device [n], local index of a column inside its component
+};
+
+}  // namespace cmsvd
+
+struct cmsvd_context {
+    int device = 0;
+    cudaStream_t user = nullptr;       // borrowed
+    cudaStream_t s = nullptr;          // owned, non-blocking: all library work runs here
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    int sm_count = 0;
+    int* pinned = nullptr;             // host-pinned flags for polling
+};
+
+struct cmsvd_matrix {
+    cmsvd_context* ctx = nullptr;
+    cmsvd::Csr A, At;
+    double norm_est = 0.0;             // cached ||A||_2 estimate (0 = not yet)
+    cmsvd::Components comp;
+};
+
+struct cmsvd_result {
+    int64_t m = 0, n = 0, t = 0;
+    cmsvd_context* ctx = nullptr;
+    double* sigma = nullptr;   // device pointers into the caller workspace
+    double* U = nullptr;       // m x t column-major
+    double* V = nullptr;       // n x t column-major
+    double* res_u = nullptr;
+    double* res_v = nullptr;
+    double* tau = nullptr;
+    cmsvd_stats stats{};
+};
+
+namespace cmsvd {
+
+// ----------------------------------------------------------------------------- workspace arena
+// Bump allocator over the caller's workspace. With base == nullptr it only
+// measures, so the size query and the solve run the same allocation sequence.
+struct Arena {
+    char* base = nullptr;
+    size_t off = 0, cap = 0;
+    template <typename T>
+    T* take(size_t count) {
+        off = (off + 255) & ~size_t(255);
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += count * sizeof(T);
+        return p;
+    }
+    bool fits() const { return base == nullptr || off <= cap; }
+};
+
+// ----------------------------------------------------------------------------- launchers (csr.cu)
+int csr_upload_validate(cmsvd_context* ctx, int64_t m, int64_t n, int64_t nnz, const int64_t* rowptr,
+                        const int32_t* colidx, const double* vals, int where, Csr* out);
+int csr_transpose(cmsvd_context* ctx, const Csr& A, Csr* At);
+void csr_free(Csr* A);
+// Y (rows x L, ldy) = A X (X: ncols x L, ldx); optional per-column scale of the result.
+int spmm(const Csr& A, int L, const double* X, int64_t ldx, double* Y, int64_t ldy, cudaStream_t s);
+int components_build(cmsvd_matrix* M);
+void components_free(Components* c);
+
+// ----------------------------------------------------------------------------- quadrature (krylov.cu)
+struct QuadParams { double a, b, alpha; int N, variant; };
+// quad: device array of 3*J double2 = (shift, weight, scaled) per point j.
+int quadrature_device(const QuadParams& q, double2* quad, cudaStream_t s);
+
+// ----------------------------------------------------------------------------- filter solves
+// S (n x L(M+1), ld = L(M+1)) = 2 Re sum_j w_j scaled_j^k (s_j I - A^T A)^{-1} X  for k = 0..Mk-1
+struct SolveOut { int64_t iters = 0; int converged = 1; int breakdown = 0; double lambda_max = 0.0; };
+size_t krylov_workspace(const cmsvd_matrix* A, const cmsvd_params* p);
+int krylov_moments(cmsvd_matrix* A, const cmsvd_params* p, const double2* quad, int Mk,
+                   const double* X, int64_t ldx, double* S, int64_t lds, Arena& ws, SolveOut* out);
+size_t direct_workspace(const cmsvd_matrix* A, const cmsvd_params* p);
+int direct_moments(cmsvd_matrix* A, const cmsvd_params* p, const double2* quad, int Mk,
+                   const double* X, int64_t ldx, double* S, int64_t lds, Arena& ws);
+int norm_estimate(cmsvd_matrix* A, Arena& ws, double* norm_out);
+
+// ----------------------------------------------------------------------------- dense (dense.cu)
+// G (c1 x c2, row-major) = X^T Y, X: n x c1 (ldx), Y: n x c2 (ldy). Deterministic.
+int gram(const double* X, int64_t ldx, int c1, const double* Y, int64_t ldy, int c2, int64_t n,
+         double* G, double* partials, size_t partials_cap, int sm_count, cudaStream_t s);
+size_t gram_partials_size(int c1, int c2, int64_t n, int sm_count);
+// Z (n x c2, ldz) = X (n x c1, ldx) * W (c1 x c2, ldw)
+int gemm_nn(const double* X, int64_t ldx, const double* W, int64_t ldw, double* Z, int64_t ldz,
+            int64_t n, int c1, int c2, cudaStream_t s);
+// Shifted CholeskyQR3 of X (n x c, ldx): Q (n x c, ldq) and R (c x c) with X = Q R.
+// scratch must hold cholqr_scratch(c, n) doubles. flag: device int set on a bad pivot.
+size_t cholqr_scratch(int c, int64_t n, int sm_count);
+int cholqr3(const double* X, int64_t ldx, int64_t n, int c, double* Q, int64_t ldq, double* R,
+            double* scratch, int* flag, int sm_count, cudaStream_t s);
+// One-sided Jacobi SVD of the c x c row-major matrix Bm: on exit Xc holds the
+// rotated columns (column-major c x c), V the right singular vectors
+// (column-major), sv the column norms; then sorted descending with perm.
+int jacobi_svd(const double* Bm, int c, double* Xc, double* V, double* sv, int* perm, cudaStream_t s);
+
+}  // namespace cmsvd

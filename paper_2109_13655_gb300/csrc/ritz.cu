@@ -1,0 +1,295 @@
+// Rayleigh-Ritz extraction, Alg. 1 / Alg. 2 steps 3-5:
+//   step 3  S^ = Q_S R_S (shifted CholeskyQR3), R_S = P_R Sigma_S W_R^T (Jacobi),
+//           keep sigma_S,i > delta sigma_S,1; V~ = U_S1 = Q_S P_R(:, 1:r)   (Eq. low-rank)
+//   step 4  A V~ = U~ B (shifted CholeskyQR3)                                (Eq. avub)
+//   step 5  B = P Phi Q^T (Jacobi); candidates phi_i in [a, b] that pass the
+//           spurious test tau_i = q^T q / q^T Sigma_S1^{-1} q (Sec. 3.4.2);
+//           u = U~ p, v = V~ q; exact residuals ||A^T u - phi v||, ||A v - phi u||
+//           (Sec. 3.4.1); keep residual <= tol_triplet; ascending order; signs.
+#include "internal.cuh"
+
+namespace cmsvd {
+
+int cholqr3(const double*, int64_t, int64_t, int, double*, int64_t, double*, double*, int*, int, cudaStream_t);
+
+// ---- step 3: sorted sigma_S, rank r, and the c x r block that maps Q_S to U_S1
+__global__ void k_truncate(const double* __restrict__ Xc, const double* __restrict__ sv, const int* __restrict__ perm, int c,
+                           double delta, double* __restrict__ sS, double* __restrict__ Wsel, int* __restrict__ r_out) {
+    __shared__ int r;
+    const int t = threadIdx.x;
+    if (t == 0) {
+        const double s1 = sv[perm[0]];
+        int k = 0;
+        while (k < c && sv[perm[k]] > delta * s1) ++k;
+        r = k;
+        *r_out = k;
+    }
+    __syncthreads();
+    for (int i = t; i < c; i += blockDim.x) sS[i] = sv[perm[i]];
+    for (int e = t; e < c * r; e += blockDim.x) {
+        const int k = e / r, i = e % r;                  // Wsel[k][i] = (left vector i)_k
+        Wsel[e] = Xc[(size_t)perm[i] * c + k] / sv[perm[i]];
+    }
+}
+
+// ---- step 5: candidate selection in descending phi order
+__global__ void k_select(const double* __restrict__ Xb, const double* __restrict__ Vb, const double* __restrict__ svb,
+                         const int* __restrict__ perm, int r, const double* __restrict__ sS, double a, double b,
+                         double eps_tau, double* __restrict__ Pc, double* __restrict__ Qc, double* __restrict__ phic,
+                         double* __restrict__ tauc, int* __restrict__ counts, int* __restrict__ cand) {
+    __shared__ int nc;
+    const int t = threadIdx.x;
+    if (t == 0) {
+        int k = 0, inside = 0;
+        for (int ii = 0; ii < r; ++ii) {
+            const int j = perm[ii];
+            const double phi = svb[j];
+            if (!(phi >= a && phi <= b)) continue;
+            ++inside;
+            double num = 0.0, den = 0.0;
+            for (int i = 0; i < r; ++i) {
+                const double q = Vb[(size_t)j * r + i];
+                num += q * q;
+                den += q * q / sS[i];
+            }
+            const double tau = num / den / sS[0];
+            if (!(tau >= eps_tau)) continue;
+            cand[k] = j;
+            phic[k] = phi;
+            tauc[k] = tau;
+            ++k;
+        }
+        nc = k;
+        counts[0] = k;
+        counts[1] = inside;
+    }
+    __syncthreads();
+    const int k = nc;
+    for (int e = t; e < r * k; e += blockDim.x) {
+        const int i = e / k, c = e % k;                  // row-major r x k
+        const int j = cand[c];
+        Pc[e] = Xb[(size_t)j * r + i] / svb[j];
+        Qc[e] = Vb[(size_t)j * r + i];
+    }
+}
+
+// ---- column norms of (Z - X diag(phi)) / scale, n x k row-major, deterministic two-stage
+__global__ void k_colnorm_part(const double* __restrict__ Z, const double* __restrict__ X, const double* __restrict__ phi,
+                               int64_t n, int k, double* __restrict__ part) {
+    __shared__ double sh[8][33];
+    const int col = blockIdx.x * 32 + threadIdx.x;
+    const int64_t chunk = (n + gridDim.y - 1) / gridDim.y;
+    const int64_t r0 = (int64_t)blockIdx.y * chunk, r1 = r0 + chunk < n ? r0 + chunk : n;
+    double acc = 0.0;
+    if (col < k) {
+        const double f = phi[col];
+        for (int64_t r = r0 + threadIdx.y; r < r1; r += 8) {
+            const double d = Z[r * k + col] - f * X[r * k + col];
+            acc = __fma_rn(d, d, acc);
+        }
+    }
+    sh[threadIdx.y][threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.y == 0 && col < k) {
+        double s = 0.0;
+        for (int y = 0; y < 8; ++y) s += sh[y][threadIdx.x];
+        part[(size_t)blockIdx.y * k + col] = s;
+    }
+}
+
+__global__ void k_colnorm_sum(const double* __restrict__ part, int nchunks, int k, double scale, double* __restrict__ out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= k) return;
+    double s = 0.0;
+    for (int i = 0; i < nchunks; ++i) s += part[(size_t)i * k + c];
+    out[c] = sqrt(s) / scale;
+}
+
+static int colnorm_diff(const double* Z, const double* X, const double* phi, int64_t n, int k, double scale, double* part,
+                        int nchunks, double* out, cudaStream_t s) {
+    if (k <= 0) return CMSVD_OK;
+    dim3 grid((k + 31) / 32, nchunks);
+    k_colnorm_part<<<grid, dim3(32, 8), 0, s>>>(Z, X, phi, n, k, part);
+    CM_LAUNCH();
+    k_colnorm_sum<<<(k + 127) / 128, 128, 0, s>>>(part, nchunks, k, scale, out);
+    CM_LAUNCH();
+    return CMSVD_OK;
+}
+
+// ---- final order: keep res_u <= tol, ascending phi (stable), one thread
+__global__ void k_final_order(const double* __restrict__ phic, const double* __restrict__ resu, int k, double tol,
+                              int* __restrict__ order, int* __restrict__ count) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int t = 0;
+    for (int c = k - 1; c >= 0; --c)            // candidates are in descending phi order
+        if (resu[c] <= tol) order[t++] = c;
+    // already ascending except for ties; stable insertion sort on phi to be safe
+    for (int i = 1; i < t; ++i) {
+        const int key = order[i];
+        int j = i - 1;
+        while (j >= 0 && phic[order[j]] > phic[key]) { order[j + 1] = order[j]; --j; }
+        order[j + 1] = key;
+    }
+    *count = t;
+}
+
+// ---- output copy: one block per returned triplet; sign from the largest |v| entry (first on ties)
+__global__ void k_final_copy(const double* __restrict__ uh, const double* __restrict__ vh, int64_t m, int64_t n, int k,
+                             const int* __restrict__ order, const double* __restrict__ phic, const double* __restrict__ tauc,
+                             const double* __restrict__ resu, const double* __restrict__ resv, double* __restrict__ U,
+                             double* __restrict__ V, double* __restrict__ sigma, double* __restrict__ ru,
+                             double* __restrict__ rv, double* __restrict__ tau) {
+    __shared__ double bv[256];
+    __shared__ int64_t bi[256];
+    const int c = blockIdx.x, src = order[c], t = threadIdx.x;
+    double best = -1.0;
+    int64_t bidx = 0;
+    for (int64_t i = t; i < n; i += blockDim.x) {
+        const double a = fabs(vh[i * k + src]);
+        if (a > best) { best = a; bidx = i; }
+    }
+    bv[t] = best;
+    bi[t] = bidx;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (t < o) {
+            if (bv[t + o] > bv[t] || (bv[t + o] == bv[t] && bi[t + o] < bi[t])) { bv[t] = bv[t + o]; bi[t] = bi[t + o]; }
+        }
+        __syncthreads();
+    }
+    const double sg = vh[bi[0] * k + src] < 0.0 ? -1.0 : 1.0;
+    for (int64_t i = t; i < n; i += blockDim.x) V[(size_t)c * n + i] = sg * vh[i * k + src];
+    for (int64_t i = t; i < m; i += blockDim.x) U[(size_t)c * m + i] = sg * uh[i * k + src];
+    if (t == 0) {
+        sigma[c] = phic[src];
+        ru[c] = resu[src];
+        rv[c] = resv[src];
+        tau[c] = tauc[src];
+    }
+}
+
+// ----------------------------------------------------------------------------- driver
+struct RitzBufs {
+    double *Qs, *chol, *Rs, *Xc, *Vr, *svR, *sS, *Wsel, *Vt, *Y, *Ut, *B, *Xb, *Vb, *svB, *Pc, *Qc, *phic, *tauc, *uh, *vh, *Z,
+        *resu, *resv, *part;
+    int *permR, *permB, *cand, *ints;
+    int nchunks;
+};
+
+static void ritz_alloc(RitzBufs& b, Arena& ws, int64_t m, int64_t n, int c, int sm_count) {
+    const int64_t mx = m > n ? m : n;
+    b.Qs = ws.take<double>((size_t)n * c);
+    b.chol = ws.take<double>(cholqr_scratch(c, mx, sm_count));
+    b.Rs = ws.take<double>((size_t)c * c);
+    b.Xc = ws.take<double>((size_t)c * c);
+    b.Vr = ws.take<double>((size_t)c * c);
+    b.svR = ws.take<double>(c);
+    b.sS = ws.take<double>(c);
+    b.Wsel = ws.take<double>((size_t)c * c);
+    b.Vt = ws.take<double>((size_t)n * c);
+    b.Y = ws.take<double>((size_t)m * c);
+    b.Ut = ws.take<double>((size_t)m * c);
+    b.B = ws.take<double>((size_t)c * c);
+    b.Xb = ws.take<double>((size_t)c * c);
+    b.Vb = ws.take<double>((size_t)c * c);
+    b.svB = ws.take<double>(c);
+    b.Pc = ws.take<double>((size_t)c * c);
+    b.Qc = ws.take<double>((size_t)c * c);
+    b.phic = ws.take<double>(c);
+    b.tauc = ws.take<double>(c);
+    b.uh = ws.take<double>((size_t)m * c);
+    b.vh = ws.take<double>((size_t)n * c);
+    b.Z = ws.take<double>((size_t)mx * c);
+    b.resu = ws.take<double>(c);
+    b.resv = ws.take<double>(c);
+    b.nchunks = sm_count;
+    b.part = ws.take<double>((size_t)b.nchunks * c);
+    b.permR = ws.take<int>(c);
+    b.permB = ws.take<int>(c);
+    b.cand = ws.take<int>(c);
+    b.ints = ws.take<int>(16);
+}
+
+size_t ritz_workspace(int64_t m, int64_t n, int c, int sm_count) {
+    Arena a;
+    RitzBufs b;
+    ritz_alloc(b, a, m, n, c, sm_count);
+    return a.off + 256;
+}
+
+struct RitzOut {
+    double *sigma, *U, *V, *res_u, *res_v, *tau;   // persistent outputs (capacity c)
+};
+
+static int read_ints(cmsvd_context* ctx, const int* dev, int count, int* host) {
+    CM_CUDA(cudaMemcpyAsync(ctx->pinned, dev, sizeof(int) * count, cudaMemcpyDeviceToHost, ctx->s));
+    CM_CUDA(cudaStreamSynchronize(ctx->s));
+    memcpy(host, ctx->pinned, sizeof(int) * count);
+    return CMSVD_OK;
+}
+
+int rayleigh_ritz(cmsvd_matrix* M, const double* S, int64_t lds, int c, double a, double b, const cmsvd_params* p,
+                  double normA, Arena& ws, const RitzOut& out, cmsvd_stats* st, cudaEvent_t* ev) {
+    cmsvd_context* ctx = M->ctx;
+    cudaStream_t s = ctx->s;
+    const int64_t m = M->A.m, n = M->A.n;
+    RitzBufs bf;
+    ritz_alloc(bf, ws, m, n, c, ctx->sm_count);
+    if (!ws.fits()) { set_error("workspace too small"); return CMSVD_WORKSPACE_TOO_SMALL; }
+    int* flag = bf.ints + 8;
+    CM_CUDA(cudaMemsetAsync(bf.ints, 0, sizeof(int) * 16, s));
+    // step 3
+    CM_TRY(cholqr3(S, lds, n, c, bf.Qs, c, bf.Rs, bf.chol, flag, ctx->sm_count, s));
+    CM_TRY(jacobi_svd(bf.Rs, c, bf.Xc, bf.Vr, bf.svR, bf.permR, s));
+    k_truncate<<<1, 256, 0, s>>>(bf.Xc, bf.svR, bf.permR, c, p->delta, bf.sS, bf.Wsel, bf.ints);
+    CM_LAUNCH();
+    int h[4];
+    CM_TRY(read_ints(ctx, bf.ints, 1, h));
+    const int r = h[0];
+    st->rank = r;
+    CM_CUDA(cudaMemcpyAsync(&st->sigma_S1, bf.sS, sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (r <= 0) { st->found = 0; return CMSVD_OK; }
+    CM_TRY(gemm_nn(bf.Qs, c, bf.Wsel, r, bf.Vt, r, n, c, r, s));
+    cudaEventRecord(ev[1], s);
+    // step 4
+    CM_TRY(spmm(M->A, r, bf.Vt, r, bf.Y, r, s));
+    CM_TRY(cholqr3(bf.Y, r, m, r, bf.Ut, r, bf.B, bf.chol, flag, ctx->sm_count, s));
+    cudaEventRecord(ev[2], s);
+    // step 5
+    CM_TRY(jacobi_svd(bf.B, r, bf.Xb, bf.Vb, bf.svB, bf.permB, s));
+    k_select<<<1, 256, 0, s>>>(bf.Xb, bf.Vb, bf.svB, bf.permB, r, bf.sS, a, b, p->eps_tau, bf.Pc, bf.Qc, bf.phic, bf.tauc,
+                               bf.ints + 1, bf.cand);
+    CM_LAUNCH();
+    CM_TRY(read_ints(ctx, bf.ints + 1, 2, h));
+    const int k = h[0];
+    st->in_interval = h[1];
+    int t = 0;
+    if (k > 0) {
+        CM_TRY(gemm_nn(bf.Ut, r, bf.Pc, k, bf.uh, k, m, r, k, s));
+        CM_TRY(gemm_nn(bf.Vt, r, bf.Qc, k, bf.vh, k, n, r, k, s));
+        CM_TRY(spmm(M->At, k, bf.uh, k, bf.Z, k, s));
+        CM_TRY(colnorm_diff(bf.Z, bf.vh, bf.phic, n, k, normA, bf.part, bf.nchunks, bf.resu, s));
+        CM_TRY(spmm(M->A, k, bf.vh, k, bf.Z, k, s));
+        CM_TRY(colnorm_diff(bf.Z, bf.uh, bf.phic, m, k, normA, bf.part, bf.nchunks, bf.resv, s));
+        k_final_order<<<1, 32, 0, s>>>(bf.phic, bf.resu, k, p->tol_triplet, bf.cand + 0, bf.ints + 4);
+        CM_LAUNCH();
+        // order overwrites cand (candidates are no longer needed)
+        CM_TRY(read_ints(ctx, bf.ints + 4, 1, h));
+        t = h[0];
+        if (t > 0) {
+            k_final_copy<<<t, 256, 0, s>>>(bf.uh, bf.vh, m, n, k, bf.cand, bf.phic, bf.tauc, bf.resu, bf.resv, out.U, out.V,
+                                           out.sigma, out.res_u, out.res_v, out.tau);
+            CM_LAUNCH();
+        }
+    }
+    cudaEventRecord(ev[3], s);
+    int hf[1];
+    CM_TRY(read_ints(ctx, flag, 1, hf));
+    st->found = t;
+    if (hf[0]) {
+        set_error("CholeskyQR met a non-positive pivot (numerically rank-deficient block)");
+    }
+    return CMSVD_OK;
+}
+
+}  // namespace cmsvd

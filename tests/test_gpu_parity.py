@@ -1,0 +1,281 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances (floating point, FP64 everywhere):
+* SpMM: same per-row summation order as a sequential CSR loop; allowed
+  difference 1e-14 relative to sum |a_ij| |x_j| (fused vs separate rounding).
+* quadrature: 1e-15 relative.
+* moment block S^: 1e-9 relative to max |S| for the Krylov solver (its
+  solves stop at relative residual tol_solve = 1e-12 and the block is
+  amplified by at most 1 / min Im s_j), 1e-12 for the direct solver.
+* triplets: count exact; sigma relative error <= 1e-10; residuals
+  ||A^T u - sigma v|| / ||A||_2 <= 1e-10; vectors match the oracle's up to the
+  common sign rule within 1e-7 (singular vectors are determined to
+  residual / gap).
+"""
+import numpy as np
+import pytest
+
+from oracle import cmsvd_oracle as O
+from paper_2109_13655_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2109_13655_gb300 import binding
+    return binding
+
+
+@pytest.fixture(scope="module")
+def ctx(B):
+    c = B.Context()
+    yield c
+    c.close()
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def ragged_sparse(m, n, seed):
+    """Rows with 0..17 nonzeros at random columns (empty rows included)."""
+    rng = np.random.default_rng(seed)
+    rows, cols = [], []
+    for i in range(m):
+        k = int(rng.integers(0, 18))
+        c = np.sort(rng.choice(n, size=min(k, n), replace=False))
+        rows += [i] * c.size
+        cols += list(c)
+    return synth.csr_from_coo(m, n, rows, cols, rng.standard_normal(len(rows)))
+
+
+# ----------------------------------------------------------------------------- SpMM (row a3)
+@pytest.mark.parametrize("L", [1, 5, 16, 20, 32, 33, 64, 257])
+def test_spmm_parity(B, ctx, L):
+    A = ragged_sparse(777, 301, seed=L)
+    M = B.Matrix.from_csr(ctx, A)
+    X = np.random.default_rng(1).standard_normal((301, L))
+    Y = M.spmm(dev(X)).cpu().numpy()
+    Ad = A.to_dense()
+    ref = Ad @ X
+    scale = np.abs(Ad) @ np.abs(X) + 1e-300
+    assert np.max(np.abs(Y - ref) / scale) < 1e-14
+    Xt = np.random.default_rng(2).standard_normal((777, L))
+    Yt = M.spmm(dev(Xt), transpose=True).cpu().numpy()
+    assert np.max(np.abs(Yt - Ad.T @ Xt) / (np.abs(Ad.T) @ np.abs(Xt) + 1e-300)) < 1e-14
+    M.close()
+
+
+def test_spmm_transpose_deterministic(B, ctx):
+    A = synth.random_sparse(3000, 1000, 12, seed=5)
+    M = B.Matrix.from_csr(ctx, A)
+    X = dev(np.random.default_rng(3).standard_normal((3000, 16)))
+    y1 = M.spmm(X, transpose=True)
+    y2 = M.spmm(X, transpose=True)
+    assert torch.equal(y1, y2)
+    M.close()
+
+
+# ----------------------------------------------------------------------------- quadrature (row a1)
+@pytest.mark.parametrize("variant", ["linear", "nt"])
+@pytest.mark.parametrize("N", [2, 16, 32, 128])
+def test_quadrature_parity(B, ctx, variant, N):
+    a, b = 0.37, 1.9
+    sh, w, sc = B.cmsvd_quadrature(ctx.handle, a, b, N, variant, 0.1)
+    q = O.quadrature(a, b, N, variant, 0.1)
+    for x, y in ((sh, q.shift), (w, q.weight), (sc, q.scaled)):
+        assert np.max(np.abs(x - y) / np.abs(y)) < 1e-14
+
+
+# ----------------------------------------------------------------------------- moments (rows a3-a6)
+@pytest.mark.parametrize("variant,ell", [("linear", 1), ("nt", 1), ("linear", 2)])
+def test_moments_krylov_vs_oracle(B, ctx, variant, ell):
+    A = synth.random_sparse(400, 200, 8, seed=11)
+    s = np.linalg.svd(A.to_dense(), compute_uv=False)
+    a, b, _ = synth.window_interval(s, 60, 6)
+    N, L, Mm = 16, 8, 4
+    Vin = synth.gaussian_block(200, L, 12)
+    M = B.Matrix.from_csr(ctx, A)
+    p = B.params(N=N, L=L, M=Mm, ell=ell, variant=variant, solver="krylov")
+    S, status, st = M.moments(a, b, p, dev(Vin))
+    assert status == B.OK and st["converged"] == 1
+    ref = O.moments(O.ShiftedSolver(A), O.quadrature(a, b, N, variant), Vin, Mm, ell=ell, extra=1)
+    S = S.cpu().numpy()
+    assert np.max(np.abs(S - ref)) <= 1e-9 * np.max(np.abs(ref))
+    M.close()
+
+
+@pytest.mark.parametrize("variant,ell", [("linear", 1), ("nt", 1), ("nt", 2)])
+def test_moments_direct_vs_oracle(B, ctx, variant, ell):
+    bp = synth.block_permuted(300, 8, 4, seed=21)
+    sig = bp.sigmas_desc()
+    a, b, _ = synth.window_interval(sig, 500, 12, min_rel_gap=1e-6, max_shift=10)
+    N, L, Mm = 32, 8, 4
+    Vin = synth.gaussian_block(bp.A.n, L, 22)
+    M = B.Matrix.from_csr(ctx, bp.A)
+    p = B.params(N=N, L=L, M=Mm, ell=ell, variant=variant, solver="direct")
+    S, status, st = M.moments(a, b, p, dev(Vin))
+    assert status == B.OK and st["solver_used"] == B.SOLVER_DIRECT
+    ref = O.moments(O.ShiftedSolver(bp.A), O.quadrature(a, b, N, variant), Vin, Mm, ell=ell, extra=1)
+    assert np.max(np.abs(S.cpu().numpy() - ref)) <= 1e-12 * np.max(np.abs(ref))
+    M.close()
+
+
+def test_auto_picks_direct_for_small_components(B, ctx):
+    bp = synth.block_permuted(50, 8, 4, seed=23)
+    M = B.Matrix.from_csr(ctx, bp.A)
+    s = bp.sigmas_desc()
+    a, b, _ = synth.window_interval(s, 50, 5)
+    _, _, st = M.moments(a, b, B.params(N=16, L=4, M=2), dev(synth.gaussian_block(200, 4, 1)))
+    assert st["solver_used"] == B.SOLVER_DIRECT and st["max_component"] == 4
+    M.close()
+
+
+# ----------------------------------------------------------------------------- end to end (rows a1-a9)
+def compare(out, ref, truth=None, vec_tol=1e-7):
+    assert out.sigma.size == ref.sigma.size
+    if truth is not None:
+        assert out.sigma.size == truth.size
+        assert np.max(np.abs(out.sigma - truth) / truth) <= 1e-10
+    assert np.max(np.abs(out.sigma - ref.sigma) / ref.sigma) <= 1e-10
+    assert out.res_u.max() <= 1e-10 and out.res_v.max() <= 1e-10
+    assert np.max(np.abs(out.V - ref.V)) <= vec_tol
+    assert np.max(np.abs(out.U - ref.U)) <= vec_tol
+    assert np.max(np.abs(out.V.T @ out.V - np.eye(out.sigma.size))) <= 1e-10
+
+
+def test_solve_random_sparse_2000x1000(B, ctx):
+    """The 2000 x 1000, 8 nnz/row workload: sigma ranked 400-419, N=16, L=16, M=4."""
+    A = synth.random_sparse(2000, 1000, 8, seed=0)
+    s = np.linalg.svd(A.to_dense(), compute_uv=False)
+    a, b, _ = synth.window_interval(s, 400, 20)
+    Vin = synth.gaussian_block(1000, 16, 1)
+    ref = O.solve_interval(A, a, b, 16, 16, 4, Vin, norm_A=s[0])
+    M = B.Matrix.from_csr(ctx, A)
+    out = M.solve_interval(a, b, B.params(N=16, L=16, M=4), dev(Vin))
+    assert out.status in (B.OK,)
+    assert out.stats["solver_used"] == B.SOLVER_KRYLOV and out.stats["converged"] == 1
+    assert abs(out.stats["norm_A"] - s[0]) <= 1e-8 * s[0]
+    compare(out, ref, truth=s[400:420][::-1])
+    M.close()
+
+
+@pytest.mark.parametrize("which,variant", [(1, "linear"), (1, "nt"), (2, "nt")])
+def test_solve_model_problems(B, ctx, which, variant):
+    Ad, sig = synth.model_problem(which)
+    a, b = (0.8, 1.2) if which == 1 else (10 ** -3.025, 10 ** -1.025)
+    truth = sig[(sig >= a) & (sig <= b)]
+    Vin = synth.gaussian_block(200, 20, 3)
+    ref = O.solve_interval(Ad, a, b, 32, 20, 4, Vin, variant=variant, norm_A=sig.max())
+    A = synth.csr_from_dense(Ad)
+    M = B.Matrix.from_csr(ctx, A)
+    out = M.solve_interval(a, b, B.params(N=32, L=20, M=4, variant=variant, solver="krylov"), dev(Vin))
+    compare(out, ref, truth=truth, vec_tol=1e-6)
+    M.close()
+
+
+def c2_case():
+    bp = synth.block_permuted(25000, 8, 4, seed=2)
+    s = bp.sigmas_desc()
+    a, b, f = synth.window_interval(s, 50000, 200, min_rel_gap=1e-6, max_shift=10)
+    return bp, s, a, b, f
+
+
+def test_solve_block_permuted_200000x100000(B, ctx):
+    """The known-spectrum workload at full size: 25000 permuted 8x4 blocks, 200
+    interior sigma, N=32, L=32, M=8, ell=2 (the launch configuration of bench.py)."""
+    bp, s, a, b, f = c2_case()
+    Vin = synth.gaussian_block(bp.A.n, 32, 3)
+    M = B.Matrix.from_csr(ctx, bp.A)
+    out = M.solve_interval(a, b, B.params(N=32, L=32, M=8, ell=2), dev(Vin))
+    assert out.stats["solver_used"] == B.SOLVER_DIRECT
+    truth = np.sort(s[f:f + 200])
+    ref = O.solve_interval(bp.A, a, b, 32, 32, 8, Vin, ell=2, norm_A=s[0])
+    compare(out, ref, truth=truth)
+    M.close()
+
+
+def test_empty_interval(B, ctx):
+    A = synth.random_sparse(300, 150, 6, seed=41)
+    s = np.linalg.svd(A.to_dense(), compute_uv=False)
+    a, b = 1.05 * s[0], 2.0 * s[0]          # above the spectrum
+    M = B.Matrix.from_csr(ctx, A)
+    out = M.solve_interval(a, b, B.params(N=16, L=4, M=4), dev(synth.gaussian_block(150, 4, 1)))
+    assert out.sigma.size == 0
+    M.close()
+
+
+def test_exterior_interval_and_ragged_L(B, ctx):
+    A = synth.random_sparse(300, 150, 6, seed=43)
+    s = np.linalg.svd(A.to_dense(), compute_uv=False)
+    a, b = 0.5 * (s[6] + s[7]), 1.01 * s[0]
+    Vin = synth.gaussian_block(150, 5, 2)
+    ref = O.solve_interval(A, a, b, 16, 5, 5, Vin, norm_A=s[0])
+    M = B.Matrix.from_csr(ctx, A)
+    out = M.solve_interval(a, b, B.params(N=16, L=5, M=5), dev(Vin))
+    compare(out, ref, truth=s[:7][::-1])
+    M.close()
+
+
+def test_determinism_and_seed_invariance(B, ctx):
+    A = synth.random_sparse(600, 300, 8, seed=51)
+    s = np.linalg.svd(A.to_dense(), compute_uv=False)
+    a, b, _ = synth.window_interval(s, 100, 6)
+    M = B.Matrix.from_csr(ctx, A)
+    p = B.params(N=16, L=8, M=4)
+    V1 = dev(synth.gaussian_block(300, 8, 1))
+    o1 = M.solve_interval(a, b, p, V1)
+    o2 = M.solve_interval(a, b, p, V1)
+    assert np.array_equal(o1.sigma, o2.sigma) and np.array_equal(o1.V, o2.V)
+    o3 = M.solve_interval(a, b, p, dev(synth.gaussian_block(300, 8, 99)))
+    assert o3.sigma.size == o1.sigma.size == 6
+    assert np.max(np.abs(o3.sigma - o1.sigma) / o1.sigma) <= 1e-12
+    M.close()
+
+
+def test_not_converged_status(B, ctx):
+    A = synth.random_sparse(600, 300, 8, seed=51)
+    s = np.linalg.svd(A.to_dense(), compute_uv=False)
+    a, b, _ = synth.window_interval(s, 100, 6)
+    M = B.Matrix.from_csr(ctx, A)
+    out = M.solve_interval(a, b, B.params(N=16, L=8, M=4, max_iter=5, solver="krylov"),
+                           dev(synth.gaussian_block(300, 8, 1)))
+    assert out.status == B.NOT_CONVERGED and out.stats["converged"] == 0
+    assert out.stats["krylov_iters"] == 5
+    M.close()
+
+
+def test_invalid_arguments(B, ctx):
+    A = synth.random_sparse(60, 30, 4, seed=1)
+    M = B.Matrix.from_csr(ctx, A)
+    V = dev(synth.gaussian_block(30, 4, 1))
+    for kw, (a, b) in [({}, (2.0, 1.0)), ({"N": 15}, (0.1, 1.0)), ({"M": 16, "N": 16}, (0.1, 1.0)),
+                       ({"variant": "nt"}, (0.0, 1.0)), ({"L": 0}, (0.1, 1.0))]:
+        with pytest.raises(B.CmsvdError) as e:
+            M.solve_interval(a, b, B.params(N=kw.get("N", 16), L=kw.get("L", 4), M=kw.get("M", 2),
+                                            variant=kw.get("variant", "linear")), V)
+        assert e.value.status == B.INVALID_ARG
+    M.close()
+
+
+def test_invalid_matrix_rejected(B, ctx):
+    rowptr = np.array([0, 2, 3], dtype=np.int64)
+    bad_cols = [np.array([0, 5, 1], dtype=np.int32),    # column out of range
+                np.array([1, 0, 1], dtype=np.int32),    # unsorted row
+                np.array([1, 1, 0], dtype=np.int32)]    # duplicate
+    for cols in bad_cols:
+        with pytest.raises(B.CmsvdError) as e:
+            B.cmsvd_csr_create(ctx.handle, 2, 3, rowptr, cols, np.ones(3))
+        assert e.value.status == B.INVALID_MATRIX
+    with pytest.raises(B.CmsvdError) as e:
+        B.cmsvd_csr_create(ctx.handle, 2, 3, rowptr, np.array([0, 1, 2], dtype=np.int32),
+                           np.array([1.0, np.nan, 1.0]))
+    assert e.value.status == B.INVALID_MATRIX
+    with pytest.raises(B.CmsvdError) as e:
+        B.cmsvd_csr_create(ctx.handle, 2, 3, np.array([0, 2, 1], dtype=np.int64),   # rowptr not monotone
+                           np.array([0], dtype=np.int32), np.ones(1))
+    assert e.value.status == B.INVALID_MATRIX
