@@ -77,7 +77,20 @@ typedef struct cmsvd_params {
     double norm_A;        /* ||A||_2 if known; <= 0 lets the library estimate it by Lanczos */
     int32_t check_every;  /* Krylov iterations between host convergence checks (default 48) */
     int32_t direct_max_block; /* AUTO picks DIRECT when the largest component has at most this many columns (default 32) */
+    int32_t profile;      /* 1: time every kernel class with CUDA events and fill the prof_* statistics (default 0) */
 } cmsvd_params;
+
+/* Kernel classes of the prof_* statistics (index into the arrays). */
+enum {
+    CMSVD_PROF_SPMM = 0,        /* CSR SpMM with A or A^T outside the Krylov loop */
+    CMSVD_PROF_KRYLOV = 1,      /* Lanczos passes (graph launches: SpMMs + vector kernels) */
+    CMSVD_PROF_DIRECT = 2,      /* per-component direct solve + moments */
+    CMSVD_PROF_GRAM = 3,        /* X^T Y of tall-skinny blocks */
+    CMSVD_PROF_GEMM = 4,        /* tall-skinny X W */
+    CMSVD_PROF_SMALL = 5,       /* Cholesky, triangular inverse, Jacobi SVD, selection (one CTA) */
+    CMSVD_PROF_OTHER = 6,       /* quadrature, norm estimate, norms, output copies */
+    CMSVD_PROF_CLASSES = 8
+};
 
 /* Per-solve statistics. */
 typedef struct cmsvd_stats {
@@ -96,6 +109,13 @@ typedef struct cmsvd_stats {
     double ms_truncate;       /* step 3 */
     double ms_qr;             /* step 4 */
     double ms_ritz;           /* step 5, selection and residuals */
+    int64_t kernel_launches;  /* kernels launched by this solve (graph nodes included) */
+    /* With params.profile = 1, per kernel class: event-timed GPU ms, launches, and the
+       algorithmic bytes (compulsory DRAM traffic) and FP64 flops of those launches. */
+    double prof_ms[CMSVD_PROF_CLASSES];
+    int64_t prof_launches[CMSVD_PROF_CLASSES];
+    double prof_bytes[CMSVD_PROF_CLASSES];
+    double prof_flops[CMSVD_PROF_CLASSES];
 } cmsvd_stats;
 
 typedef struct cmsvd_context cmsvd_context;

@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import weakref
 from dataclasses import dataclass
 
 import numpy as np
@@ -29,7 +30,10 @@ class cmsvd_params(C.Structure):
                 ("delta", C.c_double), ("eps_tau", C.c_double), ("alpha", C.c_double),
                 ("variant", C.c_int32), ("solver", C.c_int32), ("precision", C.c_int32),
                 ("max_iter", C.c_int32), ("tol_solve", C.c_double), ("tol_triplet", C.c_double),
-                ("norm_A", C.c_double), ("check_every", C.c_int32), ("direct_max_block", C.c_int32)]
+                ("norm_A", C.c_double), ("check_every", C.c_int32), ("direct_max_block", C.c_int32),
+                ("profile", C.c_int32)]
+
+PROFILE_CLASSES = ("spmm", "krylov", "direct", "gram", "gemm", "small_dense", "other", "unused")
 
 
 class cmsvd_stats(C.Structure):
@@ -38,10 +42,16 @@ class cmsvd_stats(C.Structure):
                 ("solver_used", C.c_int32), ("converged", C.c_int32),
                 ("norm_A", C.c_double), ("sigma_S1", C.c_double), ("max_res_u", C.c_double),
                 ("max_res_v", C.c_double), ("ms_solve", C.c_double), ("ms_truncate", C.c_double),
-                ("ms_qr", C.c_double), ("ms_ritz", C.c_double)]
+                ("ms_qr", C.c_double), ("ms_ritz", C.c_double), ("kernel_launches", C.c_int64),
+                ("prof_ms", C.c_double * 8), ("prof_launches", C.c_int64 * 8), ("prof_bytes", C.c_double * 8),
+                ("prof_flops", C.c_double * 8)]
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            d[k] = list(v) if k.startswith("prof_") else v
+        return d
 
 
 _P = C.c_void_p
@@ -242,9 +252,13 @@ class Context:
             stream = torch.cuda.current_stream()
         self.stream = stream
         self.handle = cmsvd_context_create(stream.cuda_stream)
+        self._matrices = weakref.WeakSet()
 
     def close(self):
+        """Destroy the context; matrices created on it are destroyed first."""
         if self.handle:
+            for M in list(self._matrices):
+                M.close()
             cmsvd_context_destroy(self.handle)
             self.handle = 0
 
@@ -259,18 +273,21 @@ class Matrix:
     """A CSR matrix resident on the device (library-owned copy)."""
 
     def __init__(self, ctx: Context, m: int, n: int, rowptr, colidx, vals):
+        if not ctx.handle:
+            raise RuntimeError("context is closed")
         self.ctx = ctx
         self.m, self.n = m, n
         self.handle = cmsvd_csr_create(ctx.handle, m, n, rowptr, colidx, vals)
+        ctx._matrices.add(self)
 
     @classmethod
     def from_csr(cls, ctx: Context, A) -> "Matrix":
         return cls(ctx, A.m, A.n, A.rowptr, A.colidx, A.vals)
 
     def close(self):
-        if self.handle:
+        if self.handle and self.ctx.handle:
             cmsvd_csr_destroy(self.handle)
-            self.handle = 0
+        self.handle = 0
 
     def __del__(self):
         try:

@@ -193,6 +193,7 @@ int cmsvd_params_default(cmsvd_params* p) {
     p->norm_A = 0.0;
     p->check_every = 48;
     p->direct_max_block = 32;
+    p->profile = 0;
     return CMSVD_OK;
 }
 
@@ -330,6 +331,7 @@ int cmsvd_moments(cmsvd_matrix* A, double a, double b, const cmsvd_params* p, co
     if (ws_bytes < need) { set_error("workspace %zu < %zu bytes", ws_bytes, need); return CMSVD_WORKSPACE_TOO_SMALL; }
     cmsvd_context* ctx = A->ctx;
     CM_TRY(enter(ctx));
+    prof_reset(p->profile != 0);
     Arena ws;
     ws.base = (char*)workspace;
     ws.cap = ws_bytes;
@@ -341,6 +343,7 @@ int cmsvd_moments(cmsvd_matrix* A, double a, double b, const cmsvd_params* p, co
     const size_t bytes = sizeof(double) * A->A.n * p->L * (p->M + 1);
     CM_CUDA(cudaMemcpyAsync(S_out, pl.S, bytes, cudaMemcpyDeviceToDevice, ctx->s));
     CM_CUDA(cudaStreamSynchronize(ctx->s));
+    prof_collect(&st);
     if (stats) *stats = st;
     CM_TRY(leave(ctx));
     return status;
@@ -359,6 +362,7 @@ int cmsvd_solve_interval(cmsvd_matrix* A, double a, double b, const cmsvd_params
     CM_TRY(enter(ctx));
     Events ev;
     CM_TRY(ev.make());
+    prof_reset(p->profile != 0);
     Arena ws;
     ws.base = (char*)workspace;
     ws.cap = ws_bytes;
@@ -375,6 +379,7 @@ int cmsvd_solve_interval(cmsvd_matrix* A, double a, double b, const cmsvd_params
     const int c = p->L * p->M;
     CM_TRY(rayleigh_ritz(A, pl.S, (int64_t)p->L * (p->M + 1), c, a, b, p, normA, ws, pl.out, &st, ev.e));
     CM_CUDA(cudaStreamSynchronize(ctx->s));
+    prof_collect(&st);
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, ev.e[0], ev.e[4]) == cudaSuccess) st.ms_solve = ms;
     if (cudaEventElapsedTime(&ms, ev.e[4], ev.e[1]) == cudaSuccess) st.ms_truncate = ms;

@@ -21,6 +21,60 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
     return e == cudaErrorMemoryAllocation ? CMSVD_OUT_OF_MEMORY : CMSVD_CUDA_ERROR;
 }
 
+// ----------------------------------------------------------------------------- profiler
+Profiler& prof() {
+    static thread_local Profiler p;
+    return p;
+}
+
+void prof_reset(bool timing) {
+    Profiler& p = prof();
+    for (int i = 0; i < p.nrec; ++i) {
+        cudaEventDestroy(p.recs[i].e0);
+        cudaEventDestroy(p.recs[i].e1);
+    }
+    p.nrec = 0;
+    p.launches = 0;
+    p.captured = 0;
+    p.capture_depth = 0;
+    p.timing = timing;
+}
+
+ProfScope::ProfScope(int cls, cudaStream_t s, double bytes, double flops, int64_t launches) {
+    Profiler& p = prof();
+    if (!p.timing || p.capture_depth > 0 || p.nrec >= 4096) return;
+    Profiler::Rec& r = p.recs[p.nrec];
+    if (cudaEventCreate(&r.e0) != cudaSuccess) return;
+    if (cudaEventCreate(&r.e1) != cudaSuccess) { cudaEventDestroy(r.e0); return; }
+    r.cls = cls;
+    r.bytes = bytes;
+    r.flops = flops;
+    r.launches = launches;
+    cudaEventRecord(r.e0, s);
+    idx = p.nrec++;
+    stream_ = s;
+}
+
+ProfScope::~ProfScope() {
+    if (idx >= 0) cudaEventRecord(prof().recs[idx].e1, stream_);
+}
+
+void prof_collect(cmsvd_stats* st) {
+    Profiler& p = prof();
+    st->kernel_launches = p.launches;
+    for (int i = 0; i < p.nrec; ++i) {
+        const Profiler::Rec& r = p.recs[i];
+        float ms = 0.f;
+        if (cudaEventSynchronize(r.e1) == cudaSuccess && cudaEventElapsedTime(&ms, r.e0, r.e1) == cudaSuccess) {
+            st->prof_ms[r.cls] += ms;
+            st->prof_launches[r.cls] += r.launches;
+            st->prof_bytes[r.cls] += r.bytes;
+            st->prof_flops[r.cls] += r.flops;
+        }
+    }
+    prof_reset(false);
+}
+
 static int grid_for(int64_t work, int per_block, int cap) {
     int64_t g = (work + per_block - 1) / per_block;
     if (g < 1) g = 1;
@@ -239,6 +293,8 @@ __global__ void __launch_bounds__(256) k_spmm(const int64_t* __restrict__ rowptr
 
 int spmm(const Csr& A, int L, const double* X, int64_t ldx, double* Y, int64_t ldy, cudaStream_t s) {
     if (A.m == 0 || L <= 0) return CMSVD_OK;
+    // compulsory traffic: A (values, indices, row pointers), X once, Y once
+    ProfScope ps(CMSVD_PROF_SPMM, s, 12.0 * A.nnz + 8.0 * (A.m + 1) + 8.0 * L * (A.n + A.m), 2.0 * A.nnz * L);
     int dev_sms = 152;
     if (L <= 8) {
         int rows_per_block = 256 / 8;

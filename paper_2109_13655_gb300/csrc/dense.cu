@@ -89,6 +89,12 @@ size_t gram_partials_size(int c1, int c2, int64_t n, int sm_count) {
     return (size_t)nc * c1 * c2;
 }
 
+// Upper bound of gram_partials_size(c', c', n) over every c' <= c: the chunk
+// count is at most 2 sm / tiles + 1 and c'^2 / tiles <= 64^2.
+size_t gram_partials_cap(int c, int sm_count) {
+    return (size_t)(2 * sm_count + 1) * GT * GT + (size_t)c * c;
+}
+
 int gram(const double* X, int64_t ldx, int c1, const double* Y, int64_t ldy, int c2, int64_t n, double* G,
          double* partials, size_t partials_cap, int sm_count, cudaStream_t s) {
     int nc;
@@ -96,11 +102,14 @@ int gram(const double* X, int64_t ldx, int c1, const double* Y, int64_t ldy, int
     gram_plan(c1, c2, n, sm_count, &nc, &rpc);
     if ((size_t)nc * c1 * c2 > partials_cap) { set_error("gram scratch too small"); return CMSVD_WORKSPACE_TOO_SMALL; }
     dim3 grid((c1 + GT - 1) / GT, (c2 + GT - 1) / GT, nc);
-    k_gram_partial<<<grid, 256, 0, s>>>(X, ldx, c1, Y, ldy, c2, n, rpc, partials);
-    CM_LAUNCH();
     const int64_t cnt = (int64_t)c1 * c2;
-    k_sum_partials<<<(int)((cnt + 255) / 256), 256, 0, s>>>(partials, nc, cnt, G);
-    CM_LAUNCH();
+    {
+        ProfScope ps(CMSVD_PROF_GRAM, s, 8.0 * n * (X == Y ? c1 : c1 + c2) + 8.0 * cnt, 2.0 * n * c1 * c2, 2);
+        k_gram_partial<<<grid, 256, 0, s>>>(X, ldx, c1, Y, ldy, c2, n, rpc, partials);
+        CM_LAUNCH();
+        k_sum_partials<<<(int)((cnt + 255) / 256), 256, 0, s>>>(partials, nc, cnt, G);
+        CM_LAUNCH();
+    }
     return CMSVD_OK;
 }
 
@@ -155,6 +164,7 @@ int gemm_nn(const double* X, int64_t ldx, const double* W, int64_t ldw, double* 
             int c2, cudaStream_t s) {
     if (n <= 0 || c2 <= 0) return CMSVD_OK;
     dim3 grid((c2 + GT - 1) / GT, (unsigned)((n + GT - 1) / GT));
+    ProfScope ps(CMSVD_PROF_GEMM, s, 8.0 * ((double)n * c1 + (double)c1 * c2 + (double)n * c2), 2.0 * n * c1 * c2);
     k_gemm_nn<<<grid, 256, 0, s>>>(X, ldx, W, ldw, Z, ldz, n, c1, c2);
     CM_LAUNCH();
     return CMSVD_OK;
@@ -218,70 +228,25 @@ __global__ void k_trinv(const double* __restrict__ R, int c, double* __restrict_
     }
 }
 
-size_t cholqr_scratch(int c, int64_t n, int sm_count) {
-    return (size_t)n * c + 6 * (size_t)c * c + gram_partials_size(c, c, n, sm_count) + 64;
-}
-
-// Shifted CholeskyQR3: the first pass adds the shift 11 (n c + c (c+1)) u ||X||_F^2 so
-// that it succeeds for numerically rank-deficient X; two plain passes restore
-// orthogonality. X = Q R3 R2 R1.
-int cholqr3(const double* X, int64_t ldx, int64_t n, int c, double* Q, int64_t ldq, double* R, double* scratch,
-            int* flag, int sm_count, cudaStream_t s) {
-    double* T = scratch;
-    double* G = T + (size_t)n * c;
-    double* R1 = G + (size_t)c * c;
-    double* R2 = R1 + (size_t)c * c;
-    double* R3 = R2 + (size_t)c * c;
-    double* Ri = R3 + (size_t)c * c;
-    double* Tm = Ri + (size_t)c * c;
-    double* part = Tm + (size_t)c * c;
-    const size_t pcap = gram_partials_size(c, c, n, sm_count);
-    const double u = 1.1102230246251565e-16;
-    const double shift_coef = 11.0 * ((double)n * c + (double)c * (c + 1)) * u;
-    const int tpb = c < 1024 ? ((c + 31) / 32 * 32) : 1024;
-    // pass 1: X -> Q (shifted)
-    CM_TRY(gram(X, ldx, c, X, ldx, c, n, G, part, pcap, sm_count, s));
-    k_chol<<<1, 1024, 0, s>>>(G, c, shift_coef, R1, flag);
-    CM_LAUNCH();
-    k_trinv<<<(c + tpb - 1) / tpb, tpb, 0, s>>>(R1, c, Ri);
-    CM_LAUNCH();
-    CM_TRY(gemm_nn(X, ldx, Ri, c, Q, ldq, n, c, c, s));
-    // pass 2: Q -> T
-    CM_TRY(gram(Q, ldq, c, Q, ldq, c, n, G, part, pcap, sm_count, s));
-    k_chol<<<1, 1024, 0, s>>>(G, c, 0.0, R2, flag);
-    CM_LAUNCH();
-    k_trinv<<<(c + tpb - 1) / tpb, tpb, 0, s>>>(R2, c, Ri);
-    CM_LAUNCH();
-    CM_TRY(gemm_nn(Q, ldq, Ri, c, T, c, n, c, c, s));
-    // pass 3: T -> Q
-    CM_TRY(gram(T, c, c, T, c, c, n, G, part, pcap, sm_count, s));
-    k_chol<<<1, 1024, 0, s>>>(G, c, 0.0, R3, flag);
-    CM_LAUNCH();
-    k_trinv<<<(c + tpb - 1) / tpb, tpb, 0, s>>>(R3, c, Ri);
-    CM_LAUNCH();
-    CM_TRY(gemm_nn(T, c, Ri, c, Q, ldq, n, c, c, s));
-    // R = R3 R2 R1
-    CM_TRY(gemm_nn(R3, c, R2, c, Tm, c, c, c, c, s));
-    CM_TRY(gemm_nn(Tm, c, R1, c, R, c, c, c, c, s));
-    return CMSVD_OK;
-}
-
 // ----------------------------------------------------------------------------- one-sided Jacobi SVD
-// Columns of Xc (column-major c x c, a copy of B) are rotated pairwise until
-// mutually orthogonal (Hestenes). Round-robin ordering; one warp per pair.
-__global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ Bm, int c, double* __restrict__ Xc,
+// The cols columns (length rows) of Bm (rows x cols, row-major) are copied to Xc
+// (column-major) and rotated pairwise until mutually orthogonal (Hestenes):
+// Bm V = Xc, so sv_j = ||Xc_j|| are the singular values (zero when cols > rows),
+// Xc_j / sv_j the left and V_j the right singular vectors. Round-robin
+// ordering; one warp per pair; perm sorts sv descending (stable).
+__global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ Bm, int rows, int cols, double* __restrict__ Xc,
                                                  double* __restrict__ V, double* __restrict__ sv, int* __restrict__ perm) {
     __shared__ int rotated;
     const int t = threadIdx.x, nt = blockDim.x;
     const int lane = t & 31, warp = t >> 5, nwarps = nt >> 5;
-    for (int e = t; e < c * c; e += nt) {
-        const int i = e / c, j = e % c;          // B row-major (i, j) -> Xc column j, row i
-        Xc[(size_t)j * c + i] = Bm[e];
-        V[e] = (i == j) ? 1.0 : 0.0;
+    for (int e = t; e < rows * cols; e += nt) {
+        const int i = e / cols, j = e % cols;     // Bm (i, j) -> column j, row i
+        Xc[(size_t)j * rows + i] = Bm[e];
     }
+    for (int e = t; e < cols * cols; e += nt) V[e] = (e / cols == e % cols) ? 1.0 : 0.0;
     __syncthreads();
-    const int np = (c + 1) / 2 * 2;               // players (one dummy when c is odd)
-    const double tol = fmax(1e-15, c * 2.220446049250313e-16);
+    const int np = (cols + 1) / 2 * 2;            // players (one dummy when cols is odd)
+    const double tol = fmax(1e-15, rows * 2.220446049250313e-16);
     for (int sweep = 0; sweep < 60; ++sweep) {
         if (t == 0) rotated = 0;
         __syncthreads();
@@ -290,12 +255,12 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ Bm, 
                 int p, q;
                 if (k == 0) { p = round; q = np - 1; }
                 else { p = (round + k) % (np - 1); q = (round - k + (np - 1)) % (np - 1); }
-                if (p >= c || q >= c) continue;
+                if (p >= cols || q >= cols) continue;
                 if (p > q) { int tmp = p; p = q; q = tmp; }
-                double* xp = Xc + (size_t)p * c;
-                double* xq = Xc + (size_t)q * c;
+                double* xp = Xc + (size_t)p * rows;
+                double* xq = Xc + (size_t)q * rows;
                 double al = 0.0, be = 0.0, ga = 0.0;
-                for (int i = lane; i < c; i += 32) {
+                for (int i = lane; i < rows; i += 32) {
                     const double a = xp[i], b = xq[i];
                     al = __fma_rn(a, a, al);
                     be = __fma_rn(b, b, be);
@@ -311,12 +276,14 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ Bm, 
                     const double zeta = (be - al) / (2.0 * ga);
                     const double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
                     const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
-                    double* vp = V + (size_t)p * c;
-                    double* vq = V + (size_t)q * c;
-                    for (int i = lane; i < c; i += 32) {
+                    for (int i = lane; i < rows; i += 32) {
                         const double a = xp[i], b = xq[i];
                         xp[i] = cs * a - sn * b;
                         xq[i] = sn * a + cs * b;
+                    }
+                    double* vp = V + (size_t)p * cols;
+                    double* vq = V + (size_t)q * cols;
+                    for (int i = lane; i < cols; i += 32) {
                         const double va = vp[i], vb = vq[i];
                         vp[i] = cs * va - sn * vb;
                         vq[i] = sn * va + cs * vb;
@@ -329,18 +296,17 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ Bm, 
         if (!rotated) break;
         __syncthreads();
     }
-    // column norms, then descending order (stable) by one thread
-    for (int j = warp; j < c; j += nwarps) {
+    for (int j = warp; j < cols; j += nwarps) {
         double s2 = 0.0;
-        for (int i = lane; i < c; i += 32) s2 = __fma_rn(Xc[(size_t)j * c + i], Xc[(size_t)j * c + i], s2);
+        for (int i = lane; i < rows; i += 32) s2 = __fma_rn(Xc[(size_t)j * rows + i], Xc[(size_t)j * rows + i], s2);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
         if (lane == 0) sv[j] = sqrt(s2);
     }
     __syncthreads();
     if (t == 0) {
-        for (int i = 0; i < c; ++i) perm[i] = i;
-        for (int i = 1; i < c; ++i) {
+        for (int i = 0; i < cols; ++i) perm[i] = i;
+        for (int i = 1; i < cols; ++i) {
             const int key = perm[i];
             int j = i - 1;
             while (j >= 0 && sv[perm[j]] < sv[key]) { perm[j + 1] = perm[j]; --j; }
@@ -349,9 +315,121 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ Bm, 
     }
 }
 
-int jacobi_svd(const double* Bm, int c, double* Xc, double* V, double* sv, int* perm, cudaStream_t s) {
-    k_jacobi<<<1, 1024, 0, s>>>(Bm, c, Xc, V, sv, perm);
+int jacobi_svd(const double* Bm, int rows, int cols, double* Xc, double* V, double* sv, int* perm, cudaStream_t s) {
+    ProfScope ps(CMSVD_PROF_SMALL, s, 16.0 * (rows + cols) * cols, 0.0);
+    k_jacobi<<<1, 1024, 0, s>>>(Bm, rows, cols, Xc, V, sv, perm);
     CM_LAUNCH();
+    return CMSVD_OK;
+}
+
+// ----------------------------------------------------------------------------- deflated orthogonalization
+// Deflation after two shifted passes: with G = Q2^T Q2 = W diag(sv^2) W^T (from the
+// Jacobi SVD of its shifted Cholesky factor), keep the directions with
+// sv_k^2 > keep * sv_max^2; T3 = W_g diag(1/sv_g) (c x c') and R3 = diag(sv_g) W_g^T (c' x c).
+__global__ void k_deflate(const double* __restrict__ V, const double* __restrict__ sv, const int* __restrict__ perm, int c,
+                          double keep, double* __restrict__ T3, double* __restrict__ R3, int* __restrict__ cp_out) {
+    __shared__ int cp;
+    const int t = threadIdx.x;
+    if (t == 0) {
+        const double s0 = sv[perm[0]];
+        int k = 0;
+        while (k < c && sv[perm[k]] * sv[perm[k]] > keep * s0 * s0) ++k;
+        cp = k;
+        *cp_out = k;
+    }
+    __syncthreads();
+    const int k = cp;
+    for (int e = t; e < c * k; e += blockDim.x) {
+        const int i = e / k, g = e % k;               // T3 row-major c x k
+        const int j = perm[g];
+        T3[e] = V[(size_t)j * c + i] / sv[j];
+    }
+    for (int e = t; e < k * c; e += blockDim.x) {
+        const int g = e / c, i = e % c;               // R3 row-major k x c
+        const int j = perm[g];
+        R3[e] = sv[j] * V[(size_t)j * c + i];
+    }
+}
+
+size_t orth_scratch(int c, int64_t n, int sm_count) {
+    return (size_t)n * c + 14 * (size_t)c * c + 2 * (size_t)c + gram_partials_cap(c, sm_count) + 256;
+}
+
+// X (n x c, ldx) = Q R with Q (n x c', ld c') orthonormal and R (c' x c, row-major):
+//   two shifted CholeskyQR passes (shift 11 (n c + c (c+1)) u ||.||_F^2 each) bring
+//   every direction of X whose singular value exceeds ~1e-14 ||X|| to O(1),
+//   deflation drops the rest (rounding noise far below any useful threshold),
+//   two plain CholeskyQR passes restore orthogonality to working precision.
+// *c_out receives c'. scratch: orth_scratch(c, n) doubles; flag: device int.
+int orth_deflate(const double* X, int64_t ldx, int64_t n, int c, double* Q, double* R, int* c_out, double* scratch,
+                 int* flag, int* cp_dev, int* pinned, int sm_count, cudaStream_t s) {
+    double* T = scratch;
+    double* G = T + (size_t)n * c;
+    double* R1 = G + (size_t)c * c;
+    double* R2 = R1 + (size_t)c * c;
+    double* R3 = R2 + (size_t)c * c;
+    double* R4 = R3 + (size_t)c * c;
+    double* R5 = R4 + (size_t)c * c;
+    double* Ri = R5 + (size_t)c * c;
+    double* Rb = Ri + (size_t)c * c;
+    double* Xj = Rb + (size_t)c * c;
+    double* Vj = Xj + (size_t)c * c;
+    double* T3 = Vj + (size_t)c * c;
+    double* M1 = T3 + (size_t)c * c;
+    double* M2 = M1 + (size_t)c * c;
+    double* sv = M2 + (size_t)c * c;
+    int* perm = (int*)(sv + c);
+    double* part = sv + 2 * (size_t)c;
+    const size_t pcap = gram_partials_cap(c, sm_count);
+    const double u = 1.1102230246251565e-16;
+    const double coef = 11.0 * ((double)n * c + (double)c * (c + 1)) * u;
+    auto chol_inv = [&](int cc, double sc, double* Rout) -> int {
+        const int tpb = cc < 1024 ? ((cc + 31) / 32 * 32) : 1024;
+        ProfScope ps(CMSVD_PROF_SMALL, s, 24.0 * cc * cc, 2.0 * cc * cc * cc / 3.0, 2);
+        k_chol<<<1, 1024, 0, s>>>(G, cc, sc, Rout, flag);
+        CM_LAUNCH();
+        k_trinv<<<(cc + tpb - 1) / tpb, tpb, 0, s>>>(Rout, cc, Ri);
+        CM_LAUNCH();
+        return CMSVD_OK;
+    };
+    // two shifted passes: X -> Q (R1), Q -> T (R2)
+    CM_TRY(gram(X, ldx, c, X, ldx, c, n, G, part, pcap, sm_count, s));
+    CM_TRY(chol_inv(c, coef, R1));
+    CM_TRY(gemm_nn(X, ldx, Ri, c, Q, c, n, c, c, s));
+    CM_TRY(gram(Q, c, c, Q, c, c, n, G, part, pcap, sm_count, s));
+    CM_TRY(chol_inv(c, coef, R2));
+    CM_TRY(gemm_nn(Q, c, Ri, c, T, c, n, c, c, s));
+    // deflation
+    CM_TRY(gram(T, c, c, T, c, c, n, G, part, pcap, sm_count, s));
+    {
+        ProfScope ps(CMSVD_PROF_SMALL, s, 24.0 * c * c, 2.0 * c * c * c / 3.0);
+        k_chol<<<1, 1024, 0, s>>>(G, c, coef, Rb, flag);
+        CM_LAUNCH();
+    }
+    CM_TRY(jacobi_svd(Rb, c, c, Xj, Vj, sv, perm, s));
+    {
+        ProfScope ps(CMSVD_PROF_SMALL, s, 24.0 * c * c, 0.0);
+        k_deflate<<<1, 256, 0, s>>>(Vj, sv, perm, c, 1e-10, T3, R3, cp_dev);
+        CM_LAUNCH();
+    }
+    CM_CUDA(cudaMemcpyAsync(pinned, cp_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CM_CUDA(cudaStreamSynchronize(s));
+    const int cp = pinned[0];
+    *c_out = cp;
+    if (cp <= 0) return CMSVD_OK;
+    CM_TRY(gemm_nn(T, c, T3, cp, Q, cp, n, c, cp, s));
+    // two plain passes: Q -> T (R4), T -> Q (R5)
+    CM_TRY(gram(Q, cp, cp, Q, cp, cp, n, G, part, pcap, sm_count, s));
+    CM_TRY(chol_inv(cp, 0.0, R4));
+    CM_TRY(gemm_nn(Q, cp, Ri, cp, T, cp, n, cp, cp, s));
+    CM_TRY(gram(T, cp, cp, T, cp, cp, n, G, part, pcap, sm_count, s));
+    CM_TRY(chol_inv(cp, 0.0, R5));
+    CM_TRY(gemm_nn(T, cp, Ri, cp, Q, cp, n, cp, cp, s));
+    // R = R5 R4 R3 R2 R1
+    CM_TRY(gemm_nn(R2, c, R1, c, M1, c, c, c, c, s));
+    CM_TRY(gemm_nn(R3, c, M1, c, M2, c, cp, c, c, s));
+    CM_TRY(gemm_nn(R4, cp, M2, c, M1, c, cp, cp, c, s));
+    CM_TRY(gemm_nn(R5, cp, M1, c, R, c, cp, cp, c, s));
     return CMSVD_OK;
 }
 

@@ -317,6 +317,17 @@ int direct_moments(cmsvd_matrix* M, const cmsvd_params* p, const double2* quad, 
     a.J = p->N / 2;
     a.Mk = Mk;
     a.ell = p->ell;
+    // compulsory traffic: A once, X once, S written once; FP64 flops of the
+    // per-component work (H_c, Jacobi sweeps estimated at 6, coefficients, P and S)
+    double flops = 0.0;
+    for (int64_t g = 0; g < C.n_groups; ++g) {
+        const double sz = C.group_size[g], cnt = (double)C.group_count[g];
+        flops += cnt * (2.0 * sz * sz * (M->A.m / (double)C.count) + 6.0 * 0.5 * sz * (sz - 1) * 12.0 * sz +
+                        sz * a.J * (12.0 + 8.0 * Mk) + 2.0 * sz * sz * a.L * (1.0 + Mk));
+    }
+    ProfScope ps(CMSVD_PROF_DIRECT, M->ctx->s,
+                 12.0 * M->A.nnz + 8.0 * (M->A.m + 1) + 8.0 * M->A.n * a.L + 8.0 * M->A.n * a.L * Mk, flops,
+                 C.n_groups);
     for (int64_t g = 0; g < C.n_groups; ++g) {
         a.s = C.group_size[g];
         a.comp0 = C.group_col_off[g];

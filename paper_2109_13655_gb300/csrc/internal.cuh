@@ -17,12 +17,43 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
         cudaError_t e__ = (call);                                                  \
         if (e__ != cudaSuccess) return ::cmsvd::cuda_fail(e__, #call, __FILE__, __LINE__); \
     } while (0)
-#define CM_LAUNCH() CM_CUDA(cudaGetLastError())
+#define CM_LAUNCH()               \
+    do {                          \
+        ::cmsvd::note_launch();   \
+        CM_CUDA(cudaGetLastError()); \
+    } while (0)
 #define CM_TRY(expr)                                                               \
     do {                                                                           \
         int s__ = (expr);                                                          \
         if (s__ != CMSVD_OK) return s__;                                           \
     } while (0)
+
+// ----------------------------------------------------------------------------- launch counting / profiling
+// One profiler per host thread, active for the duration of one library call.
+// Launch counting is always on; event timing only when params.profile is set.
+struct Profiler {
+    bool timing = false;
+    int capture_depth = 0;        // > 0 while a CUDA graph is being captured
+    int64_t launches = 0;         // kernels launched (graph nodes added per graph launch)
+    int64_t captured = 0;         // kernels recorded into the graph being captured
+    struct Rec { int cls; cudaEvent_t e0, e1; double bytes, flops; int64_t launches; };
+    Rec recs[4096];
+    int nrec = 0;
+};
+Profiler& prof();
+inline void note_launch() {
+    Profiler& p = prof();
+    if (p.capture_depth > 0) ++p.captured; else ++p.launches;
+}
+// Times the launches issued inside its scope on stream s as one record of class cls.
+struct ProfScope {
+    int idx = -1;
+    cudaStream_t stream_ = nullptr;
+    ProfScope(int cls, cudaStream_t s, double bytes, double flops, int64_t launches = 1);
+    ~ProfScope();
+};
+void prof_reset(bool timing);
+void prof_collect(cmsvd_stats* st);   // synchronizes the recorded events
 
 // ----------------------------------------------------------------------------- objects
 struct Csr {
@@ -128,17 +159,16 @@ int norm_estimate(cmsvd_matrix* A, Arena& ws, double* norm_out);
 int gram(const double* X, int64_t ldx, int c1, const double* Y, int64_t ldy, int c2, int64_t n,
          double* G, double* partials, size_t partials_cap, int sm_count, cudaStream_t s);
 size_t gram_partials_size(int c1, int c2, int64_t n, int sm_count);
+size_t gram_partials_cap(int c, int sm_count);
 // Z (n x c2, ldz) = X (n x c1, ldx) * W (c1 x c2, ldw)
 int gemm_nn(const double* X, int64_t ldx, const double* W, int64_t ldw, double* Z, int64_t ldz,
             int64_t n, int c1, int c2, cudaStream_t s);
-// Shifted CholeskyQR3 of X (n x c, ldx): Q (n x c, ldq) and R (c x c) with X = Q R.
-// scratch must hold cholqr_scratch(c, n) doubles. flag: device int set on a bad pivot.
-size_t cholqr_scratch(int c, int64_t n, int sm_count);
-int cholqr3(const double* X, int64_t ldx, int64_t n, int c, double* Q, int64_t ldq, double* R,
-            double* scratch, int* flag, int sm_count, cudaStream_t s);
-// One-sided Jacobi SVD of the c x c row-major matrix Bm: on exit Xc holds the
-// rotated columns (column-major c x c), V the right singular vectors
-// (column-major), sv the column norms; then sorted descending with perm.
-int jacobi_svd(const double* Bm, int c, double* Xc, double* V, double* sv, int* perm, cudaStream_t s);
+// Deflated orthogonalization X (n x c) = Q (n x c', ld c') R (c' x c); see dense.cu.
+size_t orth_scratch(int c, int64_t n, int sm_count);
+int orth_deflate(const double* X, int64_t ldx, int64_t n, int c, double* Q, double* R, int* c_out, double* scratch,
+                 int* flag, int* cp_dev, int* pinned, int sm_count, cudaStream_t s);
+// One-sided Jacobi SVD of Bm (rows x cols, row-major): Xc (column-major, rows x cols)
+// = Bm V, sv_j = ||Xc_j||, V (cols x cols, column-major), perm sorts sv descending.
+int jacobi_svd(const double* Bm, int rows, int cols, double* Xc, double* V, double* sv, int* perm, cudaStream_t s);
 
 }  // namespace cmsvd

@@ -70,6 +70,7 @@ __global__ void k_quadrature(QuadParams q, double2* quad) {
 }
 
 int quadrature_device(const QuadParams& q, double2* quad, cudaStream_t s) {
+    ProfScope ps(CMSVD_PROF_OTHER, s, 48.0 * (q.N / 2), 0.0);
     k_quadrature<<<1, 64, 0, s>>>(q, quad);
     CM_LAUNCH();
     return CMSVD_OK;
@@ -481,6 +482,9 @@ static int lanczos_run(cmsvd_matrix* M, Lz& z, const double* X, int64_t ldx, dou
     if (chunk > 3 * ((z.max_iter + 2) / 3)) chunk = 3 * ((z.max_iter + 2) / 3);
     cudaGraph_t g = nullptr;
     cudaGraphExec_t ge = nullptr;
+    Profiler& pr = prof();
+    pr.captured = 0;
+    pr.capture_depth++;
     CM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     for (int it = 0; it < chunk; ++it) {
         const int p = it % 3;
@@ -494,13 +498,22 @@ static int lanczos_run(cmsvd_matrix* M, Lz& z, const double* X, int64_t ldx, dou
         k_lz_scale<<<grid, blk, 0, s>>>(z, W);
     }
     cudaError_t ce = cudaStreamEndCapture(s, &g);
+    pr.capture_depth--;
+    const int64_t nodes1 = pr.captured;
     if (ce != cudaSuccess) return cuda_fail(ce, "capture pass 1", __FILE__, __LINE__);
     ce = cudaGraphInstantiate(&ge, g, 0);
     cudaGraphDestroy(g);
     if (ce != cudaSuccess) return cuda_fail(ce, "instantiate pass 1", __FILE__, __LINE__);
     int* h = ctx->pinned;
     int st = CMSVD_OK;
+    // compulsory traffic per Lanczos step: A and A^T once each, X read and Y written by
+    // both SpMMs, and the vector kernels (dot 4, update 3, scale 2 n x L passes)
+    const double nnz = (double)M->A.nnz, mm = (double)M->A.m, nn = (double)M->A.n, LL = z.L;
+    const double step_bytes = 2 * (12.0 * nnz) + 8.0 * (mm + nn + 2) + 16.0 * LL * (mm + nn) + 72.0 * nn * LL;
+    const double step_flops = 4.0 * nnz * LL + 10.0 * nn * LL;
     for (;;) {
+        ProfScope ps(CMSVD_PROF_KRYLOV, s, step_bytes * chunk, step_flops * chunk, nodes1);
+        pr.launches += nodes1;
         ce = cudaGraphLaunch(ge, s);
         if (ce == cudaSuccess) ce = cudaMemcpyAsync(h, z.ctrl, sizeof(int) * C_WORDS, cudaMemcpyDeviceToHost, s);
         if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
@@ -531,6 +544,8 @@ static int lanczos_run(cmsvd_matrix* M, Lz& z, const double* X, int64_t ldx, dou
     CM_LAUNCH();
     int chunk2 = chunk;
     if (chunk2 > 3 * ((Kmax + 2) / 3)) chunk2 = 3 * ((Kmax + 2) / 3);
+    pr.captured = 0;
+    pr.capture_depth++;
     CM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     for (int it = 0; it < chunk2; ++it) {
         const int p = it % 3;
@@ -542,11 +557,18 @@ static int lanczos_run(cmsvd_matrix* M, Lz& z, const double* X, int64_t ldx, dou
         k_lz2_step<<<grid, blk, 0, s>>>(z, Qk, Qp, W, S, lds);
     }
     ce = cudaStreamEndCapture(s, &g);
+    pr.capture_depth--;
+    const int64_t nodes2 = pr.captured;
     if (ce != cudaSuccess) return cuda_fail(ce, "capture pass 2", __FILE__, __LINE__);
     ce = cudaGraphInstantiate(&ge, g, 0);
     cudaGraphDestroy(g);
     if (ce != cudaSuccess) return cuda_fail(ce, "instantiate pass 2", __FILE__, __LINE__);
+    const double step2_bytes = 2 * (12.0 * nnz) + 8.0 * (mm + nn + 2) + 16.0 * LL * (mm + nn) +
+                               8.0 * nn * LL * (4.0 + 2.0 * z.Mk);
+    const double step2_flops = 4.0 * nnz * LL + nn * LL * (6.0 + 2.0 * z.Mk);
     for (int done = 0; done < Kmax; done += chunk2) {
+        ProfScope ps(CMSVD_PROF_KRYLOV, s, step2_bytes * chunk2, step2_flops * chunk2, nodes2);
+        pr.launches += nodes2;
         ce = cudaGraphLaunch(ge, s);
         if (ce != cudaSuccess) break;
     }

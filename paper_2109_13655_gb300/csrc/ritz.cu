@@ -10,31 +10,32 @@
 
 namespace cmsvd {
 
-int cholqr3(const double*, int64_t, int64_t, int, double*, int64_t, double*, double*, int*, int, cudaStream_t);
-
 // ---- step 3: sorted sigma_S, rank r, and the c x r block that maps Q_S to U_S1
+// Xc: column-major rows x c (columns = R_S V, rows = c'); Wsel: rows x r, row-major.
 __global__ void k_truncate(const double* __restrict__ Xc, const double* __restrict__ sv, const int* __restrict__ perm, int c,
-                           double delta, double* __restrict__ sS, double* __restrict__ Wsel, int* __restrict__ r_out) {
+                           int rows, double delta, double* __restrict__ sS, double* __restrict__ Wsel,
+                           int* __restrict__ r_out) {
     __shared__ int r;
     const int t = threadIdx.x;
     if (t == 0) {
         const double s1 = sv[perm[0]];
         int k = 0;
-        while (k < c && sv[perm[k]] > delta * s1) ++k;
+        while (k < c && k < rows && sv[perm[k]] > delta * s1) ++k;
         r = k;
         *r_out = k;
     }
     __syncthreads();
     for (int i = t; i < c; i += blockDim.x) sS[i] = sv[perm[i]];
-    for (int e = t; e < c * r; e += blockDim.x) {
+    for (int e = t; e < rows * r; e += blockDim.x) {
         const int k = e / r, i = e % r;                  // Wsel[k][i] = (left vector i)_k
-        Wsel[e] = Xc[(size_t)perm[i] * c + k] / sv[perm[i]];
+        Wsel[e] = Xc[(size_t)perm[i] * rows + k] / sv[perm[i]];
     }
 }
 
 // ---- step 5: candidate selection in descending phi order
+// Xb: column-major rows x r (B Q = Xb); Vb: r x r column-major (Q); Pc: rows x k, Qc: r x k (row-major).
 __global__ void k_select(const double* __restrict__ Xb, const double* __restrict__ Vb, const double* __restrict__ svb,
-                         const int* __restrict__ perm, int r, const double* __restrict__ sS, double a, double b,
+                         const int* __restrict__ perm, int r, int rows, const double* __restrict__ sS, double a, double b,
                          double eps_tau, double* __restrict__ Pc, double* __restrict__ Qc, double* __restrict__ phic,
                          double* __restrict__ tauc, int* __restrict__ counts, int* __restrict__ cand) {
     __shared__ int nc;
@@ -44,7 +45,7 @@ __global__ void k_select(const double* __restrict__ Xb, const double* __restrict
         for (int ii = 0; ii < r; ++ii) {
             const int j = perm[ii];
             const double phi = svb[j];
-            if (!(phi >= a && phi <= b)) continue;
+            if (!(phi >= a && phi <= b) || !(phi > 0.0)) continue;
             ++inside;
             double num = 0.0, den = 0.0;
             for (int i = 0; i < r; ++i) {
@@ -65,11 +66,14 @@ __global__ void k_select(const double* __restrict__ Xb, const double* __restrict
     }
     __syncthreads();
     const int k = nc;
+    for (int e = t; e < rows * k; e += blockDim.x) {
+        const int i = e / k, c = e % k;                  // row-major rows x k
+        const int j = cand[c];
+        Pc[e] = Xb[(size_t)j * rows + i] / svb[j];
+    }
     for (int e = t; e < r * k; e += blockDim.x) {
         const int i = e / k, c = e % k;                  // row-major r x k
-        const int j = cand[c];
-        Pc[e] = Xb[(size_t)j * r + i] / svb[j];
-        Qc[e] = Vb[(size_t)j * r + i];
+        Qc[e] = Vb[(size_t)cand[c] * r + i];
     }
 }
 
@@ -109,6 +113,7 @@ static int colnorm_diff(const double* Z, const double* X, const double* phi, int
                         int nchunks, double* out, cudaStream_t s) {
     if (k <= 0) return CMSVD_OK;
     dim3 grid((k + 31) / 32, nchunks);
+    ProfScope ps(CMSVD_PROF_OTHER, s, 16.0 * n * k, 3.0 * n * k, 2);
     k_colnorm_part<<<grid, dim3(32, 8), 0, s>>>(Z, X, phi, n, k, part);
     CM_LAUNCH();
     k_colnorm_sum<<<(k + 127) / 128, 128, 0, s>>>(part, nchunks, k, scale, out);
@@ -179,7 +184,7 @@ struct RitzBufs {
 static void ritz_alloc(RitzBufs& b, Arena& ws, int64_t m, int64_t n, int c, int sm_count) {
     const int64_t mx = m > n ? m : n;
     b.Qs = ws.take<double>((size_t)n * c);
-    b.chol = ws.take<double>(cholqr_scratch(c, mx, sm_count));
+    b.chol = ws.take<double>(orth_scratch(c, mx, sm_count));
     b.Rs = ws.take<double>((size_t)c * c);
     b.Xc = ws.take<double>((size_t)c * c);
     b.Vr = ws.take<double>((size_t)c * c);
@@ -207,7 +212,7 @@ static void ritz_alloc(RitzBufs& b, Arena& ws, int64_t m, int64_t n, int c, int 
     b.permR = ws.take<int>(c);
     b.permB = ws.take<int>(c);
     b.cand = ws.take<int>(c);
-    b.ints = ws.take<int>(16);
+    b.ints = ws.take<int>(32);
 }
 
 size_t ritz_workspace(int64_t m, int64_t n, int c, int sm_count) {
@@ -237,46 +242,58 @@ int rayleigh_ritz(cmsvd_matrix* M, const double* S, int64_t lds, int c, double a
     ritz_alloc(bf, ws, m, n, c, ctx->sm_count);
     if (!ws.fits()) { set_error("workspace too small"); return CMSVD_WORKSPACE_TOO_SMALL; }
     int* flag = bf.ints + 8;
-    CM_CUDA(cudaMemsetAsync(bf.ints, 0, sizeof(int) * 16, s));
-    // step 3
-    CM_TRY(cholqr3(S, lds, n, c, bf.Qs, c, bf.Rs, bf.chol, flag, ctx->sm_count, s));
-    CM_TRY(jacobi_svd(bf.Rs, c, bf.Xc, bf.Vr, bf.svR, bf.permR, s));
-    k_truncate<<<1, 256, 0, s>>>(bf.Xc, bf.svR, bf.permR, c, p->delta, bf.sS, bf.Wsel, bf.ints);
-    CM_LAUNCH();
+    CM_CUDA(cudaMemsetAsync(bf.ints, 0, sizeof(int) * 32, s));
+    // step 3: S^ = Q_S R_S, SVD of R_S, truncation
+    int cp = 0;
+    CM_TRY(orth_deflate(S, lds, n, c, bf.Qs, bf.Rs, &cp, bf.chol, flag, bf.ints + 12, ctx->pinned, ctx->sm_count, s));
+    if (cp <= 0) { st->found = 0; return CMSVD_OK; }
+    CM_TRY(jacobi_svd(bf.Rs, cp, c, bf.Xc, bf.Vr, bf.svR, bf.permR, s));
+    {
+        ProfScope ps_t(CMSVD_PROF_SMALL, s, 16.0 * c * c, 0.0);
+        k_truncate<<<1, 256, 0, s>>>(bf.Xc, bf.svR, bf.permR, c, cp, p->delta, bf.sS, bf.Wsel, bf.ints);
+        CM_LAUNCH();
+    }
     int h[4];
     CM_TRY(read_ints(ctx, bf.ints, 1, h));
     const int r = h[0];
     st->rank = r;
     CM_CUDA(cudaMemcpyAsync(&st->sigma_S1, bf.sS, sizeof(double), cudaMemcpyDeviceToHost, s));
     if (r <= 0) { st->found = 0; return CMSVD_OK; }
-    CM_TRY(gemm_nn(bf.Qs, c, bf.Wsel, r, bf.Vt, r, n, c, r, s));
+    CM_TRY(gemm_nn(bf.Qs, cp, bf.Wsel, r, bf.Vt, r, n, cp, r, s));
     cudaEventRecord(ev[1], s);
-    // step 4
+    // step 4: A V~ = U~ B
     CM_TRY(spmm(M->A, r, bf.Vt, r, bf.Y, r, s));
-    CM_TRY(cholqr3(bf.Y, r, m, r, bf.Ut, r, bf.B, bf.chol, flag, ctx->sm_count, s));
+    int rp = 0;
+    CM_TRY(orth_deflate(bf.Y, r, m, r, bf.Ut, bf.B, &rp, bf.chol, flag, bf.ints + 12, ctx->pinned, ctx->sm_count, s));
     cudaEventRecord(ev[2], s);
-    // step 5
-    CM_TRY(jacobi_svd(bf.B, r, bf.Xb, bf.Vb, bf.svB, bf.permB, s));
-    k_select<<<1, 256, 0, s>>>(bf.Xb, bf.Vb, bf.svB, bf.permB, r, bf.sS, a, b, p->eps_tau, bf.Pc, bf.Qc, bf.phic, bf.tauc,
-                               bf.ints + 1, bf.cand);
-    CM_LAUNCH();
+    if (rp <= 0) { st->found = 0; return CMSVD_OK; }
+    // step 5: B = P Phi Q^T, selection, Ritz vectors, residuals
+    CM_TRY(jacobi_svd(bf.B, rp, r, bf.Xb, bf.Vb, bf.svB, bf.permB, s));
+    {
+        ProfScope ps_s(CMSVD_PROF_SMALL, s, 24.0 * r * r, 2.0 * r * r);
+        k_select<<<1, 256, 0, s>>>(bf.Xb, bf.Vb, bf.svB, bf.permB, r, rp, bf.sS, a, b, p->eps_tau, bf.Pc, bf.Qc, bf.phic,
+                                   bf.tauc, bf.ints + 1, bf.cand);
+        CM_LAUNCH();
+    }
     CM_TRY(read_ints(ctx, bf.ints + 1, 2, h));
     const int k = h[0];
     st->in_interval = h[1];
     int t = 0;
     if (k > 0) {
-        CM_TRY(gemm_nn(bf.Ut, r, bf.Pc, k, bf.uh, k, m, r, k, s));
+        CM_TRY(gemm_nn(bf.Ut, rp, bf.Pc, k, bf.uh, k, m, rp, k, s));
         CM_TRY(gemm_nn(bf.Vt, r, bf.Qc, k, bf.vh, k, n, r, k, s));
         CM_TRY(spmm(M->At, k, bf.uh, k, bf.Z, k, s));
         CM_TRY(colnorm_diff(bf.Z, bf.vh, bf.phic, n, k, normA, bf.part, bf.nchunks, bf.resu, s));
         CM_TRY(spmm(M->A, k, bf.vh, k, bf.Z, k, s));
         CM_TRY(colnorm_diff(bf.Z, bf.uh, bf.phic, m, k, normA, bf.part, bf.nchunks, bf.resv, s));
+        ProfScope ps_o(CMSVD_PROF_SMALL, s, 16.0 * k, 0.0);
         k_final_order<<<1, 32, 0, s>>>(bf.phic, bf.resu, k, p->tol_triplet, bf.cand + 0, bf.ints + 4);
         CM_LAUNCH();
         // order overwrites cand (candidates are no longer needed)
         CM_TRY(read_ints(ctx, bf.ints + 4, 1, h));
         t = h[0];
         if (t > 0) {
+            ProfScope ps_c(CMSVD_PROF_OTHER, s, 16.0 * (double)(m + n) * t, 0.0);
             k_final_copy<<<t, 256, 0, s>>>(bf.uh, bf.vh, m, n, k, bf.cand, bf.phic, bf.tauc, bf.resu, bf.resv, out.U, out.V,
                                            out.sigma, out.res_u, out.res_v, out.tau);
             CM_LAUNCH();
