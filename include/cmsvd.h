@@ -87,8 +87,9 @@ enum {
     CMSVD_PROF_DIRECT = 2,      /* per-component direct solve + moments */
     CMSVD_PROF_GRAM = 3,        /* X^T Y of tall-skinny blocks */
     CMSVD_PROF_GEMM = 4,        /* tall-skinny X W */
-    CMSVD_PROF_SMALL = 5,       /* Cholesky, triangular inverse, Jacobi SVD, selection (one CTA) */
+    CMSVD_PROF_SMALL = 5,       /* Cholesky, triangular inverse, selection (one CTA) */
     CMSVD_PROF_OTHER = 6,       /* quadrature, norm estimate, norms, output copies */
+    CMSVD_PROF_JACOBI = 7,      /* one-sided Jacobi SVDs of the small blocks */
     CMSVD_PROF_CLASSES = 8
 };
 
@@ -175,6 +176,19 @@ int cmsvd_spmm(cmsvd_matrix* A, int transpose, int64_t L, const double* X, int64
  */
 int cmsvd_quadrature(cmsvd_context* ctx, double a, double b, int32_t N, int32_t variant,
                      double alpha, double* shift, double* weight, double* scaled);
+
+/*
+ * G = X^T Y for tall-skinny device blocks: the Gram product of the CholeskyQR
+ * orthogonalizations in the rank truncation (Alg. 1 step 3) and in qr(A V~)
+ * (step 4). X: n x c1 (leading dimension ldx >= c1), Y: n x c2 (ldy >= c2),
+ * G: c1 x c2 row-major; all device, all FP64. Deterministic: the rows are split
+ * into fixed chunks whose partial products are added in chunk order.
+ * workspace: device scratch of at least cmsvd_gram_workspace_size bytes, owned by
+ * the caller. 1 <= c1, c2 <= 4096, n >= 1.
+ */
+int cmsvd_gram_workspace_size(cmsvd_context* ctx, int64_t n, int32_t c1, int32_t c2, size_t* bytes);
+int cmsvd_gram(cmsvd_context* ctx, int64_t n, int32_t c1, int32_t c2, const double* X, int64_t ldx,
+               const double* Y, int64_t ldy, double* G, void* workspace, size_t ws_bytes);
 
 /* Device workspace (bytes) that cmsvd_moments / cmsvd_solve_interval need for A and *p. */
 int cmsvd_workspace_size(const cmsvd_matrix* A, const cmsvd_params* p, size_t* bytes);

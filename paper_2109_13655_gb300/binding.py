@@ -33,7 +33,7 @@ class cmsvd_params(C.Structure):
                 ("norm_A", C.c_double), ("check_every", C.c_int32), ("direct_max_block", C.c_int32),
                 ("profile", C.c_int32)]
 
-PROFILE_CLASSES = ("spmm", "krylov", "direct", "gram", "gemm", "small_dense", "other", "unused")
+PROFILE_CLASSES = ("spmm", "krylov", "direct", "gram", "gemm", "small_dense", "other", "jacobi")
 
 
 class cmsvd_stats(C.Structure):
@@ -68,6 +68,8 @@ _SIGS = {
     "cmsvd_spmm": (C.c_int, [_P, C.c_int, _I64, _P, _I64, _P, _I64]),
     "cmsvd_quadrature": (C.c_int, [_P, C.c_double, C.c_double, C.c_int32, C.c_int32, C.c_double, _P, _P, _P]),
     "cmsvd_workspace_size": (C.c_int, [_P, C.POINTER(cmsvd_params), C.POINTER(C.c_size_t)]),
+    "cmsvd_gram_workspace_size": (C.c_int, [_P, _I64, C.c_int32, C.c_int32, C.POINTER(C.c_size_t)]),
+    "cmsvd_gram": (C.c_int, [_P, _I64, C.c_int32, C.c_int32, _P, _I64, _P, _I64, _P, _P, C.c_size_t]),
     "cmsvd_moments": (C.c_int, [_P, C.c_double, C.c_double, C.POINTER(cmsvd_params), _P, _P, _P, C.c_size_t,
                                 C.POINTER(cmsvd_stats)]),
     "cmsvd_solve_interval": (C.c_int, [_P, C.c_double, C.c_double, C.POINTER(cmsvd_params), _P, _P, C.c_size_t,
@@ -185,6 +187,26 @@ def cmsvd_quadrature(ctx: int, a: float, b: float, N: int, variant="linear", alp
     v = VARIANTS[variant] if isinstance(variant, str) else variant
     _check(lib().cmsvd_quadrature(_P(ctx), a, b, N, v, alpha, *(o.ctypes.data for o in out)), "cmsvd_quadrature")
     return tuple(o[0::2] + 1j * o[1::2] for o in out)
+
+
+def cmsvd_gram_workspace_size(ctx: int, n: int, c1: int, c2: int) -> int:
+    b = C.c_size_t()
+    _check(lib().cmsvd_gram_workspace_size(_P(ctx), n, c1, c2, C.byref(b)), "cmsvd_gram_workspace_size")
+    return b.value
+
+
+def cmsvd_gram(ctx: int, X, Y, G, workspace) -> None:
+    """G (c1 x c2) = X^T Y for float64 CUDA tensors X (n x c1), Y (n x c2) (row strides as leading dims)."""
+    n, c1 = X.shape
+    c2 = Y.shape[1]
+    _check(lib().cmsvd_gram(_P(ctx), n, c1, c2, _ptr_any(X), X.stride(0), _ptr_any(Y), Y.stride(0), _ptr(G),
+                            _ptr(workspace), workspace.numel() * workspace.element_size()), "cmsvd_gram")
+
+
+def _ptr_any(t) -> int:
+    """Device address of a row-strided tensor (unit column stride)."""
+    assert t.stride(1) == 1
+    return t.data_ptr()
 
 
 def cmsvd_workspace_size(A: int, p: cmsvd_params) -> int:

@@ -2,7 +2,9 @@
 #include "internal.cuh"
 #include <cmath>
 #include <cstdlib>
+#include <map>
 #include <new>
+#include <tuple>
 
 namespace cmsvd {
 const char* last_error();
@@ -13,6 +15,38 @@ int rayleigh_ritz(cmsvd_matrix* M, const double* S, int64_t lds, int c, double a
 }  // namespace cmsvd
 
 using namespace cmsvd;
+
+// ----------------------------------------------------------------------------- graph cache
+// Instantiated graphs keyed by the buffers and shape they were captured for; a
+// graph is only replayed for a call with the same buffers, which are valid then.
+namespace {
+using GraphKey = std::tuple<const void*, const void*, const void*, int, int>;
+using GraphMap = std::map<GraphKey, cudaGraphExec_t>;
+}  // namespace
+
+namespace cmsvd {
+cudaGraphExec_t graph_cache_get(cmsvd_context* ctx, const void* a, const void* b, const void* c, int x, int y) {
+    if (!ctx->graphs) return nullptr;
+    auto* m = (GraphMap*)ctx->graphs;
+    auto it = m->find(GraphKey(a, b, c, x, y));
+    return it == m->end() ? nullptr : it->second;
+}
+void graph_cache_put(cmsvd_context* ctx, const void* a, const void* b, const void* c, int x, int y, cudaGraphExec_t g) {
+    if (!ctx->graphs) ctx->graphs = new (std::nothrow) GraphMap();
+    auto* m = (GraphMap*)ctx->graphs;
+    if (!m) { cudaGraphExecDestroy(g); return; }
+    if (m->size() >= 64) graph_cache_clear(ctx), m = (GraphMap*)(ctx->graphs = new (std::nothrow) GraphMap());
+    if (!m) { cudaGraphExecDestroy(g); return; }
+    (*m)[GraphKey(a, b, c, x, y)] = g;
+}
+void graph_cache_clear(cmsvd_context* ctx) {
+    auto* m = (GraphMap*)ctx->graphs;
+    if (!m) return;
+    for (auto& kv : *m) cudaGraphExecDestroy(kv.second);
+    delete m;
+    ctx->graphs = nullptr;
+}
+}  // namespace cmsvd
 
 namespace {
 
@@ -220,7 +254,9 @@ int cmsvd_context_create(void* stream, cmsvd_context** out) {
 
 int cmsvd_context_destroy(cmsvd_context* c) {
     if (!c) return CMSVD_OK;
-    if (c->s) { cudaStreamSynchronize(c->s); cudaStreamDestroy(c->s); }
+    if (c->s) cudaStreamSynchronize(c->s);
+    graph_cache_clear(c);
+    if (c->s) cudaStreamDestroy(c->s);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
     if (c->ev_out) cudaEventDestroy(c->ev_out);
     if (c->pinned) cudaFreeHost(c->pinned);
@@ -310,6 +346,26 @@ int cmsvd_quadrature(cmsvd_context* ctx, double a, double b, int32_t N, int32_t 
     free(h);
     cudaFree(d);
     if (st != CMSVD_OK) return st;
+    return leave(ctx);
+}
+
+int cmsvd_gram_workspace_size(cmsvd_context* ctx, int64_t n, int32_t c1, int32_t c2, size_t* bytes) {
+    if (!ctx || !bytes) { set_error("NULL argument"); return CMSVD_INVALID_ARG; }
+    if (n < 1 || c1 < 1 || c2 < 1 || c1 > 4096 || c2 > 4096) { set_error("need n >= 1 and 1 <= c1, c2 <= 4096"); return CMSVD_INVALID_ARG; }
+    *bytes = sizeof(double) * gram_partials_size(c1, c2, n, ctx->sm_count) + 256;
+    return CMSVD_OK;
+}
+
+int cmsvd_gram(cmsvd_context* ctx, int64_t n, int32_t c1, int32_t c2, const double* X, int64_t ldx, const double* Y,
+               int64_t ldy, double* G, void* workspace, size_t ws_bytes) {
+    size_t need = 0;
+    CM_TRY(cmsvd_gram_workspace_size(ctx, n, c1, c2, &need));
+    if (!X || !Y || !G || !workspace) { set_error("NULL argument"); return CMSVD_INVALID_ARG; }
+    if (ldx < c1 || ldy < c2) { set_error("need ldx >= c1 and ldy >= c2"); return CMSVD_INVALID_ARG; }
+    if (ws_bytes < need) { set_error("workspace %zu < %zu bytes", ws_bytes, need); return CMSVD_WORKSPACE_TOO_SMALL; }
+    CM_TRY(enter(ctx));
+    CM_TRY(gram(X, ldx, c1, Y, ldy, c2, n, G, (double*)workspace, (ws_bytes - 256) / sizeof(double), ctx->sm_count,
+                ctx->s));
     return leave(ctx);
 }
 

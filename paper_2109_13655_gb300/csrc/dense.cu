@@ -16,10 +16,11 @@ constexpr int GK = 16;   // rows per slab
 
 __global__ void __launch_bounds__(256) k_gram_partial(const double* __restrict__ X, int64_t ldx, int c1,
                                                       const double* __restrict__ Y, int64_t ldy, int c2, int64_t n,
-                                                      int64_t rows_per_chunk, double* __restrict__ partials) {
+                                                      int64_t rows_per_chunk, int sym, double* __restrict__ partials) {
     __shared__ double Xs[GK][GT];
     __shared__ double Ys[GK][GT];
     const int ti = blockIdx.x * GT, tj = blockIdx.y * GT;
+    if (sym && blockIdx.x > blockIdx.y) return;   // symmetric: lower tiles are mirrored by the sum
     const int64_t r0 = (int64_t)blockIdx.z * rows_per_chunk;
     const int64_t r1 = r0 + rows_per_chunk < n ? r0 + rows_per_chunk : n;
     const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
@@ -60,17 +61,26 @@ __global__ void __launch_bounds__(256) k_gram_partial(const double* __restrict__
         }
 }
 
-__global__ void k_sum_partials(const double* __restrict__ partials, int nchunks, int64_t count, double* __restrict__ G) {
+// G = sum of the chunk partials in chunk order. sym: only tiles with
+// row tile <= column tile were computed; the rest is mirrored.
+__global__ void k_sum_partials(const double* __restrict__ partials, int nchunks, int c1, int c2, int sym,
+                               double* __restrict__ G) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t count = (int64_t)c1 * c2;
     if (e >= count) return;
+    int i = (int)(e / c2), j = (int)(e % c2);
+    if (sym && i / GT > j / GT) { const int t = i; i = j; j = t; }
+    const int64_t src = (int64_t)i * c2 + j;
     double s = 0.0;
-    for (int c = 0; c < nchunks; ++c) s += partials[(size_t)c * count + e];
+    for (int c = 0; c < nchunks; ++c) s += partials[(size_t)c * count + src];
     G[e] = s;
 }
 
-static void gram_plan(int c1, int c2, int64_t n, int sm_count, int* nchunks, int64_t* rpc) {
-    const int tiles = ((c1 + GT - 1) / GT) * ((c2 + GT - 1) / GT);
-    int64_t want = (2 * (int64_t)sm_count + tiles - 1) / tiles;
+static void gram_plan(int c1, int c2, int64_t n, int sm_count, int* nchunks, int64_t* rpc, int sym = 0) {
+    const int tx = (c1 + GT - 1) / GT;
+    const int tiles = sym ? tx * (tx + 1) / 2 : tx * ((c2 + GT - 1) / GT);
+    // about 4 working CTAs per SM (256 threads x 64 registers each fill the register file)
+    int64_t want = (4 * (int64_t)sm_count + tiles - 1) / tiles;
     int64_t maxc = (n + 63) / 64;
     if (want > maxc) want = maxc;
     if (want < 1) want = 1;
@@ -90,32 +100,38 @@ size_t gram_partials_size(int c1, int c2, int64_t n, int sm_count) {
 }
 
 // Upper bound of gram_partials_size(c', c', n) over every c' <= c: the chunk
-// count is at most 2 sm / tiles + 1 and c'^2 / tiles <= 64^2.
+// count is at most 4 sm / tiles + 1 and c'^2 / tiles <= 2 * 64^2 (symmetric tiles).
 size_t gram_partials_cap(int c, int sm_count) {
-    return (size_t)(2 * sm_count + 1) * GT * GT + (size_t)c * c;
+    const size_t tiles = (size_t)((c + GT - 1) / GT) * ((c + GT - 1) / GT);
+    return (size_t)(4 * sm_count + 1) * GT * GT * 2 + tiles * GT * GT;
 }
 
 int gram(const double* X, int64_t ldx, int c1, const double* Y, int64_t ldy, int c2, int64_t n, double* G,
          double* partials, size_t partials_cap, int sm_count, cudaStream_t s) {
     int nc;
     int64_t rpc;
-    gram_plan(c1, c2, n, sm_count, &nc, &rpc);
+    const int sym = (X == Y && c1 == c2 && ldx == ldy) ? 1 : 0;
+    gram_plan(c1, c2, n, sm_count, &nc, &rpc, sym);
     if ((size_t)nc * c1 * c2 > partials_cap) { set_error("gram scratch too small"); return CMSVD_WORKSPACE_TOO_SMALL; }
     dim3 grid((c1 + GT - 1) / GT, (c2 + GT - 1) / GT, nc);
     const int64_t cnt = (int64_t)c1 * c2;
+    const double tiles = (double)grid.x * grid.y, tiles_done = sym ? grid.x * (grid.x + 1) / 2.0 : tiles;
     {
-        ProfScope ps(CMSVD_PROF_GRAM, s, 8.0 * n * (X == Y ? c1 : c1 + c2) + 8.0 * cnt, 2.0 * n * c1 * c2, 2);
-        k_gram_partial<<<grid, 256, 0, s>>>(X, ldx, c1, Y, ldy, c2, n, rpc, partials);
+        ProfScope ps(CMSVD_PROF_GRAM, s, 8.0 * n * (sym ? c1 : c1 + c2) + 8.0 * cnt,
+                     2.0 * n * c1 * c2 * tiles_done / tiles, 2);
+        k_gram_partial<<<grid, 256, 0, s>>>(X, ldx, c1, Y, ldy, c2, n, rpc, sym, partials);
         CM_LAUNCH();
-        k_sum_partials<<<(int)((cnt + 255) / 256), 256, 0, s>>>(partials, nc, cnt, G);
+        k_sum_partials<<<(int)((cnt + 255) / 256), 256, 0, s>>>(partials, nc, c1, c2, sym, G);
         CM_LAUNCH();
     }
     return CMSVD_OK;
 }
 
 // ----------------------------------------------------------------------------- Z = X W
+// upper != 0: W is upper triangular, so column tile [cc0, cc0+64) needs k < cc0 + 64 only.
 __global__ void __launch_bounds__(256) k_gemm_nn(const double* __restrict__ X, int64_t ldx, const double* __restrict__ W,
-                                                 int64_t ldw, double* __restrict__ Z, int64_t ldz, int64_t n, int c1, int c2) {
+                                                 int64_t ldw, double* __restrict__ Z, int64_t ldz, int64_t n, int c1, int c2,
+                                                 int upper) {
     __shared__ double Xs[GT][GK + 1];
     __shared__ double Ws[GK][GT];
     const int64_t r0 = (int64_t)blockIdx.y * GT;
@@ -126,7 +142,8 @@ __global__ void __launch_bounds__(256) k_gemm_nn(const double* __restrict__ X, i
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
-    for (int k0 = 0; k0 < c1; k0 += GK) {
+    const int kend = upper ? min(c1, cc0 + GT) : c1;
+    for (int k0 = 0; k0 < kend; k0 += GK) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int e = tid + 256 * q;
@@ -161,11 +178,13 @@ __global__ void __launch_bounds__(256) k_gemm_nn(const double* __restrict__ X, i
 }
 
 int gemm_nn(const double* X, int64_t ldx, const double* W, int64_t ldw, double* Z, int64_t ldz, int64_t n, int c1,
-            int c2, cudaStream_t s) {
+            int c2, cudaStream_t s, int upper) {
     if (n <= 0 || c2 <= 0) return CMSVD_OK;
     dim3 grid((c2 + GT - 1) / GT, (unsigned)((n + GT - 1) / GT));
-    ProfScope ps(CMSVD_PROF_GEMM, s, 8.0 * ((double)n * c1 + (double)c1 * c2 + (double)n * c2), 2.0 * n * c1 * c2);
-    k_gemm_nn<<<grid, 256, 0, s>>>(X, ldx, W, ldw, Z, ldz, n, c1, c2);
+    double work = 0.0;   // multiply-adds actually performed per row
+    for (int cc0 = 0; cc0 < c2; cc0 += GT) work += (double)(upper ? min(c1, cc0 + GT) : c1) * min(GT, c2 - cc0);
+    ProfScope ps(CMSVD_PROF_GEMM, s, 8.0 * ((double)n * c1 + (double)c1 * c2 + (double)n * c2), 2.0 * n * work);
+    k_gemm_nn<<<grid, 256, 0, s>>>(X, ldx, W, ldw, Z, ldz, n, c1, c2, upper);
     CM_LAUNCH();
     return CMSVD_OK;
 }
@@ -234,19 +253,15 @@ __global__ void k_trinv(const double* __restrict__ R, int c, double* __restrict_
 // Bm V = Xc, so sv_j = ||Xc_j|| are the singular values (zero when cols > rows),
 // Xc_j / sv_j the left and V_j the right singular vectors. Round-robin
 // ordering; one warp per pair; perm sorts sv descending (stable).
-__global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ Bm, int rows, int cols, double* __restrict__ Xc,
-                                                 double* __restrict__ V, double* __restrict__ sv, int* __restrict__ perm) {
+__global__ void __launch_bounds__(1024) k_jacobi(double* __restrict__ Xc, int rows, int cols, double* __restrict__ V,
+                                                 const double* __restrict__ fro2, double* __restrict__ sv,
+                                                 int* __restrict__ perm) {
     __shared__ int rotated;
     const int t = threadIdx.x, nt = blockDim.x;
     const int lane = t & 31, warp = t >> 5, nwarps = nt >> 5;
-    for (int e = t; e < rows * cols; e += nt) {
-        const int i = e / cols, j = e % cols;     // Bm (i, j) -> column j, row i
-        Xc[(size_t)j * rows + i] = Bm[e];
-    }
-    for (int e = t; e < cols * cols; e += nt) V[e] = (e / cols == e % cols) ? 1.0 : 0.0;
-    __syncthreads();
     const int np = (cols + 1) / 2 * 2;            // players (one dummy when cols is odd)
     const double tol = fmax(1e-15, rows * 2.220446049250313e-16);
+    const double negl = 1e-36 * *fro2;
     for (int sweep = 0; sweep < 60; ++sweep) {
         if (t == 0) rotated = 0;
         __syncthreads();
@@ -272,7 +287,7 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ Bm, 
                     be += __shfl_xor_sync(0xffffffffu, be, o);
                     ga += __shfl_xor_sync(0xffffffffu, ga, o);
                 }
-                if (fabs(ga) > tol * sqrt(al * be) && al > 0.0 && be > 0.0) {
+                if (fabs(ga) > tol * sqrt(al * be) && al > negl && be > negl) {
                     const double zeta = (be - al) / (2.0 * ga);
                     const double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
                     const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
@@ -315,18 +330,174 @@ __global__ void __launch_bounds__(1024) k_jacobi(const double* __restrict__ Bm, 
     }
 }
 
-int jacobi_svd(const double* Bm, int rows, int cols, double* Xc, double* V, double* sv, int* perm, cudaStream_t s) {
-    ProfScope ps(CMSVD_PROF_SMALL, s, 16.0 * (rows + cols) * cols, 0.0);
-    k_jacobi<<<1, 1024, 0, s>>>(Bm, rows, cols, Xc, V, sv, perm);
+// Multi-CTA form for larger blocks: one CTA per pair of a round (the pairs of a
+// round are disjoint), one launch per round; a sweep is np-1 launches and the
+// host checks the "rotated" flag after every sweep. Columns whose squared norm is
+// below negl (1e-36 ||Bm||_F^2) are treated as zero.
+__device__ __forceinline__ double block_sum256(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += sh[w];
+    return t;
+}
+
+__global__ void __launch_bounds__(256) k_jacobi_round(double* __restrict__ Xc, double* __restrict__ V, int rows, int cols,
+                                                      int np, int round, double tol, const double* __restrict__ fro2,
+                                                      int* __restrict__ rotated) {
+    __shared__ double sh[3][8];
+    const int k = blockIdx.x;
+    int p, q;
+    if (k == 0) { p = round; q = np - 1; }
+    else { p = (round + k) % (np - 1); q = (round - k + (np - 1)) % (np - 1); }
+    if (p >= cols || q >= cols) return;
+    if (p > q) { const int t = p; p = q; q = t; }
+    double* xp = Xc + (size_t)p * rows;
+    double* xq = Xc + (size_t)q * rows;
+    double al = 0.0, be = 0.0, ga = 0.0;
+    for (int i = threadIdx.x; i < rows; i += 256) {
+        const double a = xp[i], b = xq[i];
+        al = __fma_rn(a, a, al);
+        be = __fma_rn(b, b, be);
+        ga = __fma_rn(a, b, ga);
+    }
+    al = block_sum256(al, sh[0]);
+    be = block_sum256(be, sh[1]);
+    ga = block_sum256(ga, sh[2]);
+    const double negl = 1e-36 * *fro2;
+    if (!(fabs(ga) > tol * sqrt(al * be)) || !(al > negl) || !(be > negl)) return;
+    const double zeta = (be - al) / (2.0 * ga);
+    const double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+    const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
+    for (int i = threadIdx.x; i < rows; i += 256) {
+        const double a = xp[i], b = xq[i];
+        xp[i] = cs * a - sn * b;
+        xq[i] = sn * a + cs * b;
+    }
+    double* vp = V + (size_t)p * cols;
+    double* vq = V + (size_t)q * cols;
+    for (int i = threadIdx.x; i < cols; i += 256) {
+        const double va = vp[i], vb = vq[i];
+        vp[i] = cs * va - sn * vb;
+        vq[i] = sn * va + cs * vb;
+    }
+    if (threadIdx.x == 0) *rotated = 1;
+}
+
+__global__ void __launch_bounds__(1024) k_jacobi_finish(const double* __restrict__ Xc, int rows, int cols,
+                                                        double* __restrict__ sv, int* __restrict__ perm) {
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarps = blockDim.x >> 5;
+    for (int j = warp; j < cols; j += nwarps) {
+        double s2 = 0.0;
+        for (int i = lane; i < rows; i += 32) s2 = __fma_rn(Xc[(size_t)j * rows + i], Xc[(size_t)j * rows + i], s2);
+        for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        if (lane == 0) sv[j] = sqrt(s2);
+    }
+    __syncthreads();
+    if (t == 0) {
+        for (int i = 0; i < cols; ++i) perm[i] = i;
+        for (int i = 1; i < cols; ++i) {
+            const int key = perm[i];
+            int j = i - 1;
+            while (j >= 0 && sv[perm[j]] < sv[key]) { perm[j + 1] = perm[j]; --j; }
+            perm[j + 1] = key;
+        }
+    }
+}
+
+// Rotates the columns of Bm (trans = 0; Bm V = Xc) or of Bm^T (trans = 1; Bm^T V = Xc,
+// so Bm = V diag(sv) (Xc / sv)^T: V holds the LEFT singular vectors of Bm). Applying
+// the method to the transpose of the R factors met here roughly halves the sweeps.
+__global__ void k_jacobi_init_t(const double* __restrict__ Bm, int brows, int bcols, int trans, double* __restrict__ Xc,
+                                double* __restrict__ V, double* __restrict__ fro2) {
+    const int rows = trans ? bcols : brows, cols = trans ? brows : bcols;
+    const int64_t nt = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t e = t0; e < (int64_t)brows * bcols; e += nt) {
+        const int i = (int)(e / bcols), j = (int)(e % bcols);     // Bm(i, j)
+        if (trans) Xc[(size_t)i * rows + j] = Bm[e];             // column i of Bm^T, row j
+        else Xc[(size_t)j * rows + i] = Bm[e];
+    }
+    for (int64_t e = t0; e < (int64_t)cols * cols; e += nt) V[e] = (e / cols == e % cols) ? 1.0 : 0.0;
+    if (blockIdx.x == 0) {
+        __shared__ double sh[32];
+        double acc = 0.0;
+        for (int64_t e = threadIdx.x; e < (int64_t)brows * bcols; e += blockDim.x) acc = __fma_rn(Bm[e], Bm[e], acc);
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+            *fro2 = t;
+        }
+    }
+}
+
+int jacobi_svd(const double* Bm, int brows, int bcols, int trans, double* Xc, double* V, double* sv, int* perm,
+               int* flag2, cmsvd_context* ctx) {
+    cudaStream_t s = ctx->s;
+    const int rows = trans ? bcols : brows, cols = trans ? brows : bcols;
+    double* fro2 = (double*)(flag2 + 2);   // flag2: 16 bytes of scratch (int rotated, pad, double)
+    {
+        ProfScope ps(CMSVD_PROF_JACOBI, s, 16.0 * rows * cols + 8.0 * cols * cols, 0.0);
+        k_jacobi_init_t<<<64, 256, 0, s>>>(Bm, brows, bcols, trans, Xc, V, fro2);
+        CM_LAUNCH();
+    }
+    const int np = (cols + 1) / 2 * 2;
+    const double tol = fmax(1e-15, rows * 2.220446049250313e-16);
+    if (cols <= 96) {
+        ProfScope ps(CMSVD_PROF_JACOBI, s, 16.0 * (rows + cols) * cols, 0.0);
+        k_jacobi<<<1, 1024, 0, s>>>(Xc, rows, cols, V, fro2, sv, perm);
+        CM_LAUNCH();
+        return CMSVD_OK;
+    }
+    // one sweep = memset(flag) + np-1 round kernels, captured once per shape and buffers
+    cudaGraphExec_t ge = graph_cache_get(ctx, Xc, V, flag2, rows, cols);
+    if (!ge) {
+        cudaGraph_t g = nullptr;
+        Profiler& pr = prof();
+        pr.capture_depth++;
+        cudaError_t ce = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+        if (ce == cudaSuccess) {
+            cudaMemsetAsync(flag2, 0, sizeof(int), s);
+            for (int round = 0; round < np - 1; ++round)
+                k_jacobi_round<<<np / 2, 256, 0, s>>>(Xc, V, rows, cols, np, round, tol, fro2, flag2);
+            ce = cudaStreamEndCapture(s, &g);
+        }
+        pr.capture_depth--;
+        if (ce != cudaSuccess) return cuda_fail(ce, "capture Jacobi sweep", __FILE__, __LINE__);
+        ce = cudaGraphInstantiate(&ge, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) return cuda_fail(ce, "instantiate Jacobi sweep", __FILE__, __LINE__);
+        graph_cache_put(ctx, Xc, V, flag2, rows, cols, ge);
+    }
+    for (int sweep = 0; sweep < 40; ++sweep) {
+        {
+            ProfScope ps(CMSVD_PROF_JACOBI, s, (np - 1.0) * (np / 2) * 32.0 * (rows + cols),
+                         (np - 1.0) * (np / 2) * (6.0 * rows + 6.0 * (rows + cols)), np - 1);
+            prof().launches += np - 1;
+            CM_CUDA(cudaGraphLaunch(ge, s));
+        }
+        CM_CUDA(cudaMemcpyAsync(ctx->pinned, flag2, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CM_CUDA(cudaStreamSynchronize(s));
+        if (ctx->pinned[0] == 0) break;
+    }
+    ProfScope ps(CMSVD_PROF_JACOBI, s, 8.0 * rows * cols, 2.0 * rows * cols);
+    k_jacobi_finish<<<1, 1024, 0, s>>>(Xc, rows, cols, sv, perm);
     CM_LAUNCH();
     return CMSVD_OK;
 }
 
-// ----------------------------------------------------------------------------- deflated orthogonalization
-// Deflation after two shifted passes: with G = Q2^T Q2 = W diag(sv^2) W^T (from the
-// Jacobi SVD of its shifted Cholesky factor), keep the directions with
-// sv_k^2 > keep * sv_max^2; T3 = W_g diag(1/sv_g) (c x c') and R3 = diag(sv_g) W_g^T (c' x c).
-__global__ void k_deflate(const double* __restrict__ V, const double* __restrict__ sv, const int* __restrict__ perm, int c,
+// ----------------------------------------------------------------------------- orthogonalization
+// Deflation: with G = Q2^T Q2 = Rb^T Rb and Rb^T = Xj diag(sv) V^T... (Jacobi on Rb^T),
+// Rb = V diag(sv) W^T with W_j = Xj_j / sv_j, so G = W diag(sv^2) W^T. Keep the
+// directions with sv_k^2 > keep * sv_max^2: T3 = W_g diag(1/sv_g) (c x c') and
+// R3 = diag(sv_g) W_g^T (c' x c).
+__global__ void k_deflate(const double* __restrict__ Xj, const double* __restrict__ sv, const int* __restrict__ perm, int c,
                           double keep, double* __restrict__ T3, double* __restrict__ R3, int* __restrict__ cp_out) {
     __shared__ int cp;
     const int t = threadIdx.x;
@@ -342,27 +513,90 @@ __global__ void k_deflate(const double* __restrict__ V, const double* __restrict
     for (int e = t; e < c * k; e += blockDim.x) {
         const int i = e / k, g = e % k;               // T3 row-major c x k
         const int j = perm[g];
-        T3[e] = V[(size_t)j * c + i] / sv[j];
+        T3[e] = Xj[(size_t)j * c + i] / (sv[j] * sv[j]);
     }
     for (int e = t; e < k * c; e += blockDim.x) {
         const int g = e / c, i = e % c;               // R3 row-major k x c
-        const int j = perm[g];
-        R3[e] = sv[j] * V[(size_t)j * c + i];
+        R3[e] = Xj[(size_t)perm[g] * c + i];
     }
+}
+
+// min over max of the diagonal of an upper-triangular R (condition estimate of CholeskyQR)
+__global__ void k_diag_ratio(const double* __restrict__ R, int c, double* __restrict__ out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double lo = 1e300, hi = 0.0;
+    for (int i = 0; i < c; ++i) {
+        const double d = fabs(R[(size_t)i * c + i]);
+        lo = fmin(lo, d);
+        hi = fmax(hi, d);
+    }
+    *out = hi > 0.0 ? lo / hi : 0.0;
 }
 
 size_t orth_scratch(int c, int64_t n, int sm_count) {
     return (size_t)n * c + 14 * (size_t)c * c + 2 * (size_t)c + gram_partials_cap(c, sm_count) + 256;
 }
 
-// X (n x c, ldx) = Q R with Q (n x c', ld c') orthonormal and R (c' x c, row-major):
-//   two shifted CholeskyQR passes (shift 11 (n c + c (c+1)) u ||.||_F^2 each) bring
-//   every direction of X whose singular value exceeds ~1e-14 ||X|| to O(1),
-//   deflation drops the rest (rounding noise far below any useful threshold),
-//   two plain CholeskyQR passes restore orthogonality to working precision.
-// *c_out receives c'. scratch: orth_scratch(c, n) doubles; flag: device int.
-int orth_deflate(const double* X, int64_t ldx, int64_t n, int c, double* Q, double* R, int* c_out, double* scratch,
-                 int* flag, int* cp_dev, int* pinned, int sm_count, cudaStream_t s) {
+namespace {
+struct OrthCtx {
+    cmsvd_context* ctx;
+    cudaStream_t s;
+    double *G, *Ri, *part;
+    size_t pcap;
+    int* flag;       // device int
+    int64_t n;
+};
+
+// R (cc x cc) with R^T R = G + shift I. base = 0: plain Cholesky first. A failed
+// attempt (non-positive pivot) is repeated with a 100x larger shift, starting from
+// 10 (cc + sqrt(n)) u trace(G) -- the size of the rounding error of a computed Gram.
+int chol_adaptive(OrthCtx& o, int cc, bool shifted, double* R) {
+    const double u = 1.1102230246251565e-16;
+    double coef = shifted ? 10.0 * (cc + sqrt((double)o.n)) * u : 0.0;
+    for (int attempt = 0; attempt < 12; ++attempt) {
+        CM_CUDA(cudaMemsetAsync(o.flag, 0, sizeof(int), o.s));
+        {
+            ProfScope ps(CMSVD_PROF_SMALL, o.s, 16.0 * cc * cc, cc * (double)cc * cc / 3.0);
+            k_chol<<<1, 1024, 0, o.s>>>(o.G, cc, coef, R, o.flag);
+            CM_LAUNCH();
+        }
+        CM_CUDA(cudaMemcpyAsync(o.ctx->pinned, o.flag, sizeof(int), cudaMemcpyDeviceToHost, o.s));
+        CM_CUDA(cudaStreamSynchronize(o.s));
+        if (o.ctx->pinned[0] == 0) return CMSVD_OK;
+        coef = coef > 0.0 ? coef * 100.0 : 10.0 * (cc + sqrt((double)o.n)) * u;
+    }
+    set_error("Cholesky of a Gram matrix failed for every shift");
+    return CMSVD_BREAKDOWN;
+}
+
+int trinv(OrthCtx& o, const double* R, int cc) {
+    const int tpb = cc < 1024 ? ((cc + 31) / 32 * 32) : 1024;
+    ProfScope ps(CMSVD_PROF_SMALL, o.s, 16.0 * cc * cc, cc * (double)cc * cc / 3.0);
+    k_trinv<<<(cc + tpb - 1) / tpb, tpb, 0, o.s>>>(R, cc, o.Ri);
+    CM_LAUNCH();
+    return CMSVD_OK;
+}
+
+// one CholeskyQR pass: Xout = Xin R^{-1}, R^T R = Xin^T Xin (+ shift)
+int cholqr_pass(OrthCtx& o, const double* Xin, int64_t ldi, int cc, bool shifted, double* R, double* Xout) {
+    CM_TRY(gram(Xin, ldi, cc, Xin, ldi, cc, o.n, o.G, o.part, o.pcap, o.ctx->sm_count, o.s));
+    CM_TRY(chol_adaptive(o, cc, shifted, R));
+    CM_TRY(trinv(o, R, cc));
+    CM_TRY(gemm_nn(Xin, ldi, o.Ri, cc, Xout, cc, o.n, cc, cc, o.s, 1));
+    return CMSVD_OK;
+}
+}  // namespace
+
+// X (n x c, ldx) = Q R with Q (n x c', ld c') orthonormal and R (c' x c, row-major).
+//   deflate = 0: when the first plain Cholesky succeeds and diag(R) spans less than
+//   1e5 (cond(X) well below 1/sqrt(u)), CholeskyQR2 is used (c' = c).
+//   Otherwise: two shifted CholeskyQR passes bring every direction of X whose
+//   singular value exceeds ~1e-14 ||X|| to O(1); the Gram of the result is
+//   eigen-decomposed and the directions left at rounding level are deflated; two
+//   plain passes restore orthogonality to working precision.
+int orth_qr(const double* X, int64_t ldx, int64_t n, int c, double* Q, double* R, int* c_out, double* scratch, int* ints,
+            int deflate, cmsvd_context* ctx) {
+    cudaStream_t s = ctx->s;
     double* T = scratch;
     double* G = T + (size_t)n * c;
     double* R1 = G + (size_t)c * c;
@@ -380,51 +614,55 @@ int orth_deflate(const double* X, int64_t ldx, int64_t n, int c, double* Q, doub
     double* sv = M2 + (size_t)c * c;
     int* perm = (int*)(sv + c);
     double* part = sv + 2 * (size_t)c;
-    const size_t pcap = gram_partials_cap(c, sm_count);
-    const double u = 1.1102230246251565e-16;
-    const double coef = 11.0 * ((double)n * c + (double)c * (c + 1)) * u;
-    auto chol_inv = [&](int cc, double sc, double* Rout) -> int {
-        const int tpb = cc < 1024 ? ((cc + 31) / 32 * 32) : 1024;
-        ProfScope ps(CMSVD_PROF_SMALL, s, 24.0 * cc * cc, 2.0 * cc * cc * cc / 3.0, 2);
-        k_chol<<<1, 1024, 0, s>>>(G, cc, sc, Rout, flag);
-        CM_LAUNCH();
-        k_trinv<<<(cc + tpb - 1) / tpb, tpb, 0, s>>>(Rout, cc, Ri);
-        CM_LAUNCH();
-        return CMSVD_OK;
-    };
-    // two shifted passes: X -> Q (R1), Q -> T (R2)
-    CM_TRY(gram(X, ldx, c, X, ldx, c, n, G, part, pcap, sm_count, s));
-    CM_TRY(chol_inv(c, coef, R1));
-    CM_TRY(gemm_nn(X, ldx, Ri, c, Q, c, n, c, c, s));
-    CM_TRY(gram(Q, c, c, Q, c, c, n, G, part, pcap, sm_count, s));
-    CM_TRY(chol_inv(c, coef, R2));
-    CM_TRY(gemm_nn(Q, c, Ri, c, T, c, n, c, c, s));
-    // deflation
-    CM_TRY(gram(T, c, c, T, c, c, n, G, part, pcap, sm_count, s));
-    {
-        ProfScope ps(CMSVD_PROF_SMALL, s, 24.0 * c * c, 2.0 * c * c * c / 3.0);
-        k_chol<<<1, 1024, 0, s>>>(G, c, coef, Rb, flag);
-        CM_LAUNCH();
+    OrthCtx o{ctx, s, G, Ri, part, gram_partials_cap(c, ctx->sm_count), ints, n};
+    int* cp_dev = ints + 1;
+    int* flag2 = ints + 4;             // 16 bytes: ints[4..7]
+    double* ratio = (double*)(ints + 2);
+    if (!deflate) {
+        // CholeskyQR2 attempt
+        CM_TRY(gram(X, ldx, c, X, ldx, c, n, G, part, o.pcap, ctx->sm_count, s));
+        CM_CUDA(cudaMemsetAsync(o.flag, 0, sizeof(int), s));
+        {
+            ProfScope ps(CMSVD_PROF_SMALL, s, 16.0 * c * c, c * (double)c * c / 3.0, 2);
+            k_chol<<<1, 1024, 0, s>>>(G, c, 0.0, R1, o.flag);
+            CM_LAUNCH();
+            k_diag_ratio<<<1, 32, 0, s>>>(R1, c, ratio);
+            CM_LAUNCH();
+        }
+        CM_CUDA(cudaMemcpyAsync(ctx->pinned, ints, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        CM_CUDA(cudaStreamSynchronize(s));
+        double rat;
+        memcpy(&rat, ctx->pinned + 2, sizeof(double));
+        if (ctx->pinned[0] == 0 && rat > 1e-5) {
+            CM_TRY(trinv(o, R1, c));
+            CM_TRY(gemm_nn(X, ldx, Ri, c, T, c, n, c, c, s, 1));
+            CM_TRY(cholqr_pass(o, T, c, c, false, R2, Q));
+            CM_TRY(gemm_nn(R2, c, R1, c, R, c, c, c, c, s));
+            *c_out = c;
+            return CMSVD_OK;
+        }
     }
-    CM_TRY(jacobi_svd(Rb, c, c, Xj, Vj, sv, perm, s));
+    // two shifted passes: X -> Q (R1), Q -> T (R2)
+    CM_TRY(cholqr_pass(o, X, ldx, c, true, R1, Q));
+    CM_TRY(cholqr_pass(o, Q, c, c, true, R2, T));
+    // deflation
+    CM_TRY(gram(T, c, c, T, c, c, n, G, part, o.pcap, ctx->sm_count, s));
+    CM_TRY(chol_adaptive(o, c, true, Rb));
+    CM_TRY(jacobi_svd(Rb, c, c, 1, Xj, Vj, sv, perm, flag2, ctx));
     {
         ProfScope ps(CMSVD_PROF_SMALL, s, 24.0 * c * c, 0.0);
-        k_deflate<<<1, 256, 0, s>>>(Vj, sv, perm, c, 1e-10, T3, R3, cp_dev);
+        k_deflate<<<1, 256, 0, s>>>(Xj, sv, perm, c, 1e-10, T3, R3, cp_dev);
         CM_LAUNCH();
     }
-    CM_CUDA(cudaMemcpyAsync(pinned, cp_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CM_CUDA(cudaMemcpyAsync(ctx->pinned, cp_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
     CM_CUDA(cudaStreamSynchronize(s));
-    const int cp = pinned[0];
+    const int cp = ctx->pinned[0];
     *c_out = cp;
     if (cp <= 0) return CMSVD_OK;
     CM_TRY(gemm_nn(T, c, T3, cp, Q, cp, n, c, cp, s));
     // two plain passes: Q -> T (R4), T -> Q (R5)
-    CM_TRY(gram(Q, cp, cp, Q, cp, cp, n, G, part, pcap, sm_count, s));
-    CM_TRY(chol_inv(cp, 0.0, R4));
-    CM_TRY(gemm_nn(Q, cp, Ri, cp, T, cp, n, cp, cp, s));
-    CM_TRY(gram(T, cp, cp, T, cp, cp, n, G, part, pcap, sm_count, s));
-    CM_TRY(chol_inv(cp, 0.0, R5));
-    CM_TRY(gemm_nn(T, cp, Ri, cp, Q, cp, n, cp, cp, s));
+    CM_TRY(cholqr_pass(o, Q, cp, cp, false, R4, T));
+    CM_TRY(cholqr_pass(o, T, cp, cp, false, R5, Q));
     // R = R5 R4 R3 R2 R1
     CM_TRY(gemm_nn(R2, c, R1, c, M1, c, c, c, c, s));
     CM_TRY(gemm_nn(R3, c, M1, c, M2, c, cp, c, c, s));

@@ -89,6 +89,7 @@ struct cmsvd_context {
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     int sm_count = 0;
     int* pinned = nullptr;             // host-pinned flags for polling
+    void* graphs = nullptr;            // cache of instantiated graphs (api.cu)
 };
 
 struct cmsvd_matrix {
@@ -162,13 +163,22 @@ size_t gram_partials_size(int c1, int c2, int64_t n, int sm_count);
 size_t gram_partials_cap(int c, int sm_count);
 // Z (n x c2, ldz) = X (n x c1, ldx) * W (c1 x c2, ldw)
 int gemm_nn(const double* X, int64_t ldx, const double* W, int64_t ldw, double* Z, int64_t ldz,
-            int64_t n, int c1, int c2, cudaStream_t s);
-// Deflated orthogonalization X (n x c) = Q (n x c', ld c') R (c' x c); see dense.cu.
+            int64_t n, int c1, int c2, cudaStream_t s, int upper = 0);
+// Orthogonalization X (n x c) = Q (n x c', ld c') R (c' x c, row-major); see dense.cu.
+// deflate = 0 tries CholeskyQR2 first and falls back to the deflated form when
+// X is too ill-conditioned for it. ints: 8 device ints of scratch (8-byte aligned).
 size_t orth_scratch(int c, int64_t n, int sm_count);
-int orth_deflate(const double* X, int64_t ldx, int64_t n, int c, double* Q, double* R, int* c_out, double* scratch,
-                 int* flag, int* cp_dev, int* pinned, int sm_count, cudaStream_t s);
-// One-sided Jacobi SVD of Bm (rows x cols, row-major): Xc (column-major, rows x cols)
-// = Bm V, sv_j = ||Xc_j||, V (cols x cols, column-major), perm sorts sv descending.
-int jacobi_svd(const double* Bm, int rows, int cols, double* Xc, double* V, double* sv, int* perm, cudaStream_t s);
+int orth_qr(const double* X, int64_t ldx, int64_t n, int c, double* Q, double* R, int* c_out, double* scratch, int* ints,
+            int deflate, cmsvd_context* ctx);
+// One-sided Jacobi SVD of Bm (brows x bcols, row-major). trans = 0 rotates the columns of
+// Bm: Bm V = Xc (column-major brows x bcols), V bcols x bcols. trans = 1 rotates the
+// columns of Bm^T: Bm^T V = Xc (column-major bcols x brows), V brows x brows holds the
+// left singular vectors of Bm. sv_j = ||Xc_j||, perm sorts sv descending.
+// flag2: 16 bytes of device scratch (8-byte aligned + 8).
+int jacobi_svd(const double* Bm, int brows, int bcols, int trans, double* Xc, double* V, double* sv, int* perm,
+               int* flag2, cmsvd_context* ctx);
+cudaGraphExec_t graph_cache_get(cmsvd_context* ctx, const void* a, const void* b, const void* c, int x, int y);
+void graph_cache_put(cmsvd_context* ctx, const void* a, const void* b, const void* c, int x, int y, cudaGraphExec_t g);
+void graph_cache_clear(cmsvd_context* ctx);
 
 }  // namespace cmsvd

@@ -10,46 +10,47 @@
 
 namespace cmsvd {
 
-// ---- step 3: sorted sigma_S, rank r, and the c x r block that maps Q_S to U_S1
-// Xc: column-major rows x c (columns = R_S V, rows = c'); Wsel: rows x r, row-major.
-__global__ void k_truncate(const double* __restrict__ Xc, const double* __restrict__ sv, const int* __restrict__ perm, int c,
-                           int rows, double delta, double* __restrict__ sS, double* __restrict__ Wsel,
-                           int* __restrict__ r_out) {
+// ---- step 3: sorted sigma_S, rank r, and the c' x r block that maps Q_S to U_S1.
+// V (column-major cp x cp) holds the left singular vectors of R_S (Jacobi on R_S^T).
+__global__ void k_truncate(const double* __restrict__ V, const double* __restrict__ sv, const int* __restrict__ perm, int cp,
+                           double delta, double* __restrict__ sS, double* __restrict__ Wsel, int* __restrict__ r_out) {
     __shared__ int r;
     const int t = threadIdx.x;
     if (t == 0) {
         const double s1 = sv[perm[0]];
         int k = 0;
-        while (k < c && k < rows && sv[perm[k]] > delta * s1) ++k;
+        while (k < cp && sv[perm[k]] > delta * s1) ++k;
         r = k;
         *r_out = k;
     }
     __syncthreads();
-    for (int i = t; i < c; i += blockDim.x) sS[i] = sv[perm[i]];
-    for (int e = t; e < rows * r; e += blockDim.x) {
+    for (int i = t; i < cp; i += blockDim.x) sS[i] = sv[perm[i]];
+    for (int e = t; e < cp * r; e += blockDim.x) {
         const int k = e / r, i = e % r;                  // Wsel[k][i] = (left vector i)_k
-        Wsel[e] = Xc[(size_t)perm[i] * rows + k] / sv[perm[i]];
+        Wsel[e] = V[(size_t)perm[i] * cp + k];
     }
 }
 
-// ---- step 5: candidate selection in descending phi order
-// Xb: column-major rows x r (B Q = Xb); Vb: r x r column-major (Q); Pc: rows x k, Qc: r x k (row-major).
+// ---- step 5: candidate selection in descending phi order. Jacobi ran on B^T (rp x r):
+// B^T P = Xb, so P (Vb, column-major rp x rp) are the left singular vectors,
+// phi_j = ||Xb_j|| and q_j = Xb_j / phi_j (length r) the right ones.
 __global__ void k_select(const double* __restrict__ Xb, const double* __restrict__ Vb, const double* __restrict__ svb,
-                         const int* __restrict__ perm, int r, int rows, const double* __restrict__ sS, double a, double b,
+                         const int* __restrict__ perm, int rp, int r, const double* __restrict__ sS, double a, double b,
                          double eps_tau, double* __restrict__ Pc, double* __restrict__ Qc, double* __restrict__ phic,
                          double* __restrict__ tauc, int* __restrict__ counts, int* __restrict__ cand) {
     __shared__ int nc;
     const int t = threadIdx.x;
     if (t == 0) {
         int k = 0, inside = 0;
-        for (int ii = 0; ii < r; ++ii) {
+        for (int ii = 0; ii < rp; ++ii) {
             const int j = perm[ii];
             const double phi = svb[j];
             if (!(phi >= a && phi <= b) || !(phi > 0.0)) continue;
             ++inside;
+            // tau_i = q^T q / q^T Sigma_S1^{-1} q (scale-free, so the raw column is used)
             double num = 0.0, den = 0.0;
             for (int i = 0; i < r; ++i) {
-                const double q = Vb[(size_t)j * r + i];
+                const double q = Xb[(size_t)j * r + i];
                 num += q * q;
                 den += q * q / sS[i];
             }
@@ -66,14 +67,14 @@ __global__ void k_select(const double* __restrict__ Xb, const double* __restrict
     }
     __syncthreads();
     const int k = nc;
-    for (int e = t; e < rows * k; e += blockDim.x) {
-        const int i = e / k, c = e % k;                  // row-major rows x k
-        const int j = cand[c];
-        Pc[e] = Xb[(size_t)j * rows + i] / svb[j];
+    for (int e = t; e < rp * k; e += blockDim.x) {
+        const int i = e / k, c = e % k;                  // Pc row-major rp x k
+        Pc[e] = Vb[(size_t)cand[c] * rp + i];
     }
     for (int e = t; e < r * k; e += blockDim.x) {
-        const int i = e / k, c = e % k;                  // row-major r x k
-        Qc[e] = Vb[(size_t)cand[c] * r + i];
+        const int i = e / k, c = e % k;                  // Qc row-major r x k
+        const int j = cand[c];
+        Qc[e] = Xb[(size_t)j * r + i] / svb[j];
     }
 }
 
@@ -241,16 +242,15 @@ int rayleigh_ritz(cmsvd_matrix* M, const double* S, int64_t lds, int c, double a
     RitzBufs bf;
     ritz_alloc(bf, ws, m, n, c, ctx->sm_count);
     if (!ws.fits()) { set_error("workspace too small"); return CMSVD_WORKSPACE_TOO_SMALL; }
-    int* flag = bf.ints + 8;
     CM_CUDA(cudaMemsetAsync(bf.ints, 0, sizeof(int) * 32, s));
     // step 3: S^ = Q_S R_S, SVD of R_S, truncation
     int cp = 0;
-    CM_TRY(orth_deflate(S, lds, n, c, bf.Qs, bf.Rs, &cp, bf.chol, flag, bf.ints + 12, ctx->pinned, ctx->sm_count, s));
+    CM_TRY(orth_qr(S, lds, n, c, bf.Qs, bf.Rs, &cp, bf.chol, bf.ints + 16, 1, ctx));
     if (cp <= 0) { st->found = 0; return CMSVD_OK; }
-    CM_TRY(jacobi_svd(bf.Rs, cp, c, bf.Xc, bf.Vr, bf.svR, bf.permR, s));
+    CM_TRY(jacobi_svd(bf.Rs, cp, c, 1, bf.Xc, bf.Vr, bf.svR, bf.permR, bf.ints + 24, ctx));
     {
         ProfScope ps_t(CMSVD_PROF_SMALL, s, 16.0 * c * c, 0.0);
-        k_truncate<<<1, 256, 0, s>>>(bf.Xc, bf.svR, bf.permR, c, cp, p->delta, bf.sS, bf.Wsel, bf.ints);
+        k_truncate<<<1, 256, 0, s>>>(bf.Vr, bf.svR, bf.permR, cp, p->delta, bf.sS, bf.Wsel, bf.ints);
         CM_LAUNCH();
     }
     int h[4];
@@ -264,14 +264,14 @@ int rayleigh_ritz(cmsvd_matrix* M, const double* S, int64_t lds, int c, double a
     // step 4: A V~ = U~ B
     CM_TRY(spmm(M->A, r, bf.Vt, r, bf.Y, r, s));
     int rp = 0;
-    CM_TRY(orth_deflate(bf.Y, r, m, r, bf.Ut, bf.B, &rp, bf.chol, flag, bf.ints + 12, ctx->pinned, ctx->sm_count, s));
+    CM_TRY(orth_qr(bf.Y, r, m, r, bf.Ut, bf.B, &rp, bf.chol, bf.ints + 16, 0, ctx));
     cudaEventRecord(ev[2], s);
     if (rp <= 0) { st->found = 0; return CMSVD_OK; }
     // step 5: B = P Phi Q^T, selection, Ritz vectors, residuals
-    CM_TRY(jacobi_svd(bf.B, rp, r, bf.Xb, bf.Vb, bf.svB, bf.permB, s));
+    CM_TRY(jacobi_svd(bf.B, rp, r, 1, bf.Xb, bf.Vb, bf.svB, bf.permB, bf.ints + 24, ctx));
     {
         ProfScope ps_s(CMSVD_PROF_SMALL, s, 24.0 * r * r, 2.0 * r * r);
-        k_select<<<1, 256, 0, s>>>(bf.Xb, bf.Vb, bf.svB, bf.permB, r, rp, bf.sS, a, b, p->eps_tau, bf.Pc, bf.Qc, bf.phic,
+        k_select<<<1, 256, 0, s>>>(bf.Xb, bf.Vb, bf.svB, bf.permB, rp, r, bf.sS, a, b, p->eps_tau, bf.Pc, bf.Qc, bf.phic,
                                    bf.tauc, bf.ints + 1, bf.cand);
         CM_LAUNCH();
     }
@@ -300,12 +300,7 @@ int rayleigh_ritz(cmsvd_matrix* M, const double* S, int64_t lds, int c, double a
         }
     }
     cudaEventRecord(ev[3], s);
-    int hf[1];
-    CM_TRY(read_ints(ctx, flag, 1, hf));
     st->found = t;
-    if (hf[0]) {
-        set_error("CholeskyQR met a non-positive pivot (numerically rank-deficient block)");
-    }
     return CMSVD_OK;
 }
 

@@ -81,6 +81,26 @@ def test_spmm_transpose_deterministic(B, ctx):
     M.close()
 
 
+# ----------------------------------------------------------------------------- Gram (rows a7-a8)
+@pytest.mark.parametrize("n,c1,c2", [(1, 1, 1), (37, 5, 9), (1000, 64, 64), (3001, 80, 80), (20000, 256, 256),
+                                      (777, 130, 7)])
+def test_gram_parity(B, ctx, n, c1, c2):
+    rng = np.random.default_rng(n + c1)
+    X = dev(rng.standard_normal((n, c1 + 3)))[:, :c1]      # leading dimension c1 + 3
+    Xh = X.cpu().numpy()
+    Y = X if c1 == c2 else dev(rng.standard_normal((n, c2)))
+    Yh = Y.cpu().numpy()
+    G = torch.empty((c1, c2), dtype=torch.float64, device="cuda")
+    ws = torch.empty(B.cmsvd_gram_workspace_size(ctx.handle, n, c1, c2), dtype=torch.uint8, device="cuda")
+    B.cmsvd_gram(ctx.handle, X, Y, G, ws)
+    ref = Xh.T @ Yh
+    scale = np.abs(Xh).T @ np.abs(Yh)
+    assert np.max(np.abs(G.cpu().numpy() - ref) / scale) < 1e-13
+    G2 = torch.empty_like(G)
+    B.cmsvd_gram(ctx.handle, X, Y, G2, ws)
+    assert torch.equal(G, G2)                                 # deterministic
+
+
 # ----------------------------------------------------------------------------- quadrature (row a1)
 @pytest.mark.parametrize("variant", ["linear", "nt"])
 @pytest.mark.parametrize("N", [2, 16, 32, 128])
