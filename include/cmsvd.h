@@ -78,6 +78,9 @@ typedef struct cmsvd_params {
     int32_t check_every;  /* Krylov iterations between host convergence checks (default 48) */
     int32_t direct_max_block; /* AUTO picks DIRECT when the largest component has at most this many columns (default 32) */
     int32_t profile;      /* 1: time every kernel class with CUDA events and fill the prof_* statistics (default 0) */
+    int32_t refine;       /* Krylov solver: up to this many rounds of FP64 iterative refinement of every shifted
+                             solve, R_j = X - (s_j I - A^T A) Y_j, (s_j I - A^T A) E_j = R_j, Y_j += E_j, until
+                             max ||R_j|| / ||X|| <= tol_solve (default 0: none) */
 } cmsvd_params;
 
 /* Kernel classes of the prof_* statistics (index into the arrays). */
@@ -111,6 +114,9 @@ typedef struct cmsvd_stats {
     double ms_qr;             /* step 4 */
     double ms_ritz;           /* step 5, selection and residuals */
     int64_t kernel_launches;  /* kernels launched by this solve (graph nodes included) */
+    int32_t refine_rounds;    /* refinement rounds run (last filter application) */
+    int32_t pad_;
+    double refine_residual;   /* max ||R_j|| / ||X|| after refinement (0 without refinement) */
     /* With params.profile = 1, per kernel class: event-timed GPU ms, launches, and the
        algorithmic bytes (compulsory DRAM traffic) and FP64 flops of those launches. */
     double prof_ms[CMSVD_PROF_CLASSES];

@@ -31,7 +31,7 @@ class cmsvd_params(C.Structure):
                 ("variant", C.c_int32), ("solver", C.c_int32), ("precision", C.c_int32),
                 ("max_iter", C.c_int32), ("tol_solve", C.c_double), ("tol_triplet", C.c_double),
                 ("norm_A", C.c_double), ("check_every", C.c_int32), ("direct_max_block", C.c_int32),
-                ("profile", C.c_int32)]
+                ("profile", C.c_int32), ("refine", C.c_int32)]
 
 PROFILE_CLASSES = ("spmm", "krylov", "direct", "gram", "gemm", "small_dense", "other", "jacobi")
 
@@ -43,6 +43,7 @@ class cmsvd_stats(C.Structure):
                 ("norm_A", C.c_double), ("sigma_S1", C.c_double), ("max_res_u", C.c_double),
                 ("max_res_v", C.c_double), ("ms_solve", C.c_double), ("ms_truncate", C.c_double),
                 ("ms_qr", C.c_double), ("ms_ritz", C.c_double), ("kernel_launches", C.c_int64),
+                ("refine_rounds", C.c_int32), ("pad_", C.c_int32), ("refine_residual", C.c_double),
                 ("prof_ms", C.c_double * 8), ("prof_launches", C.c_int64 * 8), ("prof_bytes", C.c_double * 8),
                 ("prof_flops", C.c_double * 8)]
 

@@ -74,6 +74,7 @@ int check_params(const cmsvd_matrix* A, double a, double b, const cmsvd_params* 
     if (p->variant == CMSVD_NT && !(a > 0.0)) { set_error("the exp transform (NT variant) needs a > 0"); return CMSVD_INVALID_ARG; }
     if (!(p->alpha > 0.0)) { set_error("alpha must be > 0"); return CMSVD_INVALID_ARG; }
     if (p->max_iter < 1) { set_error("max_iter must be >= 1"); return CMSVD_INVALID_ARG; }
+    if (p->refine < 0 || p->refine > 100) { set_error("refine must be in [0, 100]"); return CMSVD_INVALID_ARG; }
     if (!(p->delta >= 0.0) || !(p->eps_tau >= 0.0) || !(p->tol_triplet > 0.0) || !(p->tol_solve > 0.0)) {
         set_error("delta, eps_tau >= 0 and tol_solve, tol_triplet > 0 required");
         return CMSVD_INVALID_ARG;
@@ -180,6 +181,8 @@ int run_moments(cmsvd_matrix* A, double a, double b, const cmsvd_params* p, cons
         CM_TRY(krylov_moments(A, p, pl.quad, p->M + 1, V_in, p->L, pl.S, lds, ws, &so));
         st->krylov_iters = so.iters;
         st->converged = so.converged;
+        st->refine_rounds = so.refine_rounds;
+        st->refine_residual = so.refine_residual;
         if (!so.converged) status = CMSVD_NOT_CONVERGED;
     }
     ws.off = mark;
@@ -228,6 +231,7 @@ int cmsvd_params_default(cmsvd_params* p) {
     p->check_every = 48;
     p->direct_max_block = 32;
     p->profile = 0;
+    p->refine = 0;
     return CMSVD_OK;
 }
 
@@ -352,7 +356,10 @@ int cmsvd_quadrature(cmsvd_context* ctx, double a, double b, int32_t N, int32_t 
 int cmsvd_gram_workspace_size(cmsvd_context* ctx, int64_t n, int32_t c1, int32_t c2, size_t* bytes) {
     if (!ctx || !bytes) { set_error("NULL argument"); return CMSVD_INVALID_ARG; }
     if (n < 1 || c1 < 1 || c2 < 1 || c1 > 4096 || c2 > 4096) { set_error("need n >= 1 and 1 <= c1, c2 <= 4096"); return CMSVD_INVALID_ARG; }
-    *bytes = sizeof(double) * gram_partials_size(c1, c2, n, ctx->sm_count) + 256;
+    // X == Y (same buffer and leading dimension) selects the symmetric plan, which may use more chunks
+    size_t a = gram_partials_size(c1, c2, n, ctx->sm_count, 0);
+    size_t b = c1 == c2 ? gram_partials_size(c1, c2, n, ctx->sm_count, 1) : 0;
+    *bytes = sizeof(double) * (a > b ? a : b) + 256;
     return CMSVD_OK;
 }
 

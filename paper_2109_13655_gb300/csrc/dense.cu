@@ -92,10 +92,10 @@ static void gram_plan(int c1, int c2, int64_t n, int sm_count, int* nchunks, int
     if (*nchunks < 1) *nchunks = 1;
 }
 
-size_t gram_partials_size(int c1, int c2, int64_t n, int sm_count) {
+size_t gram_partials_size(int c1, int c2, int64_t n, int sm_count, int sym) {
     int nc;
     int64_t rpc;
-    gram_plan(c1, c2, n, sm_count, &nc, &rpc);
+    gram_plan(c1, c2, n, sm_count, &nc, &rpc, sym);
     return (size_t)nc * c1 * c2;
 }
 
@@ -234,17 +234,26 @@ __global__ void __launch_bounds__(1024) k_chol(const double* __restrict__ G, int
     }
 }
 
-// Ri = R^{-1} for upper-triangular R (row-major); one thread per column.
-__global__ void k_trinv(const double* __restrict__ R, int c, double* __restrict__ Ri) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+// Ri = R^{-1} for upper-triangular R (row-major): one 128-thread CTA per column j,
+// back substitution x_i = -(sum_{k=i+1..j} R_ik x_k) / R_ii with a block reduction per i.
+__global__ void __launch_bounds__(128) k_trinv(const double* __restrict__ R, int c, double* __restrict__ Ri) {
+    __shared__ double x[1024];
+    __shared__ double sh[4];
+    const int j = blockIdx.x, t = threadIdx.x;
     if (j >= c) return;
-    for (int i = j + 1; i < c; ++i) Ri[(size_t)i * c + j] = 0.0;
-    Ri[(size_t)j * c + j] = 1.0 / R[(size_t)j * c + j];
+    for (int i = t; i < c; i += 128) Ri[(size_t)i * c + j] = 0.0;
+    if (t == 0) x[j] = 1.0 / R[(size_t)j * c + j];
+    __syncthreads();
     for (int i = j - 1; i >= 0; --i) {
         double s = 0.0;
-        for (int k = i + 1; k <= j; ++k) s = __fma_rn(R[(size_t)i * c + k], Ri[(size_t)k * c + j], s);
-        Ri[(size_t)i * c + j] = -s / R[(size_t)i * c + i];
+        for (int k = i + 1 + t; k <= j; k += 128) s = __fma_rn(R[(size_t)i * c + k], x[k], s);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((t & 31) == 0) sh[t >> 5] = s;
+        __syncthreads();
+        if (t == 0) x[i] = -((sh[0] + sh[1]) + (sh[2] + sh[3])) / R[(size_t)i * c + i];
+        __syncthreads();
     }
+    for (int i = t; i <= j; i += 128) Ri[(size_t)i * c + j] = x[i];
 }
 
 // ----------------------------------------------------------------------------- one-sided Jacobi SVD
@@ -254,13 +263,12 @@ __global__ void k_trinv(const double* __restrict__ R, int c, double* __restrict_
 // Xc_j / sv_j the left and V_j the right singular vectors. Round-robin
 // ordering; one warp per pair; perm sorts sv descending (stable).
 __global__ void __launch_bounds__(1024) k_jacobi(double* __restrict__ Xc, int rows, int cols, double* __restrict__ V,
-                                                 const double* __restrict__ fro2, double* __restrict__ sv,
+                                                 const double* __restrict__ fro2, double tol, double* __restrict__ sv,
                                                  int* __restrict__ perm) {
     __shared__ int rotated;
     const int t = threadIdx.x, nt = blockDim.x;
     const int lane = t & 31, warp = t >> 5, nwarps = nt >> 5;
     const int np = (cols + 1) / 2 * 2;            // players (one dummy when cols is odd)
-    const double tol = fmax(1e-15, rows * 2.220446049250313e-16);
     const double negl = 1e-36 * *fro2;
     for (int sweep = 0; sweep < 60; ++sweep) {
         if (t == 0) rotated = 0;
@@ -334,21 +342,25 @@ __global__ void __launch_bounds__(1024) k_jacobi(double* __restrict__ Xc, int ro
 // round are disjoint), one launch per round; a sweep is np-1 launches and the
 // host checks the "rotated" flag after every sweep. Columns whose squared norm is
 // below negl (1e-36 ||Bm||_F^2) are treated as zero.
-__device__ __forceinline__ double block_sum256(double v, double* sh) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+// Sums three values over a 128-thread block (fixed order: deterministic).
+__device__ __forceinline__ void block_sum3_128(double& a, double& b, double& c, double (*sh)[4]) {
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) { sh[0][w] = a; sh[1][w] = b; sh[2][w] = c; }
     __syncthreads();
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-    __syncthreads();
-    double t = 0.0;
-#pragma unroll
-    for (int w = 0; w < 8; ++w) t += sh[w];
-    return t;
+    a = (sh[0][0] + sh[0][1]) + (sh[0][2] + sh[0][3]);
+    b = (sh[1][0] + sh[1][1]) + (sh[1][2] + sh[1][3]);
+    c = (sh[2][0] + sh[2][1]) + (sh[2][2] + sh[2][3]);
 }
 
-__global__ void __launch_bounds__(256) k_jacobi_round(double* __restrict__ Xc, double* __restrict__ V, int rows, int cols,
+__global__ void __launch_bounds__(128) k_jacobi_round(double* __restrict__ Xc, double* __restrict__ V, int rows, int cols,
                                                       int np, int round, double tol, const double* __restrict__ fro2,
                                                       int* __restrict__ rotated) {
-    __shared__ double sh[3][8];
+    __shared__ double sh[3][4];
     const int k = blockIdx.x;
     int p, q;
     if (k == 0) { p = round; q = np - 1; }
@@ -358,28 +370,26 @@ __global__ void __launch_bounds__(256) k_jacobi_round(double* __restrict__ Xc, d
     double* xp = Xc + (size_t)p * rows;
     double* xq = Xc + (size_t)q * rows;
     double al = 0.0, be = 0.0, ga = 0.0;
-    for (int i = threadIdx.x; i < rows; i += 256) {
+    for (int i = threadIdx.x; i < rows; i += 128) {
         const double a = xp[i], b = xq[i];
         al = __fma_rn(a, a, al);
         be = __fma_rn(b, b, be);
         ga = __fma_rn(a, b, ga);
     }
-    al = block_sum256(al, sh[0]);
-    be = block_sum256(be, sh[1]);
-    ga = block_sum256(ga, sh[2]);
+    block_sum3_128(al, be, ga, sh);
     const double negl = 1e-36 * *fro2;
     if (!(fabs(ga) > tol * sqrt(al * be)) || !(al > negl) || !(be > negl)) return;
     const double zeta = (be - al) / (2.0 * ga);
     const double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
     const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
-    for (int i = threadIdx.x; i < rows; i += 256) {
+    for (int i = threadIdx.x; i < rows; i += 128) {
         const double a = xp[i], b = xq[i];
         xp[i] = cs * a - sn * b;
         xq[i] = sn * a + cs * b;
     }
     double* vp = V + (size_t)p * cols;
     double* vq = V + (size_t)q * cols;
-    for (int i = threadIdx.x; i < cols; i += 256) {
+    for (int i = threadIdx.x; i < cols; i += 128) {
         const double va = vp[i], vb = vq[i];
         vp[i] = cs * va - sn * vb;
         vq[i] = sn * va + cs * vb;
@@ -438,7 +448,7 @@ __global__ void k_jacobi_init_t(const double* __restrict__ Bm, int brows, int bc
 }
 
 int jacobi_svd(const double* Bm, int brows, int bcols, int trans, double* Xc, double* V, double* sv, int* perm,
-               int* flag2, cmsvd_context* ctx) {
+               int* flag2, cmsvd_context* ctx, double tol_in) {
     cudaStream_t s = ctx->s;
     const int rows = trans ? bcols : brows, cols = trans ? brows : bcols;
     double* fro2 = (double*)(flag2 + 2);   // flag2: 16 bytes of scratch (int rotated, pad, double)
@@ -448,15 +458,16 @@ int jacobi_svd(const double* Bm, int brows, int bcols, int trans, double* Xc, do
         CM_LAUNCH();
     }
     const int np = (cols + 1) / 2 * 2;
-    const double tol = fmax(1e-15, rows * 2.220446049250313e-16);
+    const double tol = tol_in > 0.0 ? tol_in : fmax(1e-15, rows * 2.220446049250313e-16);
     if (cols <= 96) {
         ProfScope ps(CMSVD_PROF_JACOBI, s, 16.0 * (rows + cols) * cols, 0.0);
-        k_jacobi<<<1, 1024, 0, s>>>(Xc, rows, cols, V, fro2, sv, perm);
+        k_jacobi<<<1, 1024, 0, s>>>(Xc, rows, cols, V, fro2, tol, sv, perm);
         CM_LAUNCH();
         return CMSVD_OK;
     }
     // one sweep = memset(flag) + np-1 round kernels, captured once per shape and buffers
-    cudaGraphExec_t ge = graph_cache_get(ctx, Xc, V, flag2, rows, cols);
+    const int key_cols = tol_in > 0.0 ? -cols : cols;    // loose and tight sweeps are different graphs
+    cudaGraphExec_t ge = graph_cache_get(ctx, Xc, V, flag2, rows, key_cols);
     if (!ge) {
         cudaGraph_t g = nullptr;
         Profiler& pr = prof();
@@ -465,7 +476,7 @@ int jacobi_svd(const double* Bm, int brows, int bcols, int trans, double* Xc, do
         if (ce == cudaSuccess) {
             cudaMemsetAsync(flag2, 0, sizeof(int), s);
             for (int round = 0; round < np - 1; ++round)
-                k_jacobi_round<<<np / 2, 256, 0, s>>>(Xc, V, rows, cols, np, round, tol, fro2, flag2);
+                k_jacobi_round<<<np / 2, 128, 0, s>>>(Xc, V, rows, cols, np, round, tol, fro2, flag2);
             ce = cudaStreamEndCapture(s, &g);
         }
         pr.capture_depth--;
@@ -473,7 +484,7 @@ int jacobi_svd(const double* Bm, int brows, int bcols, int trans, double* Xc, do
         ce = cudaGraphInstantiate(&ge, g, 0);
         cudaGraphDestroy(g);
         if (ce != cudaSuccess) return cuda_fail(ce, "instantiate Jacobi sweep", __FILE__, __LINE__);
-        graph_cache_put(ctx, Xc, V, flag2, rows, cols, ge);
+        graph_cache_put(ctx, Xc, V, flag2, rows, key_cols, ge);
     }
     for (int sweep = 0; sweep < 40; ++sweep) {
         {
@@ -570,9 +581,8 @@ int chol_adaptive(OrthCtx& o, int cc, bool shifted, double* R) {
 }
 
 int trinv(OrthCtx& o, const double* R, int cc) {
-    const int tpb = cc < 1024 ? ((cc + 31) / 32 * 32) : 1024;
     ProfScope ps(CMSVD_PROF_SMALL, o.s, 16.0 * cc * cc, cc * (double)cc * cc / 3.0);
-    k_trinv<<<(cc + tpb - 1) / tpb, tpb, 0, o.s>>>(R, cc, o.Ri);
+    k_trinv<<<cc, 128, 0, o.s>>>(R, cc, o.Ri);
     CM_LAUNCH();
     return CMSVD_OK;
 }
@@ -648,7 +658,8 @@ int orth_qr(const double* X, int64_t ldx, int64_t n, int c, double* Q, double* R
     // deflation
     CM_TRY(gram(T, c, c, T, c, c, n, G, part, o.pcap, ctx->sm_count, s));
     CM_TRY(chol_adaptive(o, c, true, Rb));
-    CM_TRY(jacobi_svd(Rb, c, c, 1, Xj, Vj, sv, perm, flag2, ctx));
+    // the deflation only separates rounding-level directions (lambda < 1e-10) from O(1) ones
+    CM_TRY(jacobi_svd(Rb, c, c, 1, Xj, Vj, sv, perm, flag2, ctx, 1e-7));
     {
         ProfScope ps(CMSVD_PROF_SMALL, s, 24.0 * c * c, 0.0);
         k_deflate<<<1, 256, 0, s>>>(Xj, sv, perm, c, 1e-10, T3, R3, cp_dev);

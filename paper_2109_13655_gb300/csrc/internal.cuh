@@ -146,7 +146,13 @@ int quadrature_device(const QuadParams& q, double2* quad, cudaStream_t s);
 
 // ----------------------------------------------------------------------------- filter solves
 // S (n x L(M+1), ld = L(M+1)) = 2 Re sum_j w_j scaled_j^k (s_j I - A^T A)^{-1} X  for k = 0..Mk-1
-struct SolveOut { int64_t iters = 0; int converged = 1; int breakdown = 0; double lambda_max = 0.0; };
+struct SolveOut {
+    int64_t iters = 0;
+    int converged = 1;
+    int breakdown = 0;
+    int refine_rounds = 0;
+    double refine_residual = 0.0;
+};
 size_t krylov_workspace(const cmsvd_matrix* A, const cmsvd_params* p);
 int krylov_moments(cmsvd_matrix* A, const cmsvd_params* p, const double2* quad, int Mk,
                    const double* X, int64_t ldx, double* S, int64_t lds, Arena& ws, SolveOut* out);
@@ -159,7 +165,7 @@ int norm_estimate(cmsvd_matrix* A, Arena& ws, double* norm_out);
 // G (c1 x c2, row-major) = X^T Y, X: n x c1 (ldx), Y: n x c2 (ldy). Deterministic.
 int gram(const double* X, int64_t ldx, int c1, const double* Y, int64_t ldy, int c2, int64_t n,
          double* G, double* partials, size_t partials_cap, int sm_count, cudaStream_t s);
-size_t gram_partials_size(int c1, int c2, int64_t n, int sm_count);
+size_t gram_partials_size(int c1, int c2, int64_t n, int sm_count, int sym = 0);
 size_t gram_partials_cap(int c, int sm_count);
 // Z (n x c2, ldz) = X (n x c1, ldx) * W (c1 x c2, ldw)
 int gemm_nn(const double* X, int64_t ldx, const double* W, int64_t ldw, double* Z, int64_t ldz,
@@ -175,8 +181,9 @@ int orth_qr(const double* X, int64_t ldx, int64_t n, int c, double* Q, double* R
 // columns of Bm^T: Bm^T V = Xc (column-major bcols x brows), V brows x brows holds the
 // left singular vectors of Bm. sv_j = ||Xc_j||, perm sorts sv descending.
 // flag2: 16 bytes of device scratch (8-byte aligned + 8).
+// tol > 0 overrides the rotation threshold max(1e-15, rows u) (loose sweeps for the deflation).
 int jacobi_svd(const double* Bm, int brows, int bcols, int trans, double* Xc, double* V, double* sv, int* perm,
-               int* flag2, cmsvd_context* ctx);
+               int* flag2, cmsvd_context* ctx, double tol = 0.0);
 cudaGraphExec_t graph_cache_get(cmsvd_context* ctx, const void* a, const void* b, const void* c, int x, int y);
 void graph_cache_put(cmsvd_context* ctx, const void* a, const void* b, const void* c, int x, int y, cudaGraphExec_t g);
 void graph_cache_clear(cmsvd_context* ctx);

@@ -99,6 +99,13 @@ struct Lz {
     double* partials = nullptr;// [nblk][L]
     int nblk = 0;
     const double2* quad = nullptr;
+    // pass-2 accumulation of explicit solutions (refinement): 0 = moments into S,
+    // 1 = Yacc[r][j][l] += y_{i,j,l} q_i (all shifts), 2 = correction for shift jsel:
+    // columns l and Lorig + l carry Re and Im of the right-hand side,
+    // Yacc[r][jsel][l] += y_l q_l + i y_{Lorig+l} q_{Lorig+l}.
+    int mode = 0;
+    double2* Yacc = nullptr;   // [n][Jtot][Lorig]
+    int Jtot = 0, Lorig = 0, jsel = 0;
 };
 
 static dim3 lz_block(int L) {
@@ -372,6 +379,137 @@ __global__ void k_lz2_step(Lz z, const double* __restrict__ Qk, const double* __
     }
 }
 
+// pass 2 with accumulation of explicit solutions (refinement modes 1 and 2)
+__global__ void k_lz2_step_acc(Lz z, const double* __restrict__ Qk, const double* __restrict__ Qp, double* __restrict__ W) {
+    const int i = z.ctrl[C_IT2];
+    if (i >= z.ctrl[C_KMAX]) return;
+    const int l = threadIdx.x;
+    const int K = z.Kcol[l];
+    const bool live = i < K;
+    const bool next = i + 1 < K;
+    const double a = z.alpha[(size_t)i * z.L + l];
+    const double b = i > 0 ? z.beta[(size_t)i * z.L + l] : 0.0;
+    const double bn = next ? z.beta[(size_t)(i + 1) * z.L + l] : 1.0;
+    const size_t JL = (size_t)z.J * z.L;
+    // mode 2: the thread of column l < Lorig also owns column Lorig + l
+    const int l2 = l + z.Lorig;
+    const bool pair = z.mode == 2 && l < z.Lorig;
+    const bool live2 = pair && i < z.Kcol[l2];
+    double2 y1 = make_double2(0, 0), y2 = make_double2(0, 0);
+    if (z.mode == 2) {
+        if (pair && live) y1 = z.Ybuf[i * JL + l];
+        if (live2) y2 = z.Ybuf[i * JL + l2];
+    }
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; r < z.n; r += (int64_t)gridDim.x * blockDim.y) {
+        const int64_t o = r * z.L + l;
+        const double q = Qk[o];
+        if (z.mode == 1) {
+            if (live) {
+                double2* yr = z.Yacc + ((size_t)r * z.Jtot) * z.Lorig + l;
+                for (int j = 0; j < z.J; ++j) {
+                    const double2 c = z.Ybuf[i * JL + (size_t)j * z.L + l];
+                    double2 v = yr[(size_t)j * z.Lorig];
+                    v.x = __fma_rn(c.x, q, v.x);
+                    v.y = __fma_rn(c.y, q, v.y);
+                    yr[(size_t)j * z.Lorig] = v;
+                }
+            }
+        } else if (pair && (live || live2)) {
+            const double q2 = Qk[r * z.L + l2];
+            double2* yp = z.Yacc + ((size_t)r * z.Jtot + z.jsel) * z.Lorig + l;
+            double2 v = *yp;
+            // (y1 q) + i (y2 q2) = (y1.x q - y2.y q2) + i (y1.y q + y2.x q2)
+            v.x = __fma_rn(y1.x, q, __fma_rn(-y2.y, q2, v.x));
+            v.y = __fma_rn(y1.y, q, __fma_rn(y2.x, q2, v.y));
+            *yp = v;
+        }
+        double w = 0.0;
+        if (next) {
+            w = W[o];
+            if (i > 0) w = __fma_rn(-b, Qp[o], w);
+            w = __fma_rn(-a, q, w);
+            w = __ddiv_rn(w, bn);
+        }
+        W[o] = w;
+    }
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) last = (atomicAdd(z.ctrl + C_TICKET2, 1) == (int)gridDim.x - 1);
+    __syncthreads();
+    if (last && threadIdx.x == 0 && threadIdx.y == 0) {
+        z.ctrl[C_TICKET2] = 0;
+        z.ctrl[C_IT2] = i + 1;
+    }
+}
+
+// R_j = X - (s_j I - H) Y_j (FP64), written as real blocks Rall[j] = [Re R_j | Im R_j]
+// (n x 2L), and per (j, l) partial sums of |R_j|^2 over row chunks (blockIdx.x).
+// HY is H Y with Y viewed as a real n x 2JL block.
+__global__ void k_residual(const double2* __restrict__ Y, const double2* __restrict__ HY, const double* __restrict__ X,
+                           int64_t ldx, const double2* __restrict__ quad, int64_t n, int J, int L,
+                           double* __restrict__ Rall, double* __restrict__ part) {
+    const int jl = blockIdx.y * blockDim.x + threadIdx.x;
+    if (jl >= J * L) return;
+    const int j = jl / L, l = jl % L;
+    const double2 sj = quad[3 * j];
+    const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t r0 = (int64_t)blockIdx.x * chunk, r1 = r0 + chunk < n ? r0 + chunk : n;
+    double acc = 0.0;
+    for (int64_t r = r0; r < r1; ++r) {
+        const double2 y = Y[(size_t)r * J * L + jl];
+        const double2 hy = HY[(size_t)r * J * L + jl];
+        const double x = X[r * ldx + l];
+        const double re = x - (sj.x * y.x - sj.y * y.y) + hy.x;
+        const double im = -(sj.x * y.y + sj.y * y.x) + hy.y;
+        Rall[((size_t)j * n + r) * 2 * L + l] = re;
+        Rall[((size_t)j * n + r) * 2 * L + L + l] = im;
+        acc = __fma_rn(re, re, __fma_rn(im, im, acc));
+    }
+    part[(size_t)blockIdx.x * J * L + jl] = acc;
+}
+
+// max over (j, l) of ||R_j[:, l]|| / ||X[:, l]||, partials summed in chunk order
+__global__ void k_residual_max(const double* __restrict__ part, int nchunks, int JL, int L, const double* __restrict__ xnorm,
+                               double* __restrict__ out) {
+    __shared__ double sh[256];
+    double mx = 0.0;
+    for (int jl = threadIdx.x; jl < JL; jl += blockDim.x) {
+        double s = 0.0;
+        for (int c = 0; c < nchunks; ++c) s += part[(size_t)c * JL + jl];
+        const double xn = xnorm[jl % L];
+        mx = fmax(mx, xn > 0.0 ? sqrt(s) / xn : 0.0);
+    }
+    sh[threadIdx.x] = mx;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
+}
+
+// S[r][m L + l] = 2 Re sum_j w_j scaled_j^m Y[r][j][l], m < Mk
+__global__ void k_moments_from_Y(const double2* __restrict__ Y, const double2* __restrict__ quad, int64_t n, int J, int L,
+                                 int Mk, double* __restrict__ S, int64_t lds) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * L; e += stride) {
+        const int64_t r = e / L;
+        const int l = (int)(e % L);
+        double* srow = S + r * lds + l;
+        for (int m = 0; m < Mk; ++m) srow[(size_t)m * L] = 0.0;
+        for (int j = 0; j < J; ++j) {
+            const double2 y = Y[((size_t)r * J + j) * L + l];
+            double2 f = quad[3 * j + 1];
+            const double2 sc = quad[3 * j + 2];
+            for (int m = 0; m < Mk; ++m) {
+                srow[(size_t)m * L] += 2.0 * (f.x * y.x - f.y * y.y);
+                f = cmul(f, sc);
+            }
+        }
+    }
+}
+
 __global__ void k_zero_cols(double* S, int64_t n, int cols, int64_t lds) {
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * cols; e += stride)
@@ -454,12 +592,40 @@ static void lz_alloc(Lz& z, Arena& ws, int64_t m, int64_t n, int L, int J, int M
     z.partials = ws.take<double>((size_t)z.nblk * L);
 }
 
+struct RefineBufs {
+    double2* Y = nullptr;      // [n][J][L]
+    double2* HY = nullptr;     // [n][J][L] (H applied to Y as a real n x 2JL block)
+    double* U = nullptr;       // m x 2JL
+    double* R = nullptr;       // [J][n][2L]
+    double* part = nullptr;    // [nchunks][J L]
+    double* xnorm = nullptr;   // [L]
+    double* rmax = nullptr;    // [1]
+    int nchunks = 0;
+};
+
+static void refine_alloc(RefineBufs& b, Lz& zc, Arena& ws, int64_t m, int64_t n, int L, int J, int max_iter, int sm) {
+    b.Y = ws.take<double2>((size_t)n * J * L);
+    b.HY = ws.take<double2>((size_t)n * J * L);
+    b.U = ws.take<double>((size_t)m * 2 * J * L);
+    b.R = ws.take<double>((size_t)J * n * 2 * L);
+    b.nchunks = sm * 2;
+    b.part = ws.take<double>((size_t)b.nchunks * J * L);
+    b.xnorm = ws.take<double>(L);
+    b.rmax = ws.take<double>(4);
+    lz_alloc(zc, ws, m, n, 2 * L, 1, 0, max_iter, sm);   // correction solves: 2L real columns, one shift
+}
+
 size_t krylov_workspace(const cmsvd_matrix* A, const cmsvd_params* p) {
     Arena a;
     Lz z;
     lz_alloc(z, a, A->A.m, A->A.n, p->L, p->N / 2, p->M + 1, p->max_iter, A->ctx->sm_count);
     a.take<double>((size_t)A->A.n * p->L);   // ell > 1 restart blocks (ping-pong)
     a.take<double>((size_t)A->A.n * p->L);
+    if (p->refine > 0) {
+        RefineBufs b;
+        Lz zc;
+        refine_alloc(b, zc, a, A->A.m, A->A.n, p->L, p->N / 2, p->max_iter, A->ctx->sm_count);
+    }
     return a.off + 256;
 }
 
@@ -527,17 +693,21 @@ static int lanczos_run(cmsvd_matrix* M, Lz& z, const double* X, int64_t ldx, dou
     out->iters = iters;
     out->converged = (h[C_STATUS] & ST_NOTCONV) ? 0 : 1;
     out->breakdown = (h[C_STATUS] & ST_BREAKDOWN) ? 1 : 0;
-    if (S == nullptr) return CMSVD_OK;
+    if (S == nullptr && z.mode == 0) return CMSVD_OK;
 
     // ---- tridiagonal solves and moment coefficients
     CM_TRY(Kmax >= 0 ? CMSVD_OK : CMSVD_BREAKDOWN);
-    k_zero_cols<<<ctx->sm_count * 4, 256, 0, s>>>(S, z.n, z.L * z.Mk, lds);
-    CM_LAUNCH();
+    if (z.mode == 0) {
+        k_zero_cols<<<ctx->sm_count * 4, 256, 0, s>>>(S, z.n, z.L * z.Mk, lds);
+        CM_LAUNCH();
+    }
     if (Kmax == 0) return CMSVD_OK;
     k_tri_solve<<<(z.J * z.L + 127) / 128, 128, 0, s>>>(z);
     CM_LAUNCH();
-    k_tri_coef<<<(int)(((int64_t)Kmax * z.L + 255) / 256), 256, 0, s>>>(z, Kmax);
-    CM_LAUNCH();
+    if (z.mode == 0) {
+        k_tri_coef<<<(int)(((int64_t)Kmax * z.L + 255) / 256), 256, 0, s>>>(z, Kmax);
+        CM_LAUNCH();
+    }
 
     // ---- pass 2
     k_lz_scale0<<<grid, blk, 0, s>>>(z, X, ldx, z.Q[0]);
@@ -554,7 +724,8 @@ static int lanczos_run(cmsvd_matrix* M, Lz& z, const double* X, int64_t ldx, dou
         double* W = z.Q[(p + 1) % 3];
         spmm(M->A, z.L, Qk, z.L, z.U, z.L, s);
         spmm(M->At, z.L, z.U, z.L, W, z.L, s);
-        k_lz2_step<<<grid, blk, 0, s>>>(z, Qk, Qp, W, S, lds);
+        if (z.mode == 0) k_lz2_step<<<grid, blk, 0, s>>>(z, Qk, Qp, W, S, lds);
+        else k_lz2_step_acc<<<grid, blk, 0, s>>>(z, Qk, Qp, W);
     }
     ce = cudaStreamEndCapture(s, &g);
     pr.capture_depth--;
@@ -577,12 +748,82 @@ static int lanczos_run(cmsvd_matrix* M, Lz& z, const double* X, int64_t ldx, dou
     return CMSVD_OK;
 }
 
+// One filter application with FP64 iterative refinement: explicit Y_j from the shared
+// Lanczos process, then rounds of R_j = X - (s_j I - H) Y_j and corrections
+// (s_j I - H) E_j = R_j (one Lanczos run per shift on [Re R_j | Im R_j]) until
+// max ||R_j|| / ||X|| <= tol_solve or p->refine rounds; finally the Mk moments.
+static int refined_filter(cmsvd_matrix* M, const cmsvd_params* p, Lz& z, Lz& zc, RefineBufs& rb, const double* X,
+                          int64_t ldx, int Mk, double* S, int64_t lds, SolveOut* out) {
+    cmsvd_context* ctx = M->ctx;
+    cudaStream_t s = ctx->s;
+    const int J = z.J, L = z.L;
+    const int64_t n = z.n;
+    CM_CUDA(cudaMemsetAsync(rb.Y, 0, sizeof(double2) * n * J * L, s));
+    z.mode = 1;
+    z.Yacc = rb.Y;
+    z.Jtot = J;
+    z.Lorig = L;
+    CM_TRY(lanczos_run(M, z, X, ldx, nullptr, 0, p->check_every, out));
+    if (out->breakdown) { set_error("Lanczos breakdown (non-finite value)"); return CMSVD_BREAKDOWN; }
+    CM_CUDA(cudaMemcpyAsync(rb.xnorm, z.beta, sizeof(double) * L, cudaMemcpyDeviceToDevice, s));
+    int64_t iters = out->iters;
+    int rounds = 0;
+    double rmax = 0.0;
+    for (;;) {
+        // H Y in FP64 (Y as a real n x 2JL block)
+        CM_TRY(spmm(M->A, 2 * J * L, (const double*)rb.Y, 2 * J * L, rb.U, 2 * J * L, s));
+        CM_TRY(spmm(M->At, 2 * J * L, rb.U, 2 * J * L, (double*)rb.HY, 2 * J * L, s));
+        {
+            ProfScope ps(CMSVD_PROF_OTHER, s, 8.0 * n * (4.0 * J * L + L) + 16.0 * J * n * L, 10.0 * n * J * L, 2);
+            dim3 grid(rb.nchunks, (J * L + 127) / 128);
+            k_residual<<<grid, 128, 0, s>>>(rb.Y, rb.HY, X, ldx, z.quad, n, J, L, rb.R, rb.part);
+            CM_LAUNCH();
+            k_residual_max<<<1, 256, 0, s>>>(rb.part, rb.nchunks, J * L, L, rb.xnorm, rb.rmax);
+            CM_LAUNCH();
+        }
+        CM_CUDA(cudaMemcpyAsync(ctx->pinned, rb.rmax, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CM_CUDA(cudaStreamSynchronize(s));
+        memcpy(&rmax, ctx->pinned, sizeof(double));
+        if (!(rmax == rmax)) { set_error("refinement residual is not finite"); return CMSVD_BREAKDOWN; }
+        if (rmax <= p->tol_solve || rounds >= p->refine) break;
+        ++rounds;
+        for (int j = 0; j < J; ++j) {
+            zc.tol = p->tol_solve;
+            zc.quad = z.quad + 3 * j;
+            zc.mode = 2;
+            zc.Yacc = rb.Y;
+            zc.Jtot = J;
+            zc.Lorig = L;
+            zc.jsel = j;
+            SolveOut so;
+            CM_TRY(lanczos_run(M, zc, rb.R + (size_t)j * n * 2 * L, 2 * L, nullptr, 0, p->check_every, &so));
+            if (so.breakdown) { set_error("Lanczos breakdown in a correction solve"); return CMSVD_BREAKDOWN; }
+            iters += so.iters;
+            if (!so.converged) out->converged = 0;
+        }
+    }
+    out->iters = iters;
+    out->refine_rounds = rounds;
+    out->refine_residual = rmax;
+    if (rmax > p->tol_solve) out->converged = 0;
+    {
+        ProfScope ps(CMSVD_PROF_OTHER, s, 16.0 * n * J * L + 8.0 * n * L * Mk, 4.0 * n * J * L * Mk);
+        k_moments_from_Y<<<ctx->sm_count * 4, 256, 0, s>>>(rb.Y, z.quad, n, J, L, Mk, S, lds);
+        CM_LAUNCH();
+    }
+    z.mode = 0;
+    return CMSVD_OK;
+}
+
 int krylov_moments(cmsvd_matrix* M, const cmsvd_params* p, const double2* quad, int Mk, const double* X,
                    int64_t ldx, double* S, int64_t lds, Arena& ws, SolveOut* out) {
     cmsvd_context* ctx = M->ctx;
     Lz z;
     lz_alloc(z, ws, M->A.m, M->A.n, p->L, p->N / 2, p->M + 1, p->max_iter, ctx->sm_count);
     double* Xr[2] = {ws.take<double>((size_t)M->A.n * p->L), ws.take<double>((size_t)M->A.n * p->L)};
+    RefineBufs rb;
+    Lz zc;
+    if (p->refine > 0) refine_alloc(rb, zc, ws, M->A.m, M->A.n, p->L, p->N / 2, p->max_iter, ctx->sm_count);
     if (!ws.fits()) { set_error("workspace too small"); return CMSVD_WORKSPACE_TOO_SMALL; }
     z.tol = p->tol_solve;
     z.quad = quad;
@@ -592,12 +833,17 @@ int krylov_moments(cmsvd_matrix* M, const cmsvd_params* p, const double2* quad, 
     for (int nu = 1; nu < p->ell; ++nu) {
         z.Mk = 1;
         double* dst = Xr[nu & 1];
-        CM_TRY(lanczos_run(M, z, Xc, ldc, dst, p->L, p->check_every, out));
-        if (out->breakdown) { set_error("Lanczos breakdown (non-finite value)"); return CMSVD_BREAKDOWN; }
+        if (p->refine > 0) {
+            CM_TRY(refined_filter(M, p, z, zc, rb, Xc, ldc, 1, dst, p->L, out));
+        } else {
+            CM_TRY(lanczos_run(M, z, Xc, ldc, dst, p->L, p->check_every, out));
+            if (out->breakdown) { set_error("Lanczos breakdown (non-finite value)"); return CMSVD_BREAKDOWN; }
+        }
         Xc = dst;
         ldc = p->L;
     }
     z.Mk = Mk;
+    if (p->refine > 0) return refined_filter(M, p, z, zc, rb, Xc, ldc, Mk, S, lds, out);
     CM_TRY(lanczos_run(M, z, Xc, ldc, S, lds, p->check_every, out));
     if (out->breakdown) { set_error("Lanczos breakdown (non-finite value)"); return CMSVD_BREAKDOWN; }
     return CMSVD_OK;

@@ -78,6 +78,13 @@ __global__ void k_select(const double* __restrict__ Xb, const double* __restrict
     }
 }
 
+// ---- U (n x k, row-major) <- U diag(1 / phi)
+__global__ void k_scale_cols(double* __restrict__ U, int64_t n, int k, const double* __restrict__ phi) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * k; e += stride)
+        U[e] = U[e] / phi[e % k];
+}
+
 // ---- column norms of (Z - X diag(phi)) / scale, n x k row-major, deterministic two-stage
 __global__ void k_colnorm_part(const double* __restrict__ Z, const double* __restrict__ X, const double* __restrict__ phi,
                                int64_t n, int k, double* __restrict__ part) {
@@ -280,8 +287,15 @@ int rayleigh_ritz(cmsvd_matrix* M, const double* S, int64_t lds, int c, double a
     st->in_interval = h[1];
     int t = 0;
     if (k > 0) {
-        CM_TRY(gemm_nn(bf.Ut, rp, bf.Pc, k, bf.uh, k, m, rp, k, s));
+        // v = V~ q; u = U~ p equals A v / phi exactly (A V~ Q = U~ P Phi, Sec. 3.4.1), and one
+        // SpMM costs far less than the m x rp x k product
         CM_TRY(gemm_nn(bf.Vt, r, bf.Qc, k, bf.vh, k, n, r, k, s));
+        CM_TRY(spmm(M->A, k, bf.vh, k, bf.uh, k, s));
+        {
+            ProfScope ps_u(CMSVD_PROF_OTHER, s, 16.0 * m * k, (double)m * k);
+            k_scale_cols<<<ctx->sm_count * 4, 256, 0, s>>>(bf.uh, m, k, bf.phic);
+            CM_LAUNCH();
+        }
         CM_TRY(spmm(M->At, k, bf.uh, k, bf.Z, k, s));
         CM_TRY(colnorm_diff(bf.Z, bf.vh, bf.phic, n, k, normA, bf.part, bf.nchunks, bf.resu, s));
         CM_TRY(spmm(M->A, k, bf.vh, k, bf.Z, k, s));
