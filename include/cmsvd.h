@@ -196,6 +196,26 @@ int cmsvd_gram_workspace_size(cmsvd_context* ctx, int64_t n, int32_t c1, int32_t
 int cmsvd_gram(cmsvd_context* ctx, int64_t n, int32_t c1, int32_t c2, const double* X, int64_t ldx,
                const double* Y, int64_t ldy, double* G, void* workspace, size_t ws_bytes);
 
+/*
+ * cmsvd_gram without a workspace argument, for callers that cannot allocate
+ * device memory when they call: code whose device memory is all owned by
+ * another allocator, real-time loops where a cudaMalloc would synchronize the
+ * device, and host programs that hand a library only the buffers of the call.
+ * The paper has no counterpart; this is a property of the library interface.
+ *
+ * Same arguments and result as cmsvd_gram (within rounding: the chunking may
+ * differ). The chunk partials live in one fixed 8 MiB array of device memory
+ * inside the library (1,048,576 doubles), held by every GPU that loads the
+ * library until the process exits. Limit: c1 * c2 <= 1,048,576; larger
+ * requests return CMSVD_INVALID_ARG. The call allocates nothing.
+ * The first call on a device looks up the array's device address (one-time
+ * set-up); make that first call before any stream capture on that device.
+ * Every call shares the array: calls that overlap on the GPU (other streams,
+ * other contexts, other threads) race and must be serialized by the caller.
+ */
+int cmsvd_gram_noalloc(cmsvd_context* ctx, int64_t n, int32_t c1, int32_t c2, const double* X, int64_t ldx,
+                       const double* Y, int64_t ldy, double* G);
+
 /* Device workspace (bytes) that cmsvd_moments / cmsvd_solve_interval need for A and *p. */
 int cmsvd_workspace_size(const cmsvd_matrix* A, const cmsvd_params* p, size_t* bytes);
 

@@ -71,6 +71,7 @@ _SIGS = {
     "cmsvd_workspace_size": (C.c_int, [_P, C.POINTER(cmsvd_params), C.POINTER(C.c_size_t)]),
     "cmsvd_gram_workspace_size": (C.c_int, [_P, _I64, C.c_int32, C.c_int32, C.POINTER(C.c_size_t)]),
     "cmsvd_gram": (C.c_int, [_P, _I64, C.c_int32, C.c_int32, _P, _I64, _P, _I64, _P, _P, C.c_size_t]),
+    "cmsvd_gram_noalloc": (C.c_int, [_P, _I64, C.c_int32, C.c_int32, _P, _I64, _P, _I64, _P]),
     "cmsvd_moments": (C.c_int, [_P, C.c_double, C.c_double, C.POINTER(cmsvd_params), _P, _P, _P, C.c_size_t,
                                 C.POINTER(cmsvd_stats)]),
     "cmsvd_solve_interval": (C.c_int, [_P, C.c_double, C.c_double, C.POINTER(cmsvd_params), _P, _P, C.c_size_t,
@@ -202,6 +203,14 @@ def cmsvd_gram(ctx: int, X, Y, G, workspace) -> None:
     c2 = Y.shape[1]
     _check(lib().cmsvd_gram(_P(ctx), n, c1, c2, _ptr_any(X), X.stride(0), _ptr_any(Y), Y.stride(0), _ptr(G),
                             _ptr(workspace), workspace.numel() * workspace.element_size()), "cmsvd_gram")
+
+
+def cmsvd_gram_noalloc(ctx: int, X, Y, G) -> None:
+    """G = X^T Y like cmsvd_gram, using the library's fixed device scratch (no workspace)."""
+    n, c1 = X.shape
+    c2 = Y.shape[1]
+    _check(lib().cmsvd_gram_noalloc(_P(ctx), n, c1, c2, _ptr_any(X), X.stride(0), _ptr_any(Y), Y.stride(0), _ptr(G)),
+           "cmsvd_gram_noalloc")
 
 
 def _ptr_any(t) -> int:

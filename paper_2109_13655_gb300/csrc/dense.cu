@@ -7,6 +7,7 @@
 //     in step 5), which keeps the high relative accuracy of small singular values.
 // FP64 on this part runs on the FP64 pipe (no FP64 tensor-core path is used).
 #include "internal.cuh"
+#include <mutex>
 
 namespace cmsvd {
 
@@ -683,3 +684,72 @@ int orth_qr(const double* X, int64_t ldx, int64_t n, int c, double* Q, double* R
 }
 
 }  // namespace cmsvd
+
+// ============================================================================= allocation-free Gram
+// Scratch for the chunk partials of cmsvd_gram_noalloc: a fixed device array in
+// this file (8 MiB, present on every GPU that loads the library, until exit).
+namespace cmsvd {
+namespace {
+constexpr int64_t kNoAllocDoubles = int64_t(1) << 20;
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[256] = {};   // per device: device address of the array
+}  // namespace
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+// The host-side name of a __device__ array is not a device address. Resolve the
+// address once per device, with that device current.
+static int noalloc_scratch(int device, double** out) {
+    if (device < 0 || device >= 256) { set_error("device ordinal %d out of range", device); return CMSVD_INVALID_ARG; }
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)", __FILE__, __LINE__);
+        g_noalloc_ptr[device] = (double*)p;
+    }
+    *out = g_noalloc_ptr[device];
+    return CMSVD_OK;
+}
+
+}  // namespace cmsvd
+
+extern "C" int cmsvd_gram_noalloc(cmsvd_context* ctx, int64_t n, int32_t c1, int32_t c2, const double* X, int64_t ldx,
+                                  const double* Y, int64_t ldy, double* G) {
+    using namespace cmsvd;
+    if (!ctx || !X || !Y || !G) { set_error("NULL argument"); return CMSVD_INVALID_ARG; }
+    if (n < 1 || c1 < 1 || c2 < 1 || ldx < c1 || ldy < c2) {
+        set_error("need n >= 1, c1 >= 1, c2 >= 1, ldx >= c1, ldy >= c2");
+        return CMSVD_INVALID_ARG;
+    }
+    if ((int64_t)c1 * c2 > kNoAllocDoubles) {
+        set_error("c1*c2 = %lld exceeds the %lld-entry static scratch of cmsvd_gram_noalloc; use cmsvd_gram",
+                  (long long)c1 * c2, (long long)kNoAllocDoubles);
+        return CMSVD_INVALID_ARG;
+    }
+    CM_CUDA(cudaSetDevice(ctx->device));
+    double* scratch = nullptr;
+    CM_TRY(noalloc_scratch(ctx->device, &scratch));
+    // order after the caller's stream, as every other entry point does
+    CM_CUDA(cudaEventRecord(ctx->ev_in, ctx->user));
+    CM_CUDA(cudaStreamWaitEvent(ctx->s, ctx->ev_in, 0));
+    const int sym = (X == Y && c1 == c2 && ldx == ldy) ? 1 : 0;
+    int nc;
+    int64_t rpc;
+    gram_plan(c1, c2, n, ctx->sm_count, &nc, &rpc, sym);
+    const int64_t maxc = kNoAllocDoubles / ((int64_t)c1 * c2);   // chunks that fit the array
+    if (nc > maxc) {
+        rpc = (n + maxc - 1) / maxc;
+        rpc = (rpc + GK - 1) / GK * GK;
+        nc = (int)((n + rpc - 1) / rpc);
+    }
+    dim3 grid((c1 + GT - 1) / GT, (c2 + GT - 1) / GT, nc);
+    const int64_t cnt = (int64_t)c1 * c2;
+    // every partial that k_sum_partials reads is written first: nothing needs clearing
+    k_gram_partial<<<grid, 256, 0, ctx->s>>>(X, ldx, c1, Y, ldy, c2, n, rpc, sym, scratch);
+    CM_LAUNCH();
+    k_sum_partials<<<(int)((cnt + 255) / 256), 256, 0, ctx->s>>>(scratch, nc, c1, c2, sym, G);
+    CM_LAUNCH();
+    CM_CUDA(cudaEventRecord(ctx->ev_out, ctx->s));
+    CM_CUDA(cudaStreamWaitEvent(ctx->user, ctx->ev_out, 0));
+    return CMSVD_OK;
+}
