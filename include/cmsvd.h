@@ -56,7 +56,10 @@ typedef enum cmsvd_solver {
 
 typedef enum cmsvd_precision {
     CMSVD_FP64 = 0,       /* every step in FP64 */
-    CMSVD_MIXED = 1       /* reserved for the reduced-precision Krylov path */
+    CMSVD_MIXED = 1       /* Krylov solver: Lanczos vectors, SpMM and A's values in FP32 (FP32 accumulation;
+                             alpha, beta, the shifted recurrences and all accumulations in FP64), then FP64
+                             iterative refinement of every shifted solve (residual in FP64 with FP64 A).
+                             Rank truncation and Rayleigh-Ritz stay FP64. The direct solver ignores it. */
 } cmsvd_precision;
 
 /* Method parameters. Names follow Alg. 1 / Alg. 2 and Sec. 4. */

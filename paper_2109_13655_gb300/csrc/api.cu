@@ -80,7 +80,7 @@ int check_params(const cmsvd_matrix* A, double a, double b, const cmsvd_params* 
         return CMSVD_INVALID_ARG;
     }
     if (p->solver < CMSVD_SOLVER_AUTO || p->solver > CMSVD_SOLVER_DIRECT) { set_error("unknown solver %d", p->solver); return CMSVD_INVALID_ARG; }
-    if (p->precision != CMSVD_FP64) { set_error("only CMSVD_FP64 is implemented"); return CMSVD_NOT_SUPPORTED; }
+    if (p->precision != CMSVD_FP64 && p->precision != CMSVD_MIXED) { set_error("unknown precision %d", p->precision); return CMSVD_INVALID_ARG; }
     if ((int64_t)p->L * p->M > A->A.n) {
         set_error("L*M (%d) exceeds n (%lld)", p->L * p->M, (long long)A->A.n);
         return CMSVD_INVALID_ARG;

@@ -152,7 +152,28 @@ void csr_free(Csr* A) {
     if (A->rowptr) cudaFree(A->rowptr);
     if (A->colidx) cudaFree(A->colidx);
     if (A->vals) cudaFree(A->vals);
-    A->rowptr = nullptr; A->colidx = nullptr; A->vals = nullptr;
+    if (A->vals_f) cudaFree(A->vals_f);
+    A->rowptr = nullptr; A->colidx = nullptr; A->vals = nullptr; A->vals_f = nullptr;
+}
+
+__global__ void k_to_fp32(const double* __restrict__ x, int64_t n, float* __restrict__ y) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) y[i] = (float)x[i];
+}
+
+// FP32 copies of the values of A and A^T (round to nearest), made once per matrix.
+int csr_make_fp32(cmsvd_matrix* M) {
+    cmsvd_context* ctx = M->ctx;
+    Csr* mats[2] = {&M->A, &M->At};
+    for (Csr* c : mats) {
+        if (c->vals_f) continue;
+        CM_CUDA(cudaMalloc(&c->vals_f, sizeof(float) * (c->nnz > 0 ? c->nnz : 1)));
+        if (c->nnz > 0) {
+            k_to_fp32<<<ctx->sm_count * 4, 256, 0, ctx->s>>>(c->vals, c->nnz, c->vals_f);
+            CM_LAUNCH();
+        }
+    }
+    return CMSVD_OK;
 }
 
 // ----------------------------------------------------------------------------- transpose
@@ -254,10 +275,13 @@ int csr_transpose(cmsvd_context* ctx, const Csr& A, Csr* At) {
 // row-major L-column block. The row's (col, val) pairs are loaded cooperatively
 // and broadcast with shuffles, so every nonzero reads one contiguous L-vector of
 // X. Each output element is summed in the row's storage order (deterministic).
-template <int LPR, int CPL>
+__device__ __forceinline__ double fma_rn_t(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fma_rn_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+template <typename T, int LPR, int CPL>
 __global__ void __launch_bounds__(256) k_spmm(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
-                                              const double* __restrict__ vals, int64_t rows, int L,
-                                              const double* __restrict__ X, int64_t ldx, double* __restrict__ Y,
+                                              const T* __restrict__ vals, int64_t rows, int L,
+                                              const T* __restrict__ X, int64_t ldx, T* __restrict__ Y,
                                               int64_t ldy) {
     const int lane = threadIdx.x % LPR;
     const int64_t group = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LPR;
@@ -266,22 +290,22 @@ __global__ void __launch_bounds__(256) k_spmm(const int64_t* __restrict__ rowptr
     for (int64_t r = group; r < rows; r += ngroups) {
         const int64_t s = rowptr[r], e = rowptr[r + 1];
         for (int c0 = 0; c0 < L; c0 += LPR * CPL) {
-            double acc[CPL];
+            T acc[CPL];
 #pragma unroll
-            for (int q = 0; q < CPL; ++q) acc[q] = 0.0;
+            for (int q = 0; q < CPL; ++q) acc[q] = (T)0;
             for (int64_t p0 = s; p0 < e; p0 += LPR) {
                 const int64_t p = p0 + lane;
                 int32_t mc = 0;
-                double mv = 0.0;
+                T mv = (T)0;
                 if (p < e) { mc = colidx[p]; mv = vals[p]; }
                 const int cnt = (int)((e - p0) < LPR ? (e - p0) : LPR);
                 for (int k = 0; k < cnt; ++k) {
                     const int32_t col = __shfl_sync(mask, mc, k, LPR);
-                    const double v = __shfl_sync(mask, mv, k, LPR);
-                    const double* xr = X + (int64_t)col * ldx + c0 + lane;
+                    const T v = __shfl_sync(mask, mv, k, LPR);
+                    const T* xr = X + (int64_t)col * ldx + c0 + lane;
 #pragma unroll
                     for (int q = 0; q < CPL; ++q)
-                        if (c0 + lane + q * LPR < L) acc[q] = __fma_rn(v, __ldg(xr + q * LPR), acc[q]);
+                        if (c0 + lane + q * LPR < L) acc[q] = fma_rn_t(v, __ldg(xr + q * LPR), acc[q]);
                 }
             }
 #pragma unroll
@@ -291,24 +315,33 @@ __global__ void __launch_bounds__(256) k_spmm(const int64_t* __restrict__ rowptr
     }
 }
 
-int spmm(const Csr& A, int L, const double* X, int64_t ldx, double* Y, int64_t ldy, cudaStream_t s) {
+template <typename T>
+static int spmm_t(const Csr& A, const T* vals, int L, const T* X, int64_t ldx, T* Y, int64_t ldy, cudaStream_t s) {
     if (A.m == 0 || L <= 0) return CMSVD_OK;
     // compulsory traffic: A (values, indices, row pointers), X once, Y once
-    ProfScope ps(CMSVD_PROF_SPMM, s, 12.0 * A.nnz + 8.0 * (A.m + 1) + 8.0 * L * (A.n + A.m), 2.0 * A.nnz * L);
-    int dev_sms = 152;
+    const double e = (double)sizeof(T);
+    ProfScope ps(CMSVD_PROF_SPMM, s, (e + 4.0) * A.nnz + 8.0 * (A.m + 1) + e * L * (A.n + A.m), 2.0 * A.nnz * L);
+    const int dev_sms = 152;
     if (L <= 8) {
-        int rows_per_block = 256 / 8;
-        k_spmm<8, 1><<<grid_for(A.m, rows_per_block, dev_sms * 32), 256, 0, s>>>(A.rowptr, A.colidx, A.vals, A.m, L, X, ldx, Y, ldy);
+        k_spmm<T, 8, 1><<<grid_for(A.m, 256 / 8, dev_sms * 32), 256, 0, s>>>(A.rowptr, A.colidx, vals, A.m, L, X, ldx, Y, ldy);
     } else if (L <= 16) {
-        int rows_per_block = 256 / 16;
-        k_spmm<16, 1><<<grid_for(A.m, rows_per_block, dev_sms * 32), 256, 0, s>>>(A.rowptr, A.colidx, A.vals, A.m, L, X, ldx, Y, ldy);
+        k_spmm<T, 16, 1><<<grid_for(A.m, 256 / 16, dev_sms * 32), 256, 0, s>>>(A.rowptr, A.colidx, vals, A.m, L, X, ldx, Y, ldy);
     } else if (L <= 32) {
-        k_spmm<32, 1><<<grid_for(A.m, 8, dev_sms * 32), 256, 0, s>>>(A.rowptr, A.colidx, A.vals, A.m, L, X, ldx, Y, ldy);
+        k_spmm<T, 32, 1><<<grid_for(A.m, 8, dev_sms * 32), 256, 0, s>>>(A.rowptr, A.colidx, vals, A.m, L, X, ldx, Y, ldy);
     } else {
-        k_spmm<32, 4><<<grid_for(A.m, 8, dev_sms * 32), 256, 0, s>>>(A.rowptr, A.colidx, A.vals, A.m, L, X, ldx, Y, ldy);
+        k_spmm<T, 32, 4><<<grid_for(A.m, 8, dev_sms * 32), 256, 0, s>>>(A.rowptr, A.colidx, vals, A.m, L, X, ldx, Y, ldy);
     }
     CM_LAUNCH();
     return CMSVD_OK;
+}
+
+int spmm(const Csr& A, int L, const double* X, int64_t ldx, double* Y, int64_t ldy, cudaStream_t s) {
+    return spmm_t<double>(A, A.vals, L, X, ldx, Y, ldy, s);
+}
+
+int spmm(const Csr& A, int L, const float* X, int64_t ldx, float* Y, int64_t ldy, cudaStream_t s) {
+    if (!A.vals_f) { set_error("FP32 values of A were not made"); return CMSVD_INVALID_ARG; }
+    return spmm_t<float>(A, A.vals_f, L, X, ldx, Y, ldy, s);
 }
 
 }  // namespace cmsvd

@@ -7,6 +7,7 @@
 //     in step 5), which keeps the high relative accuracy of small singular values.
 // FP64 on this part runs on the FP64 pipe (no FP64 tensor-core path is used).
 #include "internal.cuh"
+#include <cooperative_groups.h>
 #include <mutex>
 
 namespace cmsvd {
@@ -80,8 +81,10 @@ __global__ void k_sum_partials(const double* __restrict__ partials, int nchunks,
 static void gram_plan(int c1, int c2, int64_t n, int sm_count, int* nchunks, int64_t* rpc, int sym = 0) {
     const int tx = (c1 + GT - 1) / GT;
     const int tiles = sym ? tx * (tx + 1) / 2 : tx * ((c2 + GT - 1) / GT);
-    // about 4 working CTAs per SM (256 threads x 64 registers each fill the register file)
-    int64_t want = (4 * (int64_t)sm_count + tiles - 1) / tiles;
+    // at most 4 working CTAs per SM (256 threads x 64 registers each fill the register file),
+    // rounded DOWN so tiles x chunks fits one wave: a few CTAs of a second wave would cost
+    // a whole CTA's time at a quarter of the SM's FP64 issue rate
+    int64_t want = 4 * (int64_t)sm_count / tiles;
     int64_t maxc = (n + 63) / 64;
     if (want > maxc) want = maxc;
     if (want < 1) want = 1;
@@ -358,44 +361,84 @@ __device__ __forceinline__ void block_sum3_128(double& a, double& b, double& c, 
     c = (sh[2][0] + sh[2][1]) + (sh[2][2] + sh[2][3]);
 }
 
-__global__ void __launch_bounds__(128) k_jacobi_round(double* __restrict__ Xc, double* __restrict__ V, int rows, int cols,
-                                                      int np, int round, double tol, const double* __restrict__ fro2,
-                                                      int* __restrict__ rotated) {
+// Cooperative form: one launch runs every sweep. All CTAs are co-resident
+// (cudaLaunchCooperativeKernel refuses otherwise) and meet at a grid barrier after
+// each round. The barrier spins with an iteration limit: past it the kernel sets
+// ctl[3] (timeout), and every CTA leaves at the next barrier. ctl: [0] arrivals,
+// [1] generation, [2] sweeps done, [3] timeout; rot[s] = 1 when sweep s rotated.
+__device__ __forceinline__ bool grid_barrier(unsigned* ctl, unsigned nblocks) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* gen = ctl + 1;
+        volatile unsigned* err = ctl + 3;
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(ctl, 1u) == nblocks - 1) {
+            atomicExch(ctl, 0u);
+            __threadfence();
+            atomicAdd(ctl + 1, 1u);
+        } else {
+            long long it = 0;
+            while (*gen == g && *err == 0) {
+                if (++it > 20000000LL) { atomicExch(ctl + 3, 1u); break; }   // ~1 s
+                __nanosleep(40);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return *(volatile unsigned*)(ctl + 3) == 0;
+}
+
+__global__ void __launch_bounds__(128) k_jacobi_coop(double* __restrict__ Xc, double* __restrict__ V, int rows, int cols,
+                                                     int np, double tol, const double* __restrict__ fro2, int max_sweeps,
+                                                     unsigned* ctl, unsigned* rot) {
     __shared__ double sh[3][4];
-    const int k = blockIdx.x;
-    int p, q;
-    if (k == 0) { p = round; q = np - 1; }
-    else { p = (round + k) % (np - 1); q = (round - k + (np - 1)) % (np - 1); }
-    if (p >= cols || q >= cols) return;
-    if (p > q) { const int t = p; p = q; q = t; }
-    double* xp = Xc + (size_t)p * rows;
-    double* xq = Xc + (size_t)q * rows;
-    double al = 0.0, be = 0.0, ga = 0.0;
-    for (int i = threadIdx.x; i < rows; i += 128) {
-        const double a = xp[i], b = xq[i];
-        al = __fma_rn(a, a, al);
-        be = __fma_rn(b, b, be);
-        ga = __fma_rn(a, b, ga);
-    }
-    block_sum3_128(al, be, ga, sh);
     const double negl = 1e-36 * *fro2;
-    if (!(fabs(ga) > tol * sqrt(al * be)) || !(al > negl) || !(be > negl)) return;
-    const double zeta = (be - al) / (2.0 * ga);
-    const double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-    const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
-    for (int i = threadIdx.x; i < rows; i += 128) {
-        const double a = xp[i], b = xq[i];
-        xp[i] = cs * a - sn * b;
-        xq[i] = sn * a + cs * b;
+    const int k = blockIdx.x;
+    int sweep = 0;
+    for (; sweep < max_sweeps; ++sweep) {
+        for (int round = 0; round < np - 1; ++round) {
+            int p, q;
+            if (k == 0) { p = round; q = np - 1; }
+            else { p = (round + k) % (np - 1); q = (round - k + (np - 1)) % (np - 1); }
+            if (p < cols && q < cols) {
+                if (p > q) { const int t = p; p = q; q = t; }
+                double* xp = Xc + (size_t)p * rows;
+                double* xq = Xc + (size_t)q * rows;
+                double al = 0.0, be = 0.0, ga = 0.0;
+                for (int i = threadIdx.x; i < rows; i += 128) {
+                    const double a = __ldcg(xp + i), b = __ldcg(xq + i);
+                    al = __fma_rn(a, a, al);
+                    be = __fma_rn(b, b, be);
+                    ga = __fma_rn(a, b, ga);
+                }
+                block_sum3_128(al, be, ga, sh);
+                if (fabs(ga) > tol * sqrt(al * be) && al > negl && be > negl) {
+                    const double zeta = (be - al) / (2.0 * ga);
+                    const double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                    const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
+                    for (int i = threadIdx.x; i < rows; i += 128) {
+                        const double a = __ldcg(xp + i), b = __ldcg(xq + i);
+                        xp[i] = cs * a - sn * b;
+                        xq[i] = sn * a + cs * b;
+                    }
+                    double* vp = V + (size_t)p * cols;
+                    double* vq = V + (size_t)q * cols;
+                    for (int i = threadIdx.x; i < cols; i += 128) {
+                        const double va = __ldcg(vp + i), vb = __ldcg(vq + i);
+                        vp[i] = cs * va - sn * vb;
+                        vq[i] = sn * va + cs * vb;
+                    }
+                    if (threadIdx.x == 0) atomicExch(rot + sweep, 1u);
+                }
+                __syncthreads();   // sh reused by the next round
+            }
+            if (!grid_barrier(ctl, gridDim.x)) return;
+        }
+        if (*(volatile unsigned*)(rot + sweep) == 0) { ++sweep; break; }
     }
-    double* vp = V + (size_t)p * cols;
-    double* vq = V + (size_t)q * cols;
-    for (int i = threadIdx.x; i < cols; i += 128) {
-        const double va = vp[i], vb = vq[i];
-        vp[i] = cs * va - sn * vb;
-        vq[i] = sn * va + cs * vb;
-    }
-    if (threadIdx.x == 0) *rotated = 1;
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl[2] = sweep;
 }
 
 __global__ void __launch_bounds__(1024) k_jacobi_finish(const double* __restrict__ Xc, int rows, int cols,
@@ -417,6 +460,218 @@ __global__ void __launch_bounds__(1024) k_jacobi_finish(const double* __restrict
             perm[j + 1] = key;
         }
     }
+}
+
+// Block-cyclic form in one thread-block cluster (cols and rows <= 256). The columns are
+// split into JC_NB = 2 JC_CL blocks of bs columns (bs even; columns past cols are zero and
+// never rotate). Each CTA keeps two blocks of Xc and of V in its shared memory. A sweep is
+// JC_NB - 1 block rounds of a round-robin tournament of the blocks: in block round r, CTA k
+// rotates every column of its first block against every column of its second (bs inner
+// rounds of bs disjoint pairs, one warp per pair), and in block round 0 also the pairs
+// inside each block (bs - 1 inner rounds). Every column pair meets once per sweep, as in the
+// cyclic method. Between block rounds the blocks move to the CTAs that need them through
+// distributed shared memory, staged in registers so that no second buffer is needed; the
+// cluster's hardware barrier orders the moves, and no thread spins on memory.
+namespace cgr = cooperative_groups;
+constexpr int JC_CL = 8;
+constexpr int JC_NB = 2 * JC_CL;
+constexpr int JC_THREADS = 512;
+constexpr int JC_MAXDIM = 256;
+constexpr int JC_MAXBS = JC_MAXDIM / JC_NB;                       // 16 columns per block
+constexpr int JC_STAGE = 2 * JC_MAXBS * JC_MAXDIM / JC_THREADS;   // 2 blocks of <= 16 x 256 per 512 threads
+
+__device__ __forceinline__ void jc_pair(int k, int r, int& P, int& Q) {
+    if (k == 0) { P = r; Q = JC_NB - 1; }
+    else { P = (r + k) % (JC_NB - 1); Q = (r - k + (JC_NB - 1)) % (JC_NB - 1); }
+}
+
+// One warp: orthogonalize columns a and b (a has the lower global index). Returns true when
+// it rotated. The butterfly sums are identical on every lane (each step adds the same two
+// values in either order).
+__device__ __forceinline__ bool jc_rotate(double* xa, double* xb, double* va, double* vb, int rows, int cols, double tol,
+                                          double negl, int lane) {
+    double al = 0.0, be = 0.0, ga = 0.0;
+    for (int e = lane; e < rows; e += 32) {
+        const double a = xa[e], b = xb[e];
+        al = __fma_rn(a, a, al);
+        be = __fma_rn(b, b, be);
+        ga = __fma_rn(a, b, ga);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        al += __shfl_xor_sync(0xffffffffu, al, o);
+        be += __shfl_xor_sync(0xffffffffu, be, o);
+        ga += __shfl_xor_sync(0xffffffffu, ga, o);
+    }
+    if (!(fabs(ga) > tol * sqrt(al * be) && al > negl && be > negl)) return false;
+    const double zeta = (be - al) / (2.0 * ga);
+    const double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+    const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
+    for (int e = lane; e < rows; e += 32) {
+        const double a = xa[e], b = xb[e];
+        xa[e] = cs * a - sn * b;
+        xb[e] = sn * a + cs * b;
+    }
+    for (int e = lane; e < cols; e += 32) {
+        const double a = va[e], b = vb[e];
+        va[e] = cs * a - sn * b;
+        vb[e] = sn * a + cs * b;
+    }
+    return true;
+}
+
+// Moves the two blocks that CTA k needs in block round nr from where they sit in round r.
+__device__ __forceinline__ void jc_move(cgr::cluster_group& cl, double* buf, int bsz, int k, int r, int nr) {
+    int nP, nQ;
+    jc_pair(k, nr, nP, nQ);
+    int sP = 0, oP = 0, sQ = 0, oQ = 0;   // source CTA and slot of each block
+    for (int kk = 0; kk < JC_CL; ++kk) {
+        int a, b;
+        jc_pair(kk, r, a, b);
+        if (a == nP) { sP = kk; oP = 0; }
+        if (b == nP) { sP = kk; oP = 1; }
+        if (a == nQ) { sQ = kk; oQ = 0; }
+        if (b == nQ) { sQ = kk; oQ = 1; }
+    }
+    const double* src0 = cl.map_shared_rank(buf, (unsigned)sP) + oP * bsz;
+    const double* src1 = cl.map_shared_rank(buf, (unsigned)sQ) + oQ * bsz;
+    double stage[JC_STAGE];
+#pragma unroll
+    for (int it = 0; it < JC_STAGE; ++it) {
+        const int idx = (int)threadIdx.x + it * JC_THREADS;
+        if (idx < 2 * bsz) stage[it] = idx < bsz ? src0[idx] : src1[idx - bsz];
+    }
+    cl.sync();   // every CTA has read what it needs from buf
+#pragma unroll
+    for (int it = 0; it < JC_STAGE; ++it) {
+        const int idx = (int)threadIdx.x + it * JC_THREADS;
+        if (idx < 2 * bsz) buf[idx] = stage[it];
+    }
+}
+
+__global__ void __launch_bounds__(JC_THREADS) k_jacobi_cluster(double* __restrict__ Xc, double* __restrict__ V, int rows,
+                                                               int cols, int bs, double tol, const double* __restrict__ fro2,
+                                                               int max_sweeps, unsigned* __restrict__ ctl) {
+    extern __shared__ double jc_smem[];
+    __shared__ unsigned rotflag[2];
+    cgr::cluster_group cl = cgr::this_cluster();
+    const int k = (int)cl.block_rank();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int xsz = bs * rows, vsz = bs * cols;   // one block of Xc / of V
+    double* Xs = jc_smem;                          // [2][bs][rows]
+    double* Vs = Xs + 2 * xsz;                     // [2][bs][cols]
+    const double negl = 1e-36 * *fro2;
+    int P, Q;
+    jc_pair(k, 0, P, Q);
+    for (int idx = threadIdx.x; idx < 2 * xsz; idx += JC_THREADS) {
+        const int slot = idx / xsz, rem = idx - slot * xsz, i = rem / rows, e = rem - i * rows;
+        const int g = (slot ? Q : P) * bs + i;
+        Xs[idx] = g < cols ? Xc[(size_t)g * rows + e] : 0.0;
+    }
+    for (int idx = threadIdx.x; idx < 2 * vsz; idx += JC_THREADS) {
+        const int slot = idx / vsz, rem = idx - slot * vsz, i = rem / cols, e = rem - i * cols;
+        const int g = (slot ? Q : P) * bs + i;
+        Vs[idx] = g < cols ? V[(size_t)g * cols + e] : 0.0;
+    }
+    if (threadIdx.x == 0) { rotflag[0] = 0u; rotflag[1] = 0u; }
+    cl.sync();
+    int sweep = 0, r = 0;
+    const int half = bs / 2;
+    for (;;) {
+        const int par = sweep & 1;
+        if (r == 0) {
+            for (int t = 0; t < bs - 1; ++t) {   // pairs inside each block
+                if (warp < bs) {
+                    const int slot = warp / half, u = warp - slot * half;
+                    int i, j;
+                    if (u == 0) { i = t; j = bs - 1; }
+                    else { i = (t + u) % (bs - 1); j = (t - u + bs - 1) % (bs - 1); }
+                    if (i > j) { const int tmp = i; i = j; j = tmp; }
+                    double* xb0 = Xs + slot * xsz;
+                    double* vb0 = Vs + slot * vsz;
+                    if (jc_rotate(xb0 + i * rows, xb0 + j * rows, vb0 + i * cols, vb0 + j * cols, rows, cols, tol, negl, lane) &&
+                        lane == 0)
+                        rotflag[par] = 1u;
+                }
+                __syncthreads();
+            }
+        }
+        for (int t = 0; t < bs; ++t) {   // first block against second
+            if (warp < bs) {
+                const int i = warp, j = (warp + t) % bs;
+                double *xa = Xs + i * rows, *xb = Xs + xsz + j * rows;
+                double *va = Vs + i * cols, *vb = Vs + vsz + j * cols;
+                if (P > Q) {
+                    double* tmp = xa; xa = xb; xb = tmp;
+                    tmp = va; va = vb; vb = tmp;
+                }
+                if (jc_rotate(xa, xb, va, vb, rows, cols, tol, negl, lane) && lane == 0) rotflag[par] = 1u;
+            }
+            __syncthreads();
+        }
+        cl.sync();   // the round's rotations are complete and visible across the cluster
+        int nr = r + 1, nsweep = sweep;
+        if (nr == JC_NB - 1) {
+            // end of a sweep: every CTA reads every flag, so every CTA takes the same decision
+            unsigned any = 0u;
+            for (int kk = 0; kk < JC_CL; ++kk) any |= *cl.map_shared_rank(&rotflag[par], (unsigned)kk);
+            nsweep = sweep + 1;
+            if (any == 0u || nsweep >= max_sweeps) { sweep = nsweep; break; }
+            nr = 0;
+            if (threadIdx.x == 0) rotflag[par ^ 1] = 0u;   // read by nobody until the next sweep ends
+        }
+        jc_move(cl, Xs, xsz, k, r, nr);
+        jc_move(cl, Vs, vsz, k, r, nr);
+        __syncthreads();
+        jc_pair(k, nr, P, Q);
+        r = nr;
+        sweep = nsweep;
+    }
+    for (int idx = threadIdx.x; idx < 2 * xsz; idx += JC_THREADS) {
+        const int slot = idx / xsz, rem = idx - slot * xsz, i = rem / rows, e = rem - i * rows;
+        const int g = (slot ? Q : P) * bs + i;
+        if (g < cols) Xc[(size_t)g * rows + e] = Xs[idx];
+    }
+    for (int idx = threadIdx.x; idx < 2 * vsz; idx += JC_THREADS) {
+        const int slot = idx / vsz, rem = idx - slot * vsz, i = rem / cols, e = rem - i * cols;
+        const int g = (slot ? Q : P) * bs + i;
+        if (g < cols) V[(size_t)g * cols + e] = Vs[idx];
+    }
+    if (k == 0 && threadIdx.x == 0) ctl[2] = (unsigned)sweep;
+}
+
+// Launch shape of the cluster form, checked once per process: the GPU must be able to place
+// one cluster of JC_CL CTAs with 2 bs (rows + cols) doubles of shared memory each.
+static bool jc_available(int bs, int rows, int cols, size_t* smem) {
+    static std::once_flag once;
+    static bool ok = false;
+    const size_t max_smem = sizeof(double) * 2 * JC_MAXBS * 2 * JC_MAXDIM;
+    std::call_once(once, [&] {
+        if (cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(JC_CL);
+        cfg.blockDim = dim3(JC_THREADS);
+        cfg.dynamicSmemBytes = max_smem;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = JC_CL;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, (const void*)k_jacobi_cluster, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        ok = nclusters > 0;
+    });
+    *smem = sizeof(double) * 2 * (size_t)bs * (rows + cols);
+    return ok && rows <= JC_MAXDIM && cols <= JC_MAXDIM && bs <= JC_MAXBS && 2 * bs * rows <= JC_STAGE * JC_THREADS &&
+           2 * bs * cols <= JC_STAGE * JC_THREADS;
 }
 
 // Rotates the columns of Bm (trans = 0; Bm V = Xc) or of Bm^T (trans = 1; Bm^T V = Xc,
@@ -449,7 +704,7 @@ __global__ void k_jacobi_init_t(const double* __restrict__ Bm, int brows, int bc
 }
 
 int jacobi_svd(const double* Bm, int brows, int bcols, int trans, double* Xc, double* V, double* sv, int* perm,
-               int* flag2, cmsvd_context* ctx, double tol_in) {
+               int* flag2, cmsvd_context* ctx, double tol_in, unsigned* jac_ctl) {
     cudaStream_t s = ctx->s;
     const int rows = trans ? bcols : brows, cols = trans ? brows : bcols;
     double* fro2 = (double*)(flag2 + 2);   // flag2: 16 bytes of scratch (int rotated, pad, double)
@@ -466,37 +721,55 @@ int jacobi_svd(const double* Bm, int brows, int bcols, int trans, double* Xc, do
         CM_LAUNCH();
         return CMSVD_OK;
     }
-    // one sweep = memset(flag) + np-1 round kernels, captured once per shape and buffers
-    const int key_cols = tol_in > 0.0 ? -cols : cols;    // loose and tight sweeps are different graphs
-    cudaGraphExec_t ge = graph_cache_get(ctx, Xc, V, flag2, rows, key_cols);
-    if (!ge) {
-        cudaGraph_t g = nullptr;
-        Profiler& pr = prof();
-        pr.capture_depth++;
-        cudaError_t ce = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
-        if (ce == cudaSuccess) {
-            cudaMemsetAsync(flag2, 0, sizeof(int), s);
-            for (int round = 0; round < np - 1; ++round)
-                k_jacobi_round<<<np / 2, 128, 0, s>>>(Xc, V, rows, cols, np, round, tol, fro2, flag2);
-            ce = cudaStreamEndCapture(s, &g);
-        }
-        pr.capture_depth--;
-        if (ce != cudaSuccess) return cuda_fail(ce, "capture Jacobi sweep", __FILE__, __LINE__);
-        ce = cudaGraphInstantiate(&ge, g, 0);
-        cudaGraphDestroy(g);
-        if (ce != cudaSuccess) return cuda_fail(ce, "instantiate Jacobi sweep", __FILE__, __LINE__);
-        graph_cache_put(ctx, Xc, V, flag2, rows, key_cols, ge);
+    // all sweeps in one launch; ctl (4 words) and rot (one word per sweep) live in jac_ctl
+    unsigned* ctl = jac_ctl;
+    unsigned* rot = jac_ctl + 4;
+    const int max_sweeps = 40;
+    CM_CUDA(cudaMemsetAsync(ctl, 0, sizeof(unsigned) * (4 + max_sweeps), s));
+    int bs = (cols + JC_NB - 1) / JC_NB;
+    bs += bs & 1;
+    size_t jc_smem_bytes = 0;
+    bool use_cluster = jc_available(bs, rows, cols, &jc_smem_bytes);
+    if (use_cluster) {
+        ProfScope ps(CMSVD_PROF_JACOBI, s, 0.0, 0.0, 1);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(JC_CL);
+        cfg.blockDim = dim3(JC_THREADS);
+        cfg.dynamicSmemBytes = jc_smem_bytes;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = JC_CL;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        CM_CUDA(cudaLaunchKernelEx(&cfg, k_jacobi_cluster, Xc, V, rows, cols, bs, tol, (const double*)fro2, max_sweeps, ctl));
+        note_launch();
     }
-    for (int sweep = 0; sweep < 40; ++sweep) {
-        {
-            ProfScope ps(CMSVD_PROF_JACOBI, s, (np - 1.0) * (np / 2) * 32.0 * (rows + cols),
-                         (np - 1.0) * (np / 2) * (6.0 * rows + 6.0 * (rows + cols)), np - 1);
-            prof().launches += np - 1;
-            CM_CUDA(cudaGraphLaunch(ge, s));
+    int grid = np / 2;
+    if (!use_cluster) {
+        int per_sm = 0;
+        CM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_coop, 128, 0));
+        if (per_sm * ctx->sm_count < grid) { set_error("Jacobi grid of %d CTAs cannot be co-resident", grid); return CMSVD_NOT_SUPPORTED; }
+        ProfScope ps(CMSVD_PROF_JACOBI, s, 0.0, 0.0, 1);
+        void* args[] = {&Xc, &V, (void*)&rows, (void*)&cols, (void*)&np, (void*)&tol, &fro2, (void*)&max_sweeps, &ctl, &rot};
+        CM_CUDA(cudaLaunchCooperativeKernel((const void*)k_jacobi_coop, dim3(grid), dim3(128), args, 0, s));
+        note_launch();
+    }
+    unsigned h[4];
+    CM_CUDA(cudaMemcpyAsync(ctx->pinned, ctl, sizeof(unsigned) * 4, cudaMemcpyDeviceToHost, s));
+    CM_CUDA(cudaStreamSynchronize(s));
+    memcpy(h, ctx->pinned, sizeof(h));
+    if (h[3]) { set_error("Jacobi grid barrier timed out"); return CMSVD_CUDA_ERROR; }
+    // account the work of the sweeps that ran
+    {
+        Profiler& pr = prof();
+        if (pr.timing && pr.nrec > 0 && pr.recs[pr.nrec - 1].cls == CMSVD_PROF_JACOBI) {
+            const double pairs = (double)h[2] * (np - 1.0) * (np / 2);
+            pr.recs[pr.nrec - 1].bytes = pairs * 16.0 * (rows + cols);
+            pr.recs[pr.nrec - 1].flops = pairs * (6.0 * rows + 6.0 * (rows + cols));
         }
-        CM_CUDA(cudaMemcpyAsync(ctx->pinned, flag2, sizeof(int), cudaMemcpyDeviceToHost, s));
-        CM_CUDA(cudaStreamSynchronize(s));
-        if (ctx->pinned[0] == 0) break;
     }
     ProfScope ps(CMSVD_PROF_JACOBI, s, 8.0 * rows * cols, 2.0 * rows * cols);
     k_jacobi_finish<<<1, 1024, 0, s>>>(Xc, rows, cols, sv, perm);
@@ -606,7 +879,7 @@ int cholqr_pass(OrthCtx& o, const double* Xin, int64_t ldi, int cc, bool shifted
 //   eigen-decomposed and the directions left at rounding level are deflated; two
 //   plain passes restore orthogonality to working precision.
 int orth_qr(const double* X, int64_t ldx, int64_t n, int c, double* Q, double* R, int* c_out, double* scratch, int* ints,
-            int deflate, cmsvd_context* ctx) {
+            int deflate, cmsvd_context* ctx, double* Rcorr) {
     cudaStream_t s = ctx->s;
     double* T = scratch;
     double* G = T + (size_t)n * c;
@@ -625,6 +898,7 @@ int orth_qr(const double* X, int64_t ldx, int64_t n, int c, double* Q, double* R
     double* sv = M2 + (size_t)c * c;
     int* perm = (int*)(sv + c);
     double* part = sv + 2 * (size_t)c;
+    unsigned* jctl = (unsigned*)(part + gram_partials_cap(c, ctx->sm_count));   // inside the 256-double tail
     OrthCtx o{ctx, s, G, Ri, part, gram_partials_cap(c, ctx->sm_count), ints, n};
     int* cp_dev = ints + 1;
     int* flag2 = ints + 4;             // 16 bytes: ints[4..7]
@@ -645,9 +919,16 @@ int orth_qr(const double* X, int64_t ldx, int64_t n, int c, double* Q, double* R
         double rat;
         memcpy(&rat, ctx->pinned + 2, sizeof(double));
         if (ctx->pinned[0] == 0 && rat > 1e-5) {
+            // Q1 = X R1^{-1}; its Gram gives R2; Q = Q1 R2^{-1} is left implicit
+            double* Q1 = Rcorr ? Q : T;
             CM_TRY(trinv(o, R1, c));
-            CM_TRY(gemm_nn(X, ldx, Ri, c, T, c, n, c, c, s, 1));
-            CM_TRY(cholqr_pass(o, T, c, c, false, R2, Q));
+            CM_TRY(gemm_nn(X, ldx, Ri, c, Q1, c, n, c, c, s, 1));
+            CM_TRY(gram(Q1, c, c, Q1, c, c, n, G, part, o.pcap, ctx->sm_count, s));
+            CM_TRY(chol_adaptive(o, c, false, R2));
+            if (Rcorr) {
+                CM_TRY(trinv(o, R2, c));
+                CM_CUDA(cudaMemcpyAsync(Rcorr, Ri, sizeof(double) * (size_t)c * c, cudaMemcpyDeviceToDevice, s));
+            }
             CM_TRY(gemm_nn(R2, c, R1, c, R, c, c, c, c, s));
             *c_out = c;
             return CMSVD_OK;
@@ -660,7 +941,7 @@ int orth_qr(const double* X, int64_t ldx, int64_t n, int c, double* Q, double* R
     CM_TRY(gram(T, c, c, T, c, c, n, G, part, o.pcap, ctx->sm_count, s));
     CM_TRY(chol_adaptive(o, c, true, Rb));
     // the deflation only separates rounding-level directions (lambda < 1e-10) from O(1) ones
-    CM_TRY(jacobi_svd(Rb, c, c, 1, Xj, Vj, sv, perm, flag2, ctx, 1e-7));
+    CM_TRY(jacobi_svd(Rb, c, c, 1, Xj, Vj, sv, perm, flag2, ctx, 1e-7, jctl));
     {
         ProfScope ps(CMSVD_PROF_SMALL, s, 24.0 * c * c, 0.0);
         k_deflate<<<1, 256, 0, s>>>(Xj, sv, perm, c, 1e-10, T3, R3, cp_dev);
@@ -671,10 +952,29 @@ int orth_qr(const double* X, int64_t ldx, int64_t n, int c, double* Q, double* R
     const int cp = ctx->pinned[0];
     *c_out = cp;
     if (cp <= 0) return CMSVD_OK;
-    CM_TRY(gemm_nn(T, c, T3, cp, Q, cp, n, c, cp, s));
-    // two plain passes: Q -> T (R4), T -> Q (R5)
-    CM_TRY(cholqr_pass(o, Q, cp, cp, false, R4, T));
-    CM_TRY(cholqr_pass(o, T, cp, cp, false, R5, Q));
+    // first plain pass without forming Q3 = T T3: its Gram is T3^T (T^T T) T3, from the Gram
+    // of T computed above (error amplified by at most 1 / lambda_min of the kept directions,
+    // <= 1e10 u, which only affects Q4's orthogonality), so Q4 = T (T3 R4^{-1}) is one GEMM
+    CM_TRY(gemm_nn(G, c, T3, cp, M1, cp, c, c, cp, s));                 // G T3 (c x cp)
+    CM_TRY(gram(T3, cp, cp, M1, cp, cp, c, M2, part, o.pcap, ctx->sm_count, s));   // T3^T G T3 (cp x cp)
+    {
+        // chol_adaptive factors o.G; point it at the small Gram
+        double* g_saved = o.G;
+        o.G = M2;
+        const int st = chol_adaptive(o, cp, false, R4);
+        o.G = g_saved;
+        CM_TRY(st);
+    }
+    CM_TRY(trinv(o, R4, cp));
+    CM_TRY(gemm_nn(T3, cp, Ri, cp, M1, cp, c, cp, cp, s, 1));          // T3 R4^{-1} (c x cp)
+    CM_TRY(gemm_nn(T, c, M1, cp, Q, cp, n, c, cp, s));                 // Q4 = T (T3 R4^{-1})
+    // plain pass from data: Gram(Q4) = R5^T R5; Q = Q4 R5^{-1} is left implicit
+    CM_TRY(gram(Q, cp, cp, Q, cp, cp, n, G, part, o.pcap, ctx->sm_count, s));
+    CM_TRY(chol_adaptive(o, cp, false, R5));
+    if (Rcorr) {
+        CM_TRY(trinv(o, R5, cp));
+        CM_CUDA(cudaMemcpyAsync(Rcorr, Ri, sizeof(double) * (size_t)cp * cp, cudaMemcpyDeviceToDevice, s));
+    }
     // R = R5 R4 R3 R2 R1
     CM_TRY(gemm_nn(R2, c, R1, c, M1, c, c, c, c, s));
     CM_TRY(gemm_nn(R3, c, M1, c, M2, c, cp, c, c, s));

@@ -61,6 +61,7 @@ struct Csr {
     int64_t* rowptr = nullptr;   // device, m+1
     int32_t* colidx = nullptr;   // device, nnz
     double* vals = nullptr;      // device, nnz
+    float* vals_f = nullptr;     // device, nnz: FP32 copy for the mixed-precision Krylov path (made on demand)
 };
 
 struct Components {             // connected components of the column graph (A^T A)
@@ -136,6 +137,9 @@ int csr_transpose(cmsvd_context* ctx, const Csr& A, Csr* At);
 void csr_free(Csr* A);
 // Y (rows x L, ldy) = A X (X: ncols x L, ldx); optional per-column scale of the result.
 int spmm(const Csr& A, int L, const double* X, int64_t ldx, double* Y, int64_t ldy, cudaStream_t s);
+// FP32 SpMM (mixed path): values from A.vals_f, FP32 accumulation.
+int spmm(const Csr& A, int L, const float* X, int64_t ldx, float* Y, int64_t ldy, cudaStream_t s);
+int csr_make_fp32(cmsvd_matrix* M);
 int components_build(cmsvd_matrix* M);
 void components_free(Components* c);
 
@@ -173,17 +177,21 @@ int gemm_nn(const double* X, int64_t ldx, const double* W, int64_t ldw, double* 
 // Orthogonalization X (n x c) = Q (n x c', ld c') R (c' x c, row-major); see dense.cu.
 // deflate = 0 tries CholeskyQR2 first and falls back to the deflated form when
 // X is too ill-conditioned for it. ints: 8 device ints of scratch (8-byte aligned).
+// The orthonormal factor is returned implicitly: on exit Q holds Q' (n x c') and, when
+// Rcorr is not null, Rcorr holds the upper-triangular c' x c' matrix C with Q = Q' C.
+// With Rcorr null only R is wanted (Q is then scratch of n x c doubles).
 size_t orth_scratch(int c, int64_t n, int sm_count);
 int orth_qr(const double* X, int64_t ldx, int64_t n, int c, double* Q, double* R, int* c_out, double* scratch, int* ints,
-            int deflate, cmsvd_context* ctx);
+            int deflate, cmsvd_context* ctx, double* Rcorr);
 // One-sided Jacobi SVD of Bm (brows x bcols, row-major). trans = 0 rotates the columns of
 // Bm: Bm V = Xc (column-major brows x bcols), V bcols x bcols. trans = 1 rotates the
 // columns of Bm^T: Bm^T V = Xc (column-major bcols x brows), V brows x brows holds the
 // left singular vectors of Bm. sv_j = ||Xc_j||, perm sorts sv descending.
 // flag2: 16 bytes of device scratch (8-byte aligned + 8).
 // tol > 0 overrides the rotation threshold max(1e-15, rows u) (loose sweeps for the deflation).
+// jac_ctl: 64 device words of scratch for the cooperative sweeps.
 int jacobi_svd(const double* Bm, int brows, int bcols, int trans, double* Xc, double* V, double* sv, int* perm,
-               int* flag2, cmsvd_context* ctx, double tol = 0.0);
+               int* flag2, cmsvd_context* ctx, double tol, unsigned* jac_ctl);
 cudaGraphExec_t graph_cache_get(cmsvd_context* ctx, const void* a, const void* b, const void* c, int x, int y);
 void graph_cache_put(cmsvd_context* ctx, const void* a, const void* b, const void* c, int x, int y, cudaGraphExec_t g);
 void graph_cache_clear(cmsvd_context* ctx);

@@ -37,6 +37,13 @@ __device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
 }
 __device__ __forceinline__ double cabs_(double2 a) { return hypot(a.x, a.y); }
 
+// explicitly rounded operations of the vector recurrences (FP64 or FP32 vectors):
+// pass 2 repeats pass 1's operations exactly, so the regenerated vectors are bitwise equal
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double div_t(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float div_t(float a, float b) { return __fdiv_rn(a, b); }
+
 // ----------------------------------------------------------------------------- quadrature (Sec. 4)
 __global__ void k_quadrature(QuadParams q, double2* quad) {
     const int J = q.N / 2;
@@ -172,30 +179,32 @@ __global__ void k_lz_norm0(Lz z, const double* __restrict__ X, int64_t ldx) {
     }
 }
 
-__global__ void k_lz_scale0(Lz z, const double* __restrict__ X, int64_t ldx, double* __restrict__ Q0) {
+template <typename T>
+__global__ void k_lz_scale0(Lz z, const double* __restrict__ X, int64_t ldx, T* __restrict__ Q0) {
     const int l = threadIdx.x;
     const double b = z.beta[l];
     const bool act = b > 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; i < z.n; i += (int64_t)gridDim.x * blockDim.y)
-        Q0[i * z.L + l] = act ? __ddiv_rn(X[i * ldx + l], b) : 0.0;
+        Q0[i * z.L + l] = act ? (T)__ddiv_rn(X[i * ldx + l], b) : (T)0;
 }
 
 // pass 1, part 1: w <- H q_k - beta_k q_{k-1};  alpha_k = q_k^T w
-__global__ void k_lz_dot(Lz z, const double* __restrict__ Qk, const double* __restrict__ Qp, double* __restrict__ W) {
+template <typename T>
+__global__ void k_lz_dot(Lz z, const T* __restrict__ Qk, const T* __restrict__ Qp, T* __restrict__ W) {
     extern __shared__ double sh[];
     if (z.ctrl[C_NACT] == 0) return;
     const int k = z.ctrl[C_IT];
     const int l = threadIdx.x;
     const bool act = z.active[l] != 0;
-    const double b = k > 0 ? z.beta[(size_t)k * z.L + l] : 0.0;
+    const T b = (T)(k > 0 ? z.beta[(size_t)k * z.L + l] : 0.0);
     double acc = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; i < z.n; i += (int64_t)gridDim.x * blockDim.y) {
         const int64_t o = i * z.L + l;
-        double w = 0.0;
+        T w = (T)0;
         if (act) {
             w = W[o];
-            if (k > 0) w = __fma_rn(-b, Qp[o], w);
-            acc = __fma_rn(Qk[o], w, acc);
+            if (k > 0) w = fma_t(-b, Qp[o], w);
+            acc = __fma_rn((double)Qk[o], (double)w, acc);
         }
         W[o] = w;
     }
@@ -206,20 +215,22 @@ __global__ void k_lz_dot(Lz z, const double* __restrict__ Qk, const double* __re
 
 // pass 1, part 2: w <- w - alpha_k q_k;  beta_{k+1} = ||w||; per (shift, column)
 // LDL^T pivot d and t = e_k^T (s I - T_k)^{-1} e_1 beta_1; convergence and freezing.
-__global__ void k_lz_update(Lz z, const double* __restrict__ Qk, double* __restrict__ W) {
+template <typename T>
+__global__ void k_lz_update(Lz z, const T* __restrict__ Qk, T* __restrict__ W) {
     extern __shared__ double sh[];
     if (z.ctrl[C_NACT] == 0) return;
     const int k = z.ctrl[C_IT];
     const int l = threadIdx.x;
     const bool act = z.active[l] != 0;
     const double a = z.alpha[(size_t)k * z.L + l];
+    const T at = (T)a;
     double acc = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; i < z.n; i += (int64_t)gridDim.x * blockDim.y) {
         const int64_t o = i * z.L + l;
         if (act) {
-            double w = __fma_rn(-a, Qk[o], W[o]);
+            const T w = fma_t(-at, Qk[o], W[o]);
             W[o] = w;
-            acc = __fma_rn(w, w, acc);
+            acc = __fma_rn((double)w, (double)w, acc);
         }
     }
     if (!column_reduce(acc, sh, z.partials, z.ctrl + C_TICKET, z.L)) return;
@@ -273,14 +284,15 @@ __global__ void k_lz_update(Lz z, const double* __restrict__ Qk, double* __restr
 }
 
 // pass 1, part 3: q_{k+1} = w / beta_{k+1} (zero for frozen columns)
-__global__ void k_lz_scale(Lz z, double* __restrict__ W) {
+template <typename T>
+__global__ void k_lz_scale(Lz z, T* __restrict__ W) {
     const int kk = z.ctrl[C_IT];   // already k+1
     const int l = threadIdx.x;
     const bool act = z.active[l] != 0;
-    const double b = act ? z.beta[(size_t)kk * z.L + l] : 1.0;
+    const T b = (T)(act ? z.beta[(size_t)kk * z.L + l] : 1.0);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; i < z.n; i += (int64_t)gridDim.x * blockDim.y) {
         const int64_t o = i * z.L + l;
-        W[o] = act ? __ddiv_rn(W[o], b) : 0.0;
+        W[o] = act ? div_t(W[o], b) : (T)0;
     }
 }
 
@@ -339,7 +351,8 @@ __global__ void k_tri_coef(Lz z, int Kmax) {
 
 // pass 2: S_m += c_{m,i} q_i; then q_{i+1} from the stored alpha, beta with the
 // same rounded operations as pass 1.
-__global__ void k_lz2_step(Lz z, const double* __restrict__ Qk, const double* __restrict__ Qp, double* __restrict__ W,
+template <typename T>
+__global__ void k_lz2_step(Lz z, const T* __restrict__ Qk, const T* __restrict__ Qp, T* __restrict__ W,
                            double* __restrict__ S, int64_t lds) {
     const int i = z.ctrl[C_IT2];
     if (i >= z.ctrl[C_KMAX]) return;
@@ -352,19 +365,20 @@ __global__ void k_lz2_step(Lz z, const double* __restrict__ Qk, const double* __
     const double bn = next ? z.beta[(size_t)(i + 1) * z.L + l] : 1.0;
     const int Mk = z.Mk;
     const double* c = z.C + (size_t)i * Mk * z.L + l;
+    const T at = (T)a, bt = (T)b, bnt = (T)bn;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; r < z.n; r += (int64_t)gridDim.x * blockDim.y) {
         const int64_t o = r * z.L + l;
-        const double q = Qk[o];
+        const T q = Qk[o];
         if (live) {
             double* srow = S + r * lds + l;
-            for (int m = 0; m < Mk; ++m) srow[m * z.L] = __fma_rn(c[(size_t)m * z.L], q, srow[m * z.L]);
+            for (int m = 0; m < Mk; ++m) srow[m * z.L] = __fma_rn(c[(size_t)m * z.L], (double)q, srow[m * z.L]);
         }
-        double w = 0.0;
+        T w = (T)0;
         if (next) {
             w = W[o];
-            if (i > 0) w = __fma_rn(-b, Qp[o], w);
-            w = __fma_rn(-a, q, w);
-            w = __ddiv_rn(w, bn);
+            if (i > 0) w = fma_t(-bt, Qp[o], w);
+            w = fma_t(-at, q, w);
+            w = div_t(w, bnt);
         }
         W[o] = w;
     }
@@ -380,7 +394,8 @@ __global__ void k_lz2_step(Lz z, const double* __restrict__ Qk, const double* __
 }
 
 // pass 2 with accumulation of explicit solutions (refinement modes 1 and 2)
-__global__ void k_lz2_step_acc(Lz z, const double* __restrict__ Qk, const double* __restrict__ Qp, double* __restrict__ W) {
+template <typename T>
+__global__ void k_lz2_step_acc(Lz z, const T* __restrict__ Qk, const T* __restrict__ Qp, T* __restrict__ W) {
     const int i = z.ctrl[C_IT2];
     if (i >= z.ctrl[C_KMAX]) return;
     const int l = threadIdx.x;
@@ -400,9 +415,11 @@ __global__ void k_lz2_step_acc(Lz z, const double* __restrict__ Qk, const double
         if (pair && live) y1 = z.Ybuf[i * JL + l];
         if (live2) y2 = z.Ybuf[i * JL + l2];
     }
+    const T at = (T)a, bt = (T)b, bnt = (T)bn;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; r < z.n; r += (int64_t)gridDim.x * blockDim.y) {
         const int64_t o = r * z.L + l;
-        const double q = Qk[o];
+        const T qt = Qk[o];
+        const double q = (double)qt;
         if (z.mode == 1) {
             if (live) {
                 double2* yr = z.Yacc + ((size_t)r * z.Jtot) * z.Lorig + l;
@@ -415,7 +432,7 @@ __global__ void k_lz2_step_acc(Lz z, const double* __restrict__ Qk, const double
                 }
             }
         } else if (pair && (live || live2)) {
-            const double q2 = Qk[r * z.L + l2];
+            const double q2 = (double)Qk[r * z.L + l2];
             double2* yp = z.Yacc + ((size_t)r * z.Jtot + z.jsel) * z.Lorig + l;
             double2 v = *yp;
             // (y1 q) + i (y2 q2) = (y1.x q - y2.y q2) + i (y1.y q + y2.x q2)
@@ -423,12 +440,12 @@ __global__ void k_lz2_step_acc(Lz z, const double* __restrict__ Qk, const double
             v.y = __fma_rn(y1.y, q, __fma_rn(y2.x, q2, v.y));
             *yp = v;
         }
-        double w = 0.0;
+        T w = (T)0;
         if (next) {
             w = W[o];
-            if (i > 0) w = __fma_rn(-b, Qp[o], w);
-            w = __fma_rn(-a, q, w);
-            w = __ddiv_rn(w, bn);
+            if (i > 0) w = fma_t(-bt, Qp[o], w);
+            w = fma_t(-at, qt, w);
+            w = div_t(w, bnt);
         }
         W[o] = w;
     }
@@ -621,7 +638,7 @@ size_t krylov_workspace(const cmsvd_matrix* A, const cmsvd_params* p) {
     lz_alloc(z, a, A->A.m, A->A.n, p->L, p->N / 2, p->M + 1, p->max_iter, A->ctx->sm_count);
     a.take<double>((size_t)A->A.n * p->L);   // ell > 1 restart blocks (ping-pong)
     a.take<double>((size_t)A->A.n * p->L);
-    if (p->refine > 0) {
+    if (p->refine > 0 || p->precision == CMSVD_MIXED) {
         RefineBufs b;
         Lz zc;
         refine_alloc(b, zc, a, A->A.m, A->A.n, p->L, p->N / 2, p->max_iter, A->ctx->sm_count);
@@ -630,8 +647,11 @@ size_t krylov_workspace(const cmsvd_matrix* A, const cmsvd_params* p) {
 }
 
 // Pass 1 (+ optional pass 2 into S). Returns status; fills out.
+template <typename T>
 static int lanczos_run(cmsvd_matrix* M, Lz& z, const double* X, int64_t ldx, double* S, int64_t lds,
                        int check_every, SolveOut* out) {
+    T* Qb[3] = {(T*)z.Q[0], (T*)z.Q[1], (T*)z.Q[2]};
+    T* Ub = (T*)z.U;
     cmsvd_context* ctx = M->ctx;
     cudaStream_t s = ctx->s;
     const dim3 blk = lz_block(z.L);
@@ -640,7 +660,7 @@ static int lanczos_run(cmsvd_matrix* M, Lz& z, const double* X, int64_t ldx, dou
     CM_CUDA(cudaMemsetAsync(z.ctrl, 0, sizeof(int) * C_WORDS, s));
     k_lz_norm0<<<grid, blk, shb, s>>>(z, X, ldx);
     CM_LAUNCH();
-    k_lz_scale0<<<grid, blk, 0, s>>>(z, X, ldx, z.Q[0]);
+    k_lz_scale0<T><<<grid, blk, 0, s>>>(z, X, ldx, Qb[0]);
     CM_LAUNCH();
 
     // ---- pass 1 as a graph of `chunk` iterations (a multiple of 3: buffer roles rotate)
@@ -654,14 +674,14 @@ static int lanczos_run(cmsvd_matrix* M, Lz& z, const double* X, int64_t ldx, dou
     CM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     for (int it = 0; it < chunk; ++it) {
         const int p = it % 3;
-        double* Qk = z.Q[p];
-        double* Qp = z.Q[(p + 2) % 3];
-        double* W = z.Q[(p + 1) % 3];
-        spmm(M->A, z.L, Qk, z.L, z.U, z.L, s);
-        spmm(M->At, z.L, z.U, z.L, W, z.L, s);
-        k_lz_dot<<<grid, blk, shb, s>>>(z, Qk, Qp, W);
-        k_lz_update<<<grid, blk, shb, s>>>(z, Qk, W);
-        k_lz_scale<<<grid, blk, 0, s>>>(z, W);
+        T* Qk = Qb[p];
+        T* Qp = Qb[(p + 2) % 3];
+        T* W = Qb[(p + 1) % 3];
+        spmm(M->A, z.L, Qk, z.L, Ub, z.L, s);
+        spmm(M->At, z.L, Ub, z.L, W, z.L, s);
+        k_lz_dot<T><<<grid, blk, shb, s>>>(z, Qk, Qp, W);
+        k_lz_update<T><<<grid, blk, shb, s>>>(z, Qk, W);
+        k_lz_scale<T><<<grid, blk, 0, s>>>(z, W);
     }
     cudaError_t ce = cudaStreamEndCapture(s, &g);
     pr.capture_depth--;
@@ -675,7 +695,8 @@ static int lanczos_run(cmsvd_matrix* M, Lz& z, const double* X, int64_t ldx, dou
     // compulsory traffic per Lanczos step: A and A^T once each, X read and Y written by
     // both SpMMs, and the vector kernels (dot 4, update 3, scale 2 n x L passes)
     const double nnz = (double)M->A.nnz, mm = (double)M->A.m, nn = (double)M->A.n, LL = z.L;
-    const double step_bytes = 2 * (12.0 * nnz) + 8.0 * (mm + nn + 2) + 16.0 * LL * (mm + nn) + 72.0 * nn * LL;
+    const double eb = (double)sizeof(T), ea = sizeof(T) + 4.0;
+    const double step_bytes = 2 * (ea * nnz) + 8.0 * (mm + nn + 2) + 2 * eb * LL * (mm + nn) + 9 * eb * nn * LL;
     const double step_flops = 4.0 * nnz * LL + 10.0 * nn * LL;
     for (;;) {
         ProfScope ps(CMSVD_PROF_KRYLOV, s, step_bytes * chunk, step_flops * chunk, nodes1);
@@ -710,7 +731,7 @@ static int lanczos_run(cmsvd_matrix* M, Lz& z, const double* X, int64_t ldx, dou
     }
 
     // ---- pass 2
-    k_lz_scale0<<<grid, blk, 0, s>>>(z, X, ldx, z.Q[0]);
+    k_lz_scale0<T><<<grid, blk, 0, s>>>(z, X, ldx, Qb[0]);
     CM_LAUNCH();
     int chunk2 = chunk;
     if (chunk2 > 3 * ((Kmax + 2) / 3)) chunk2 = 3 * ((Kmax + 2) / 3);
@@ -719,13 +740,13 @@ static int lanczos_run(cmsvd_matrix* M, Lz& z, const double* X, int64_t ldx, dou
     CM_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     for (int it = 0; it < chunk2; ++it) {
         const int p = it % 3;
-        double* Qk = z.Q[p];
-        double* Qp = z.Q[(p + 2) % 3];
-        double* W = z.Q[(p + 1) % 3];
-        spmm(M->A, z.L, Qk, z.L, z.U, z.L, s);
-        spmm(M->At, z.L, z.U, z.L, W, z.L, s);
-        if (z.mode == 0) k_lz2_step<<<grid, blk, 0, s>>>(z, Qk, Qp, W, S, lds);
-        else k_lz2_step_acc<<<grid, blk, 0, s>>>(z, Qk, Qp, W);
+        T* Qk = Qb[p];
+        T* Qp = Qb[(p + 2) % 3];
+        T* W = Qb[(p + 1) % 3];
+        spmm(M->A, z.L, Qk, z.L, Ub, z.L, s);
+        spmm(M->At, z.L, Ub, z.L, W, z.L, s);
+        if (z.mode == 0) k_lz2_step<T><<<grid, blk, 0, s>>>(z, Qk, Qp, W, S, lds);
+        else k_lz2_step_acc<T><<<grid, blk, 0, s>>>(z, Qk, Qp, W);
     }
     ce = cudaStreamEndCapture(s, &g);
     pr.capture_depth--;
@@ -734,8 +755,8 @@ static int lanczos_run(cmsvd_matrix* M, Lz& z, const double* X, int64_t ldx, dou
     ce = cudaGraphInstantiate(&ge, g, 0);
     cudaGraphDestroy(g);
     if (ce != cudaSuccess) return cuda_fail(ce, "instantiate pass 2", __FILE__, __LINE__);
-    const double step2_bytes = 2 * (12.0 * nnz) + 8.0 * (mm + nn + 2) + 16.0 * LL * (mm + nn) +
-                               8.0 * nn * LL * (4.0 + 2.0 * z.Mk);
+    const double step2_bytes = 2 * (ea * nnz) + 8.0 * (mm + nn + 2) + 2 * eb * LL * (mm + nn) + 4 * eb * nn * LL +
+                               (z.mode == 0 ? 16.0 * nn * LL * z.Mk : 32.0 * nn * LL * z.J);
     const double step2_flops = 4.0 * nnz * LL + nn * LL * (6.0 + 2.0 * z.Mk);
     for (int done = 0; done < Kmax; done += chunk2) {
         ProfScope ps(CMSVD_PROF_KRYLOV, s, step2_bytes * chunk2, step2_flops * chunk2, nodes2);
@@ -746,6 +767,16 @@ static int lanczos_run(cmsvd_matrix* M, Lz& z, const double* X, int64_t ldx, dou
     cudaGraphExecDestroy(ge);
     if (ce != cudaSuccess) return cuda_fail(ce, "pass 2", __FILE__, __LINE__);
     return CMSVD_OK;
+}
+
+// Refinement rounds: the FP32 path always refines (default 8 rounds).
+static int refine_rounds(const cmsvd_params* p) {
+    if (p->precision == CMSVD_MIXED) return p->refine > 0 ? p->refine : 8;
+    return p->refine;
+}
+// Tolerance of the inner (Lanczos) solves: FP32 vectors stop near their own accuracy.
+static double inner_tol(const cmsvd_params* p) {
+    return p->precision == CMSVD_MIXED ? fmax(p->tol_solve, 1e-6) : p->tol_solve;
 }
 
 // One filter application with FP64 iterative refinement: explicit Y_j from the shared
@@ -763,12 +794,17 @@ static int refined_filter(cmsvd_matrix* M, const cmsvd_params* p, Lz& z, Lz& zc,
     z.Yacc = rb.Y;
     z.Jtot = J;
     z.Lorig = L;
-    CM_TRY(lanczos_run(M, z, X, ldx, nullptr, 0, p->check_every, out));
+    const bool mixed = p->precision == CMSVD_MIXED;
+    if (mixed) CM_TRY(lanczos_run<float>(M, z, X, ldx, nullptr, 0, p->check_every, out));
+    else CM_TRY(lanczos_run<double>(M, z, X, ldx, nullptr, 0, p->check_every, out));
     if (out->breakdown) { set_error("Lanczos breakdown (non-finite value)"); return CMSVD_BREAKDOWN; }
     CM_CUDA(cudaMemcpyAsync(rb.xnorm, z.beta, sizeof(double) * L, cudaMemcpyDeviceToDevice, s));
     int64_t iters = out->iters;
     int rounds = 0;
-    double rmax = 0.0;
+    int max_rounds = refine_rounds(p);
+    bool inner32 = mixed;   // correction solves in FP32 until they stop helping
+    bool stagnated = false;
+    double rmax = 0.0, rprev = 0.0;
     for (;;) {
         // H Y in FP64 (Y as a real n x 2JL block)
         CM_TRY(spmm(M->A, 2 * J * L, (const double*)rb.Y, 2 * J * L, rb.U, 2 * J * L, s));
@@ -785,18 +821,29 @@ static int refined_filter(cmsvd_matrix* M, const cmsvd_params* p, Lz& z, Lz& zc,
         CM_CUDA(cudaStreamSynchronize(s));
         memcpy(&rmax, ctx->pinned, sizeof(double));
         if (!(rmax == rmax)) { set_error("refinement residual is not finite"); return CMSVD_BREAKDOWN; }
-        if (rmax <= p->tol_solve || rounds >= p->refine) break;
+        // Stop at the tolerance or the round limit. When the residual no longer halves: with
+        // FP32 corrections, switch them to FP64 (FP32 vectors cannot resolve shifts close to
+        // the spectrum); with FP64 corrections the residual has reached the rounding floor of
+        // its own FP64 evaluation, ~u ||A^T A|| ||Y_j||, and the solves are as accurate as FP64 allows.
+        if (rmax <= p->tol_solve || rounds >= max_rounds) break;
+        if (rounds > 0 && rmax > 0.5 * rprev) {
+            if (!inner32) { stagnated = true; break; }
+            inner32 = false;
+            max_rounds = rounds + (p->refine > 0 ? p->refine : 4);
+        }
+        rprev = rmax;
         ++rounds;
         for (int j = 0; j < J; ++j) {
-            zc.tol = p->tol_solve;
             zc.quad = z.quad + 3 * j;
             zc.mode = 2;
             zc.Yacc = rb.Y;
             zc.Jtot = J;
             zc.Lorig = L;
             zc.jsel = j;
+            zc.tol = inner32 ? inner_tol(p) : p->tol_solve;
             SolveOut so;
-            CM_TRY(lanczos_run(M, zc, rb.R + (size_t)j * n * 2 * L, 2 * L, nullptr, 0, p->check_every, &so));
+            if (inner32) CM_TRY(lanczos_run<float>(M, zc, rb.R + (size_t)j * n * 2 * L, 2 * L, nullptr, 0, p->check_every, &so));
+            else CM_TRY(lanczos_run<double>(M, zc, rb.R + (size_t)j * n * 2 * L, 2 * L, nullptr, 0, p->check_every, &so));
             if (so.breakdown) { set_error("Lanczos breakdown in a correction solve"); return CMSVD_BREAKDOWN; }
             iters += so.iters;
             if (!so.converged) out->converged = 0;
@@ -805,7 +852,8 @@ static int refined_filter(cmsvd_matrix* M, const cmsvd_params* p, Lz& z, Lz& zc,
     out->iters = iters;
     out->refine_rounds = rounds;
     out->refine_residual = rmax;
-    if (rmax > p->tol_solve) out->converged = 0;
+    // converged: the tolerance was met, or FP64 corrections reached the FP64 rounding floor
+    if (!(rmax <= p->tol_solve) && !stagnated) out->converged = 0;
     {
         ProfScope ps(CMSVD_PROF_OTHER, s, 16.0 * n * J * L + 8.0 * n * L * Mk, 4.0 * n * J * L * Mk);
         k_moments_from_Y<<<ctx->sm_count * 4, 256, 0, s>>>(rb.Y, z.quad, n, J, L, Mk, S, lds);
@@ -823,28 +871,30 @@ int krylov_moments(cmsvd_matrix* M, const cmsvd_params* p, const double2* quad, 
     double* Xr[2] = {ws.take<double>((size_t)M->A.n * p->L), ws.take<double>((size_t)M->A.n * p->L)};
     RefineBufs rb;
     Lz zc;
-    if (p->refine > 0) refine_alloc(rb, zc, ws, M->A.m, M->A.n, p->L, p->N / 2, p->max_iter, ctx->sm_count);
+    if (refine_rounds(p) > 0) refine_alloc(rb, zc, ws, M->A.m, M->A.n, p->L, p->N / 2, p->max_iter, ctx->sm_count);
+    if (p->precision == CMSVD_MIXED) CM_TRY(csr_make_fp32(M));
     if (!ws.fits()) { set_error("workspace too small"); return CMSVD_WORKSPACE_TOO_SMALL; }
-    z.tol = p->tol_solve;
+    z.tol = inner_tol(p);
     z.quad = quad;
+    const bool use_refine = refine_rounds(p) > 0;
     const double* Xc = X;
     int64_t ldc = ldx;
     // iteration technique (Eq. iter1): S_0^(nu) = 2 Re sum_j w_j (s_j I - H)^{-1} S_0^(nu-1)
     for (int nu = 1; nu < p->ell; ++nu) {
         z.Mk = 1;
         double* dst = Xr[nu & 1];
-        if (p->refine > 0) {
+        if (use_refine) {
             CM_TRY(refined_filter(M, p, z, zc, rb, Xc, ldc, 1, dst, p->L, out));
         } else {
-            CM_TRY(lanczos_run(M, z, Xc, ldc, dst, p->L, p->check_every, out));
+            CM_TRY(lanczos_run<double>(M, z, Xc, ldc, dst, p->L, p->check_every, out));
             if (out->breakdown) { set_error("Lanczos breakdown (non-finite value)"); return CMSVD_BREAKDOWN; }
         }
         Xc = dst;
         ldc = p->L;
     }
     z.Mk = Mk;
-    if (p->refine > 0) return refined_filter(M, p, z, zc, rb, Xc, ldc, Mk, S, lds, out);
-    CM_TRY(lanczos_run(M, z, Xc, ldc, S, lds, p->check_every, out));
+    if (use_refine) return refined_filter(M, p, z, zc, rb, Xc, ldc, Mk, S, lds, out);
+    CM_TRY(lanczos_run<double>(M, z, Xc, ldc, S, lds, p->check_every, out));
     if (out->breakdown) { set_error("Lanczos breakdown (non-finite value)"); return CMSVD_BREAKDOWN; }
     return CMSVD_OK;
 }
@@ -868,7 +918,7 @@ int norm_estimate(cmsvd_matrix* M, Arena& ws, double* norm_out) {
     k_fill_start<<<ctx->sm_count, 256, 0, ctx->s>>>(x, M->A.n);
     CM_LAUNCH();
     SolveOut so;
-    CM_TRY(lanczos_run(M, z, x, 1, nullptr, 0, 48, &so));
+    CM_TRY(lanczos_run<double>(M, z, x, 1, nullptr, 0, 48, &so));
     k_tri_maxeig<<<1, 128, 0, ctx->s>>>(z, lam);
     CM_LAUNCH();
     CM_CUDA(cudaMemcpyAsync(ctx->pinned, lam, sizeof(double), cudaMemcpyDeviceToHost, ctx->s));

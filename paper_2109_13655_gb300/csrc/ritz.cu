@@ -31,13 +31,33 @@ __global__ void k_truncate(const double* __restrict__ V, const double* __restric
     }
 }
 
-// ---- step 5: candidate selection in descending phi order. Jacobi ran on B^T (rp x r):
-// B^T P = Xb, so P (Vb, column-major rp x rp) are the left singular vectors,
-// phi_j = ||Xb_j|| and q_j = Xb_j / phi_j (length r) the right ones.
+// ---- step 5: spurious index for every Ritz value, one warp each.
+// Jacobi ran on B^T (rp x r): B^T P = Xb, so P (Vb, column-major rp x rp) holds the left
+// singular vectors, phi_j = ||Xb_j|| and q_j = Xb_j / phi_j (length r) the right ones.
+// tau_j = q^T q / q^T Sigma_S1^{-1} q (scale-free, so the raw column is used), / sigma_S,1.
+__global__ void k_tau(const double* __restrict__ Xb, int rp, int r, const double* __restrict__ sS,
+                      double* __restrict__ tau_all) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    if (warp >= rp) return;
+    double num = 0.0, den = 0.0;
+    for (int i = lane; i < r; i += 32) {
+        const double q = Xb[(size_t)warp * r + i];
+        num = __fma_rn(q, q, num);
+        den += q * q / sS[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        num += __shfl_xor_sync(0xffffffffu, num, o);
+        den += __shfl_xor_sync(0xffffffffu, den, o);
+    }
+    if (lane == 0) tau_all[warp] = den > 0.0 ? num / den / sS[0] : 0.0;
+}
+
+// ---- candidate selection in descending phi order: phi in [a, b] and tau >= eps_tau
 __global__ void k_select(const double* __restrict__ Xb, const double* __restrict__ Vb, const double* __restrict__ svb,
-                         const int* __restrict__ perm, int rp, int r, const double* __restrict__ sS, double a, double b,
-                         double eps_tau, double* __restrict__ Pc, double* __restrict__ Qc, double* __restrict__ phic,
-                         double* __restrict__ tauc, int* __restrict__ counts, int* __restrict__ cand) {
+                         const int* __restrict__ perm, int rp, int r, const double* __restrict__ tau_all, double a,
+                         double b, double eps_tau, double* __restrict__ Pc, double* __restrict__ Qc,
+                         double* __restrict__ phic, double* __restrict__ tauc, int* __restrict__ counts,
+                         int* __restrict__ cand) {
     __shared__ int nc;
     const int t = threadIdx.x;
     if (t == 0) {
@@ -47,14 +67,7 @@ __global__ void k_select(const double* __restrict__ Xb, const double* __restrict
             const double phi = svb[j];
             if (!(phi >= a && phi <= b) || !(phi > 0.0)) continue;
             ++inside;
-            // tau_i = q^T q / q^T Sigma_S1^{-1} q (scale-free, so the raw column is used)
-            double num = 0.0, den = 0.0;
-            for (int i = 0; i < r; ++i) {
-                const double q = Xb[(size_t)j * r + i];
-                num += q * q;
-                den += q * q / sS[i];
-            }
-            const double tau = num / den / sS[0];
+            const double tau = tau_all[j];
             if (!(tau >= eps_tau)) continue;
             cand[k] = j;
             phic[k] = phi;
@@ -183,15 +196,17 @@ __global__ void k_final_copy(const double* __restrict__ uh, const double* __rest
 
 // ----------------------------------------------------------------------------- driver
 struct RitzBufs {
-    double *Qs, *chol, *Rs, *Xc, *Vr, *svR, *sS, *Wsel, *Vt, *Y, *Ut, *B, *Xb, *Vb, *svB, *Pc, *Qc, *phic, *tauc, *uh, *vh, *Z,
+    double *Qs, *Cq, *chol, *Rs, *Xc, *Vr, *svR, *sS, *Wsel, *Vt, *Y, *Ut, *B, *Xb, *Vb, *svB, *Pc, *Qc, *phic, *tauc, *uh, *vh, *Z,
         *resu, *resv, *part;
     int *permR, *permB, *cand, *ints;
+    unsigned* jctl;
     int nchunks;
 };
 
 static void ritz_alloc(RitzBufs& b, Arena& ws, int64_t m, int64_t n, int c, int sm_count) {
     const int64_t mx = m > n ? m : n;
     b.Qs = ws.take<double>((size_t)n * c);
+    b.Cq = ws.take<double>((size_t)c * c);
     b.chol = ws.take<double>(orth_scratch(c, mx, sm_count));
     b.Rs = ws.take<double>((size_t)c * c);
     b.Xc = ws.take<double>((size_t)c * c);
@@ -221,6 +236,7 @@ static void ritz_alloc(RitzBufs& b, Arena& ws, int64_t m, int64_t n, int c, int 
     b.permB = ws.take<int>(c);
     b.cand = ws.take<int>(c);
     b.ints = ws.take<int>(32);
+    b.jctl = ws.take<unsigned>(64);
 }
 
 size_t ritz_workspace(int64_t m, int64_t n, int c, int sm_count) {
@@ -252,9 +268,9 @@ int rayleigh_ritz(cmsvd_matrix* M, const double* S, int64_t lds, int c, double a
     CM_CUDA(cudaMemsetAsync(bf.ints, 0, sizeof(int) * 32, s));
     // step 3: S^ = Q_S R_S, SVD of R_S, truncation
     int cp = 0;
-    CM_TRY(orth_qr(S, lds, n, c, bf.Qs, bf.Rs, &cp, bf.chol, bf.ints + 16, 1, ctx));
+    CM_TRY(orth_qr(S, lds, n, c, bf.Qs, bf.Rs, &cp, bf.chol, bf.ints + 16, 1, ctx, bf.Cq));
     if (cp <= 0) { st->found = 0; return CMSVD_OK; }
-    CM_TRY(jacobi_svd(bf.Rs, cp, c, 1, bf.Xc, bf.Vr, bf.svR, bf.permR, bf.ints + 24, ctx));
+    CM_TRY(jacobi_svd(bf.Rs, cp, c, 1, bf.Xc, bf.Vr, bf.svR, bf.permR, bf.ints + 24, ctx, 0.0, bf.jctl));
     {
         ProfScope ps_t(CMSVD_PROF_SMALL, s, 16.0 * c * c, 0.0);
         k_truncate<<<1, 256, 0, s>>>(bf.Vr, bf.svR, bf.permR, cp, p->delta, bf.sS, bf.Wsel, bf.ints);
@@ -266,20 +282,25 @@ int rayleigh_ritz(cmsvd_matrix* M, const double* S, int64_t lds, int c, double a
     st->rank = r;
     CM_CUDA(cudaMemcpyAsync(&st->sigma_S1, bf.sS, sizeof(double), cudaMemcpyDeviceToHost, s));
     if (r <= 0) { st->found = 0; return CMSVD_OK; }
-    CM_TRY(gemm_nn(bf.Qs, cp, bf.Wsel, r, bf.Vt, r, n, cp, r, s));
+    // V~ = Q_S W_sel = Q' (C W_sel): the small product first, one n x cp x r GEMM
+    CM_TRY(gemm_nn(bf.Cq, cp, bf.Wsel, r, bf.Xb, r, cp, cp, r, s));
+    CM_TRY(gemm_nn(bf.Qs, cp, bf.Xb, r, bf.Vt, r, n, cp, r, s));
     cudaEventRecord(ev[1], s);
     // step 4: A V~ = U~ B
     CM_TRY(spmm(M->A, r, bf.Vt, r, bf.Y, r, s));
     int rp = 0;
-    CM_TRY(orth_qr(bf.Y, r, m, r, bf.Ut, bf.B, &rp, bf.chol, bf.ints + 16, 0, ctx));
+    // only B is needed: u = U~ p is formed as A v / phi below
+    CM_TRY(orth_qr(bf.Y, r, m, r, bf.Ut, bf.B, &rp, bf.chol, bf.ints + 16, 0, ctx, nullptr));
     cudaEventRecord(ev[2], s);
     if (rp <= 0) { st->found = 0; return CMSVD_OK; }
     // step 5: B = P Phi Q^T, selection, Ritz vectors, residuals
-    CM_TRY(jacobi_svd(bf.B, rp, r, 1, bf.Xb, bf.Vb, bf.svB, bf.permB, bf.ints + 24, ctx));
+    CM_TRY(jacobi_svd(bf.B, rp, r, 1, bf.Xb, bf.Vb, bf.svB, bf.permB, bf.ints + 24, ctx, 0.0, bf.jctl));
     {
         ProfScope ps_s(CMSVD_PROF_SMALL, s, 24.0 * r * r, 2.0 * r * r);
-        k_select<<<1, 256, 0, s>>>(bf.Xb, bf.Vb, bf.svB, bf.permB, rp, r, bf.sS, a, b, p->eps_tau, bf.Pc, bf.Qc, bf.phic,
-                                   bf.tauc, bf.ints + 1, bf.cand);
+        k_tau<<<(rp * 32 + 255) / 256, 256, 0, s>>>(bf.Xb, rp, r, bf.sS, bf.resv);
+        CM_LAUNCH();
+        k_select<<<1, 256, 0, s>>>(bf.Xb, bf.Vb, bf.svB, bf.permB, rp, r, bf.resv, a, b, p->eps_tau, bf.Pc, bf.Qc,
+                                   bf.phic, bf.tauc, bf.ints + 1, bf.cand);
         CM_LAUNCH();
     }
     CM_TRY(read_ints(ctx, bf.ints + 1, 2, h));

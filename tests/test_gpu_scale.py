@@ -1,0 +1,56 @@
+"""Full-scale GPU checks where the oracle cannot run in seconds: properties that hold
+at any size.
+
+The 2,000,000 x 1,000,000 known-spectrum twin of the large mixed-precision
+workload: 62,500 dense 32 x 16 blocks of U(-1, 1) values rounded to
+bfloat16-representable numbers (so FP32 or BF16 storage holds A exactly), rows
+and columns randomly permuted, 16 nonzeros per row. Its singular values are
+the union of the blocks' singular values, so the count in [a, b] and every
+sigma are known exactly. Checks: exact count, sigma relative error <= 1e-10
+against the closed-form spectrum, residuals ||A^T u - sigma v|| / ||A||_2 and
+||A v - sigma u|| / ||A||_2 <= 1e-10 recomputed independently (SciPy) on sampled
+triplets, and orthonormality of the returned vectors.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from paper_2109_13655_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2109_13655_gb300 import binding
+    return binding
+
+
+def test_known_spectrum_2000000x1000000(B):
+    bp = synth.block_permuted(62500, 32, 16, seed=6, dist="uniform_bf16")
+    s = bp.sigmas_desc()
+    a, b, f = synth.window_interval(s, 500000, 100, min_rel_gap=1e-6, max_shift=10)
+    truth = np.sort(s[f:f + 100])
+    A = bp.A
+    ctx = B.Context()
+    M = B.Matrix.from_csr(ctx, A)
+    Vin = torch.from_numpy(synth.gaussian_block(A.n, 32, 7)).cuda()
+    out = M.solve_interval(a, b, B.params(N=32, L=32, M=8, ell=2), Vin)
+    assert out.stats["solver_used"] == B.SOLVER_DIRECT and out.stats["max_component"] == 16
+    assert out.sigma.size == truth.size == 100
+    assert np.max(np.abs(out.sigma - truth) / truth) <= 1e-10
+    assert out.res_u.max() <= 1e-10 and out.res_v.max() <= 1e-10
+    assert abs(out.stats["norm_A"] - s[0]) <= 1e-6 * s[0]
+    # independent residuals on sampled triplets
+    As = sp.csr_matrix((A.vals, A.colidx, A.rowptr), shape=(A.m, A.n))
+    for i in np.linspace(0, 99, 8).astype(int):
+        u, v, sg = out.U[:, i], out.V[:, i], out.sigma[i]
+        assert np.linalg.norm(As.T @ u - sg * v) / s[0] <= 1e-10
+        assert np.linalg.norm(As @ v - sg * u) / s[0] <= 1e-10
+    assert np.max(np.abs(out.V.T @ out.V - np.eye(100))) <= 1e-10
+    assert np.max(np.abs(out.U.T @ out.U - np.eye(100))) <= 1e-10
+    M.close()
+    ctx.close()
