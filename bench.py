@@ -241,6 +241,7 @@ def run_ours(args, w, rank, world, local_rank):
     # ---- max over ranks
     tmax, e2e_max = max_over_ranks([total_s, sum(e2e_ms) / len(e2e_ms)], dist, dev)
     krylov = measure_krylov(B, ctx, dev) if (rank == 0 and args.krylov) else None
+    table2 = measure_table2(B, dev) if (rank == 0 and args.table2) else None
     if rank == 0:
         value = job_throughput(args.steps, world, tmax)
         prof = aggregate_profile(stats)
@@ -268,6 +269,8 @@ def run_ours(args, w, rank, world, local_rank):
                               "Krylov solver, measured below",
             "krylov_workload": krylov,
         }
+        if table2 is not None:
+            line["exp3_table2"] = table2
         if args.cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w)
         print(json.dumps(line), flush=True)
@@ -327,6 +330,50 @@ def measure_krylov(B, ctx, dev, steps=3):
     return out
 
 
+def measure_table2(B, dev):
+    """Exp III (Sec. 4.3, Tables 1-2) on the digit-image stand-in: the eight intervals of
+    Table 1 (exterior [a, 1.01] with t = 21, 40, 79, 153; interior windows of t = 17, 39, 85,
+    158 values from the 41st), NT variant, N = 32, M = 4, L = 15, 30, 60, 120. Per interval:
+    the time of Steps 1-2, 3, 4, 5 and the total, the count, the largest sigma error against
+    the dense spectrum and the largest residual."""
+    import torch
+    A = synth.digits_like()
+    s = np.linalg.svd(A.to_dense(), compute_uv=False)
+    ctx = B.Context()
+    M = B.Matrix.from_csr(ctx, A)
+    rows = []
+    for kind, t, L in (("exterior", 21, 15), ("exterior", 40, 30), ("exterior", 79, 60), ("exterior", 153, 120),
+                       ("interior", 17, 15), ("interior", 39, 30), ("interior", 85, 60), ("interior", 158, 120)):
+        if kind == "exterior":
+            a, b = 0.5 * (s[t - 1] + s[t]), 1.01 * s[0]
+        else:
+            a, b, _ = synth.window_interval(s, 40, t)
+        truth = np.sort(s[(s >= a) & (s <= b)])
+        p = B.params(N=32, L=L, M=4, ell=1, variant="nt", norm_A=float(s[0]))
+        Vin = torch.from_numpy(synth.gaussian_block(A.n, L, 5)).to(dev)
+        ws = M.workspace(p)
+        for rep in range(2):   # the first solve warms up (graph capture)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            status, r = B.cmsvd_solve_interval(M.handle, a, b, p, Vin, ws)
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            st = B.cmsvd_result_stats(r)
+            k = B.cmsvd_result_count(r)
+            sig = np.zeros(k)
+            B.cmsvd_result_copy(r, sig)
+            B.cmsvd_result_destroy(r)
+        err = float(np.max(np.abs(sig - truth) / truth)) if k == truth.size and k else None
+        rows.append({"kind": kind, "a": float(a), "b": float(b), "t": int(truth.size), "L": L, "found": int(k),
+                     "ms_steps_1_2": st["ms_solve"], "ms_step_3": st["ms_truncate"], "ms_step_4": st["ms_qr"],
+                     "ms_step_5": st["ms_ritz"], "ms_total": 1e3 * wall, "lanczos_steps": int(st["krylov_iters"]),
+                     "sigma_rel_err": err, "max_res": st["max_res_u"]})
+    M.close()
+    ctx.close()
+    return {"description": "Exp III stand-in: 60000x784 digit-image matrix (synth.digits_like, ~150 nnz/row, "
+                           "||A||_2 = 1), Table 1 intervals, NT, N=32 M=4", "rows": rows}
+
+
 def aggregate_profile(stats):
     """Per kernel class: total event-timed ms and launches over the timed steps."""
     from paper_2109_13655_gb300 import binding as B
@@ -378,6 +425,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-krylov", dest="krylov", action="store_false",
                     help="skip the secondary FP64-vs-mixed measurement of the Krylov workload")
+    ap.add_argument("--table2", action="store_true",
+                    help="also run the eight Exp III intervals on the digit-image stand-in (minutes)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

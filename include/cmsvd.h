@@ -84,6 +84,10 @@ typedef struct cmsvd_params {
     int32_t refine;       /* Krylov solver: up to this many rounds of FP64 iterative refinement of every shifted
                              solve, R_j = X - (s_j I - A^T A) Y_j, (s_j I - A^T A) E_j = R_j, Y_j += E_j, until
                              max ||R_j|| / ||X|| <= tol_solve (default 0: none) */
+    int32_t estimate;     /* 1: also compute the residual estimate of Sec. 3.4.1 through S_+ = [S_1, ..., S_M]
+                             (Eq. residual; NT: Eq. res_nonlinear with mu from one exact residual), returned by
+                             cmsvd_result_copy_estimate. The exact residuals are always computed (default 0) */
+    int32_t pad_;         /* reserved, 0 */
 } cmsvd_params;
 
 /* Kernel classes of the prof_* statistics (index into the arrays). */
@@ -247,6 +251,19 @@ int cmsvd_moments(cmsvd_matrix* A, double a, double b, const cmsvd_params* p,
 int cmsvd_solve_interval(cmsvd_matrix* A, double a, double b, const cmsvd_params* p,
                          const double* V_in, void* workspace, size_t ws_bytes,
                          cmsvd_result** out);
+
+/*
+ * Residual estimate of Sec. 3.4.1 for every returned triplet (host or device memory, t
+ * doubles), relative to ||A||_2 like res_u. With scaled moment nodes m_j = (zeta_j - gamma)/rho,
+ * f(A^T A) S_k = rho S_{k+1} + gamma S_k (f(x) = x: Prop. 1, exact up to the solves; NT:
+ * f(x) = ln x, Eq. sk=aks_nonlinear, approximate), so with v = U_S1 q = S W_S1 Sigma_S1^{-1} q
+ *   r~_i = || rho S_+ W_S1 Sigma_S1^{-1} q_i + (gamma - f(sigma_i^2)) v_i || / sigma_i.
+ * Linear variant: the estimate is r~_i / ||A||_2 (equal to res_u up to rounding and solve error).
+ * NT: mu r~_i / ||A||_2 with mu = ||r_i'|| / ||r~_i'|| (Eq. res_nonlinear); i' is the candidate
+ * (sigma in [a, b], not spurious) with the largest r~ (the paper leaves i' open).
+ * CMSVD_NOT_SUPPORTED when the solve ran with estimate = 0.
+ */
+int cmsvd_result_copy_estimate(const cmsvd_result* r, double* res_est);
 
 /* Number of triplets found (t^). */
 int cmsvd_result_count(const cmsvd_result* r, int64_t* t);

@@ -218,7 +218,19 @@ class Result:
     all_phi: np.ndarray = field(default=None)    # every Ritz value, before selection
     all_tau: np.ndarray = field(default=None)
     all_res: np.ndarray = field(default=None)
-    res_est: np.ndarray = field(default=None)    # Eq. residual estimate (linear variant)
+    res_est: np.ndarray = field(default=None)    # residual estimate through S_+ (Sec. 3.4.1), / ||A||_2
+    res_tilde: np.ndarray = field(default=None)  # ||r~_i|| / ||A||_2 before the NT scaling mu
+
+
+def spectral_map(variant: str, x):
+    """f in f(A^T A) S_k = rho S_{k+1} + gamma S_k: f(x) = x for the linear variant (Prop. 1)
+    and f(x) = g^{-1}(x) = ln x for NT (Eq. sk=aks_nonlinear)."""
+    return x if variant == "linear" else np.log(x)
+
+
+def shifted_moment_operator(q: Quadrature, Splus: np.ndarray, Z: np.ndarray, V: np.ndarray) -> np.ndarray:
+    """f(A^T A) V for V = S W_S1 Sigma_S1^{-1} Q = S Z (Eq. residual): rho S_+ Z + gamma V."""
+    return q.rho * (Splus @ Z) + q.gamma * V
 
 
 def rayleigh_ritz(A, S: np.ndarray, a: float, b: float, L: int, M: int, delta: float,
@@ -242,14 +254,31 @@ def rayleigh_ritz(A, S: np.ndarray, a: float, b: float, L: int, M: int, delta: f
     # exact residuals (Sec. 3.4.1, first line)
     res_u = np.linalg.norm(A.T @ uh - vh * phi, axis=0) / norm_A
     res_v = np.linalg.norm(A @ vh - uh * phi, axis=0) / norm_A
-    # residual estimate through S_M (Eq. residual), linear variant with scaled moments:
-    # A^T A S' = rho S'_+ + gamma S', so A^T A U_S1 q = rho S'_+ W Sigma^-1 q + gamma U_S1 q.
-    res_est = None
-    if S_plus_last is not None and q is not None and q.variant == "linear":
+    # Residual estimate through S_+ (Sec. 3.4.1). With scaled moment nodes the shifted
+    # moments satisfy  f(A^T A) S'_k = rho S'_{k+1} + gamma S'_k,  with f(x) = x for the
+    # linear variant (Prop. 1, exact) and f(x) = g^{-1}(x) = ln x for NT (approximate,
+    # Eq. sk=aks_nonlinear). Since U_S1 = S' W_S1 Sigma_S1^{-1}:
+    #   f(A^T A) v = rho S'_+ W_S1 Sigma_S1^{-1} q + gamma v,   v = U_S1 q,
+    #   r~_i = || f(A^T A) v_i - f(sigma_i^2) v_i || / sigma_i      (Eq. residual).
+    # Linear: ||r_i|| = ||r~_i||. NT (Eq. res_nonlinear): ||r_i|| ~ mu ||r~_i|| with mu the
+    # ratio of one exact residual to its r~; the paper leaves the index i' open, and the
+    # candidate (in [a, b], not spurious) with the largest ||r~|| is taken.
+    res_est = rt = None
+    if S_plus_last is not None and q is not None:
         Splus = np.concatenate([S[:, L:], S_plus_last], axis=1)
         Wm = WSt[:r].T / sS[:r]
-        HV = q.rho * (Splus @ (Wm @ Q)) + q.gamma * vh
-        res_est = np.linalg.norm(HV - vh * phi ** 2, axis=0) / np.maximum(phi, 1e-300) / norm_A
+        FV = shifted_moment_operator(q, Splus, Wm @ Q, vh)
+        fphi = spectral_map(q.variant, np.maximum(phi, 1e-300) ** 2)
+        rt = np.linalg.norm(FV - vh * fphi, axis=0) / np.maximum(phi, 1e-300)
+        if q.variant == "linear":
+            res_est = rt / norm_A
+        else:
+            cand = np.nonzero((phi >= a) & (phi <= b) & (tau_rel >= eps_tau))[0]
+            res_est = np.full(phi.size, np.nan)
+            if cand.size:
+                ip = cand[np.argmax(rt[cand])]
+                if rt[ip] > 0:
+                    res_est = res_u[ip] * (rt / rt[ip])
     keep = (phi >= a) & (phi <= b) & (tau_rel >= eps_tau) & (res_u <= tol_triplet)
     idx = np.nonzero(keep)[0]
     idx = idx[np.argsort(phi[idx], kind="stable")]
@@ -262,7 +291,8 @@ def rayleigh_ritz(A, S: np.ndarray, a: float, b: float, L: int, M: int, delta: f
             U_out[:, c] *= -1.0
     return Result(phi[idx], U_out, V_out, res_u[idx], res_v[idx], tau_rel[idx], r, sS, S,
                   all_phi=phi, all_tau=tau_rel, all_res=res_u,
-                  res_est=None if res_est is None else res_est[idx])
+                  res_est=None if res_est is None else res_est[idx],
+                  res_tilde=None if rt is None else rt[idx] / norm_A)
 
 
 def solve_interval(A, a: float, b: float, N: int, L: int, M: int, V_in: np.ndarray,

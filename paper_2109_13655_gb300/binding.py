@@ -31,7 +31,7 @@ class cmsvd_params(C.Structure):
                 ("variant", C.c_int32), ("solver", C.c_int32), ("precision", C.c_int32),
                 ("max_iter", C.c_int32), ("tol_solve", C.c_double), ("tol_triplet", C.c_double),
                 ("norm_A", C.c_double), ("check_every", C.c_int32), ("direct_max_block", C.c_int32),
-                ("profile", C.c_int32), ("refine", C.c_int32)]
+                ("profile", C.c_int32), ("refine", C.c_int32), ("estimate", C.c_int32), ("pad_", C.c_int32)]
 
 PROFILE_CLASSES = ("spmm", "krylov", "direct", "gram", "gemm", "small_dense", "other", "jacobi")
 
@@ -78,6 +78,7 @@ _SIGS = {
                                        C.POINTER(_P)]),
     "cmsvd_result_count": (C.c_int, [_P, C.POINTER(_I64)]),
     "cmsvd_result_copy": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
+    "cmsvd_result_copy_estimate": (C.c_int, [_P, _P]),
     "cmsvd_result_stats": (C.c_int, [_P, C.POINTER(cmsvd_stats)]),
     "cmsvd_result_destroy": (C.c_int, [_P]),
 }
@@ -252,6 +253,10 @@ def cmsvd_result_copy(r: int, sigma=None, U=None, V=None, res_u=None, res_v=None
     _check(lib().cmsvd_result_copy(_P(r), *args), "cmsvd_result_copy")
 
 
+def cmsvd_result_copy_estimate(r: int, res_est) -> None:
+    _check(lib().cmsvd_result_copy_estimate(_P(r), _P(_ptr(res_est))), "cmsvd_result_copy_estimate")
+
+
 def cmsvd_result_stats(r: int) -> dict:
     st = cmsvd_stats()
     _check(lib().cmsvd_result_stats(_P(r), C.byref(st)), "cmsvd_result_stats")
@@ -273,6 +278,7 @@ class Triplets:
     tau: np.ndarray
     stats: dict
     status: int
+    res_est: np.ndarray | None = None   # Sec. 3.4.1 estimate, when solved with estimate=1
 
 
 class Context:
@@ -352,7 +358,11 @@ class Matrix:
             t = cmsvd_result_count(r)
             out = [np.zeros(t), np.zeros((t, self.m)), np.zeros((t, self.n)), np.zeros(t), np.zeros(t), np.zeros(t)]
             cmsvd_result_copy(r, *out)
+            est = None
+            if p.estimate:
+                est = np.zeros(t)
+                cmsvd_result_copy_estimate(r, est)
             st = cmsvd_result_stats(r)
         finally:
             cmsvd_result_destroy(r)
-        return Triplets(out[0], out[1].T.copy(), out[2].T.copy(), out[3], out[4], out[5], st, status)
+        return Triplets(out[0], out[1].T.copy(), out[2].T.copy(), out[3], out[4], out[5], st, status, est)

@@ -9,7 +9,6 @@
 namespace cmsvd {
 const char* last_error();
 size_t ritz_workspace(int64_t m, int64_t n, int c, int sm_count);
-struct RitzOut { double *sigma, *U, *V, *res_u, *res_v, *tau; };
 int rayleigh_ritz(cmsvd_matrix* M, const double* S, int64_t lds, int c, double a, double b, const cmsvd_params* p,
                   double normA, Arena& ws, const RitzOut& out, cmsvd_stats* st, cudaEvent_t* ev);
 }  // namespace cmsvd
@@ -75,6 +74,7 @@ int check_params(const cmsvd_matrix* A, double a, double b, const cmsvd_params* 
     if (!(p->alpha > 0.0)) { set_error("alpha must be > 0"); return CMSVD_INVALID_ARG; }
     if (p->max_iter < 1) { set_error("max_iter must be >= 1"); return CMSVD_INVALID_ARG; }
     if (p->refine < 0 || p->refine > 100) { set_error("refine must be in [0, 100]"); return CMSVD_INVALID_ARG; }
+    if (p->estimate != 0 && p->estimate != 1) { set_error("estimate must be 0 or 1"); return CMSVD_INVALID_ARG; }
     if (!(p->delta >= 0.0) || !(p->eps_tau >= 0.0) || !(p->tol_triplet > 0.0) || !(p->tol_solve > 0.0)) {
         set_error("delta, eps_tau >= 0 and tol_solve, tol_triplet > 0 required");
         return CMSVD_INVALID_ARG;
@@ -116,6 +116,7 @@ void plan_persistent(Arena& ws, const cmsvd_matrix* A, const cmsvd_params* p, Pl
         pl.out.res_u = ws.take<double>(c);
         pl.out.res_v = ws.take<double>(c);
         pl.out.tau = ws.take<double>(c);
+        pl.out.res_est = ws.take<double>(c);
     }
     pl.persistent = ws.off;
 }
@@ -232,6 +233,8 @@ int cmsvd_params_default(cmsvd_params* p) {
     p->direct_max_block = 32;
     p->profile = 0;
     p->refine = 0;
+    p->estimate = 0;
+    p->pad_ = 0;
     return CMSVD_OK;
 }
 
@@ -461,6 +464,7 @@ int cmsvd_solve_interval(cmsvd_matrix* A, double a, double b, const cmsvd_params
     r->res_u = pl.out.res_u;
     r->res_v = pl.out.res_v;
     r->tau = pl.out.tau;
+    r->res_est = p->estimate ? pl.out.res_est : nullptr;
     if (r->t > 0) {
         double* h = (double*)malloc(sizeof(double) * 2 * r->t);
         if (h) {
@@ -498,6 +502,15 @@ int cmsvd_result_copy(const cmsvd_result* r, double* sigma, double* U, double* V
     if (res_v) CM_CUDA(cudaMemcpyAsync(res_v, r->res_v, sizeof(double) * t, cudaMemcpyDefault, s));
     if (tau) CM_CUDA(cudaMemcpyAsync(tau, r->tau, sizeof(double) * t, cudaMemcpyDefault, s));
     CM_CUDA(cudaStreamSynchronize(s));
+    return CMSVD_OK;
+}
+
+int cmsvd_result_copy_estimate(const cmsvd_result* r, double* res_est) {
+    if (!r || !res_est) { set_error("NULL argument"); return CMSVD_INVALID_ARG; }
+    if (!r->res_est) { set_error("the solve ran without the residual estimate (estimate = 0)"); return CMSVD_NOT_SUPPORTED; }
+    if (r->t == 0) return CMSVD_OK;
+    CM_CUDA(cudaMemcpyAsync(res_est, r->res_est, sizeof(double) * (size_t)r->t, cudaMemcpyDefault, r->ctx->s));
+    CM_CUDA(cudaStreamSynchronize(r->ctx->s));
     return CMSVD_OK;
 }
 

@@ -7,7 +7,6 @@
 //     in step 5), which keeps the high relative accuracy of small singular values.
 // FP64 on this part runs on the FP64 pipe (no FP64 tensor-core path is used).
 #include "internal.cuh"
-#include <cooperative_groups.h>
 #include <mutex>
 
 namespace cmsvd {
@@ -380,8 +379,8 @@ __device__ __forceinline__ bool grid_barrier(unsigned* ctl, unsigned nblocks) {
         } else {
             long long it = 0;
             while (*gen == g && *err == 0) {
-                if (++it > 20000000LL) { atomicExch(ctl + 3, 1u); break; }   // ~1 s
-                __nanosleep(40);
+                if (++it > 20000000LL) { atomicExch(ctl + 3, 1u); break; }   // >= 0.8 s
+                if (it > 2048) __nanosleep(40);   // poll hot first: a round lasts microseconds
             }
         }
         __threadfence();
@@ -390,49 +389,115 @@ __device__ __forceinline__ bool grid_barrier(unsigned* ctl, unsigned nblocks) {
     return *(volatile unsigned*)(ctl + 3) == 0;
 }
 
-__global__ void __launch_bounds__(128) k_jacobi_coop(double* __restrict__ Xc, double* __restrict__ V, int rows, int cols,
-                                                     int np, double tol, const double* __restrict__ fro2, int max_sweeps,
-                                                     unsigned* ctl, unsigned* rot) {
-    __shared__ double sh[3][4];
+constexpr int JC_MAXDIM = 512;              // L M <= 512
+
+// Block-cyclic cooperative form: columns are grouped in blocks of JB; CTA k holds two
+// blocks per round (round-robin over the NB blocks), stages them and their V columns in
+// shared memory, rotates every column of the first against every column of the second
+// (JB inner rounds of JB disjoint pairs, one warp per pair) and, in round 0, the pairs
+// inside each block, then writes them back. A sweep needs NB - 1 grid barriers instead of
+// cols - 1, and each CTA does JB^2 rotations per barrier. Every column pair meets once per
+// sweep, as in the cyclic method.
+constexpr int JB = 4;
+__device__ __forceinline__ bool jb_rotate(double* xa, double* xb, double* va, double* vb, int rows, int cols, double tol,
+                                          double negl, int lane) {
+    double al = 0.0, be = 0.0, ga = 0.0;
+    for (int e = lane; e < rows; e += 32) {
+        const double a = xa[e], b = xb[e];
+        al = __fma_rn(a, a, al);
+        be = __fma_rn(b, b, be);
+        ga = __fma_rn(a, b, ga);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {   // butterfly: every lane ends with the same sums
+        al += __shfl_xor_sync(0xffffffffu, al, o);
+        be += __shfl_xor_sync(0xffffffffu, be, o);
+        ga += __shfl_xor_sync(0xffffffffu, ga, o);
+    }
+    if (!(fabs(ga) > tol * sqrt(al * be) && al > negl && be > negl)) return false;
+    const double zeta = (be - al) / (2.0 * ga);
+    const double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+    const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
+    for (int e = lane; e < rows; e += 32) {
+        const double a = xa[e], b = xb[e];
+        xa[e] = cs * a - sn * b;
+        xb[e] = sn * a + cs * b;
+    }
+    for (int e = lane; e < cols; e += 32) {
+        const double a = va[e], b = vb[e];
+        va[e] = cs * a - sn * b;
+        vb[e] = sn * a + cs * b;
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(32 * JB) k_jacobi_blk(double* __restrict__ Xc, double* __restrict__ V, int rows, int cols,
+                                                        int nb, double tol, const double* __restrict__ fro2, int max_sweeps,
+                                                        unsigned* ctl, unsigned* rot) {
+    extern __shared__ double jb_smem[];
+    double* Xs = jb_smem;                        // [2][JB][rows]
+    double* Vs = Xs + 2 * JB * rows;             // [2][JB][cols]
+    __shared__ int any_rot;
     const double negl = 1e-36 * *fro2;
-    const int k = blockIdx.x;
+    const int k = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int xsz = JB * rows, vsz = JB * cols;
     int sweep = 0;
     for (; sweep < max_sweeps; ++sweep) {
-        for (int round = 0; round < np - 1; ++round) {
-            int p, q;
-            if (k == 0) { p = round; q = np - 1; }
-            else { p = (round + k) % (np - 1); q = (round - k + (np - 1)) % (np - 1); }
-            if (p < cols && q < cols) {
-                if (p > q) { const int t = p; p = q; q = t; }
-                double* xp = Xc + (size_t)p * rows;
-                double* xq = Xc + (size_t)q * rows;
-                double al = 0.0, be = 0.0, ga = 0.0;
-                for (int i = threadIdx.x; i < rows; i += 128) {
-                    const double a = __ldcg(xp + i), b = __ldcg(xq + i);
-                    al = __fma_rn(a, a, al);
-                    be = __fma_rn(b, b, be);
-                    ga = __fma_rn(a, b, ga);
+        for (int round = 0; round < nb - 1; ++round) {
+            int P, Q;
+            if (k == 0) { P = round; Q = nb - 1; }
+            else { P = (round + k) % (nb - 1); Q = (round - k + (nb - 1)) % (nb - 1); }
+            for (int idx = threadIdx.x; idx < 2 * xsz; idx += blockDim.x) {
+                const int slot = idx / xsz, rem = idx - slot * xsz, i = rem / rows, e = rem - i * rows;
+                const int g = (slot ? Q : P) * JB + i;
+                Xs[idx] = g < cols ? __ldcg(Xc + (size_t)g * rows + e) : 0.0;
+            }
+            for (int idx = threadIdx.x; idx < 2 * vsz; idx += blockDim.x) {
+                const int slot = idx / vsz, rem = idx - slot * vsz, i = rem / cols, e = rem - i * cols;
+                const int g = (slot ? Q : P) * JB + i;
+                Vs[idx] = g < cols ? __ldcg(V + (size_t)g * cols + e) : 0.0;
+            }
+            if (threadIdx.x == 0) any_rot = 0;
+            __syncthreads();
+            bool rotated = false;
+            if (round == 0) {
+                for (int t = 0; t < JB - 1; ++t) {   // pairs inside each block
+                    const int slot = warp / (JB / 2), u = warp - slot * (JB / 2);
+                    int i, j;
+                    if (u == 0) { i = t; j = JB - 1; }
+                    else { i = (t + u) % (JB - 1); j = (t - u + JB - 1) % (JB - 1); }
+                    if (i > j) { const int tmp = i; i = j; j = tmp; }
+                    double* xb0 = Xs + slot * xsz;
+                    double* vb0 = Vs + slot * vsz;
+                    rotated |= jb_rotate(xb0 + i * rows, xb0 + j * rows, vb0 + i * cols, vb0 + j * cols, rows, cols, tol, negl, lane);
+                    __syncthreads();
                 }
-                block_sum3_128(al, be, ga, sh);
-                if (fabs(ga) > tol * sqrt(al * be) && al > negl && be > negl) {
-                    const double zeta = (be - al) / (2.0 * ga);
-                    const double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                    const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
-                    for (int i = threadIdx.x; i < rows; i += 128) {
-                        const double a = __ldcg(xp + i), b = __ldcg(xq + i);
-                        xp[i] = cs * a - sn * b;
-                        xq[i] = sn * a + cs * b;
-                    }
-                    double* vp = V + (size_t)p * cols;
-                    double* vq = V + (size_t)q * cols;
-                    for (int i = threadIdx.x; i < cols; i += 128) {
-                        const double va = __ldcg(vp + i), vb = __ldcg(vq + i);
-                        vp[i] = cs * va - sn * vb;
-                        vq[i] = sn * va + cs * vb;
-                    }
-                    if (threadIdx.x == 0) atomicExch(rot + sweep, 1u);
+            }
+            for (int t = 0; t < JB; ++t) {           // first block against second
+                const int i = warp, j = (warp + t) % JB;
+                double *xa = Xs + i * rows, *xb = Xs + xsz + j * rows;
+                double *va = Vs + i * cols, *vb = Vs + vsz + j * cols;
+                if (P > Q) {
+                    double* tmp = xa; xa = xb; xb = tmp;
+                    tmp = va; va = vb; vb = tmp;
                 }
-                __syncthreads();   // sh reused by the next round
+                rotated |= jb_rotate(xa, xb, va, vb, rows, cols, tol, negl, lane);
+                __syncthreads();
+            }
+            if (rotated && lane == 0) any_rot = 1;
+            __syncthreads();
+            if (any_rot) {
+                for (int idx = threadIdx.x; idx < 2 * xsz; idx += blockDim.x) {
+                    const int slot = idx / xsz, rem = idx - slot * xsz, i = rem / rows, e = rem - i * rows;
+                    const int g = (slot ? Q : P) * JB + i;
+                    if (g < cols) Xc[(size_t)g * rows + e] = Xs[idx];
+                }
+                for (int idx = threadIdx.x; idx < 2 * vsz; idx += blockDim.x) {
+                    const int slot = idx / vsz, rem = idx - slot * vsz, i = rem / cols, e = rem - i * cols;
+                    const int g = (slot ? Q : P) * JB + i;
+                    if (g < cols) V[(size_t)g * cols + e] = Vs[idx];
+                }
+                if (threadIdx.x == 0) atomicExch(rot + sweep, 1u);
             }
             if (!grid_barrier(ctl, gridDim.x)) return;
         }
@@ -460,218 +525,6 @@ __global__ void __launch_bounds__(1024) k_jacobi_finish(const double* __restrict
             perm[j + 1] = key;
         }
     }
-}
-
-// Block-cyclic form in one thread-block cluster (cols and rows <= 256). The columns are
-// split into JC_NB = 2 JC_CL blocks of bs columns (bs even; columns past cols are zero and
-// never rotate). Each CTA keeps two blocks of Xc and of V in its shared memory. A sweep is
-// JC_NB - 1 block rounds of a round-robin tournament of the blocks: in block round r, CTA k
-// rotates every column of its first block against every column of its second (bs inner
-// rounds of bs disjoint pairs, one warp per pair), and in block round 0 also the pairs
-// inside each block (bs - 1 inner rounds). Every column pair meets once per sweep, as in the
-// cyclic method. Between block rounds the blocks move to the CTAs that need them through
-// distributed shared memory, staged in registers so that no second buffer is needed; the
-// cluster's hardware barrier orders the moves, and no thread spins on memory.
-namespace cgr = cooperative_groups;
-constexpr int JC_CL = 8;
-constexpr int JC_NB = 2 * JC_CL;
-constexpr int JC_THREADS = 512;
-constexpr int JC_MAXDIM = 256;
-constexpr int JC_MAXBS = JC_MAXDIM / JC_NB;                       // 16 columns per block
-constexpr int JC_STAGE = 2 * JC_MAXBS * JC_MAXDIM / JC_THREADS;   // 2 blocks of <= 16 x 256 per 512 threads
-
-__device__ __forceinline__ void jc_pair(int k, int r, int& P, int& Q) {
-    if (k == 0) { P = r; Q = JC_NB - 1; }
-    else { P = (r + k) % (JC_NB - 1); Q = (r - k + (JC_NB - 1)) % (JC_NB - 1); }
-}
-
-// One warp: orthogonalize columns a and b (a has the lower global index). Returns true when
-// it rotated. The butterfly sums are identical on every lane (each step adds the same two
-// values in either order).
-__device__ __forceinline__ bool jc_rotate(double* xa, double* xb, double* va, double* vb, int rows, int cols, double tol,
-                                          double negl, int lane) {
-    double al = 0.0, be = 0.0, ga = 0.0;
-    for (int e = lane; e < rows; e += 32) {
-        const double a = xa[e], b = xb[e];
-        al = __fma_rn(a, a, al);
-        be = __fma_rn(b, b, be);
-        ga = __fma_rn(a, b, ga);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        al += __shfl_xor_sync(0xffffffffu, al, o);
-        be += __shfl_xor_sync(0xffffffffu, be, o);
-        ga += __shfl_xor_sync(0xffffffffu, ga, o);
-    }
-    if (!(fabs(ga) > tol * sqrt(al * be) && al > negl && be > negl)) return false;
-    const double zeta = (be - al) / (2.0 * ga);
-    const double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-    const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
-    for (int e = lane; e < rows; e += 32) {
-        const double a = xa[e], b = xb[e];
-        xa[e] = cs * a - sn * b;
-        xb[e] = sn * a + cs * b;
-    }
-    for (int e = lane; e < cols; e += 32) {
-        const double a = va[e], b = vb[e];
-        va[e] = cs * a - sn * b;
-        vb[e] = sn * a + cs * b;
-    }
-    return true;
-}
-
-// Moves the two blocks that CTA k needs in block round nr from where they sit in round r.
-__device__ __forceinline__ void jc_move(cgr::cluster_group& cl, double* buf, int bsz, int k, int r, int nr) {
-    int nP, nQ;
-    jc_pair(k, nr, nP, nQ);
-    int sP = 0, oP = 0, sQ = 0, oQ = 0;   // source CTA and slot of each block
-    for (int kk = 0; kk < JC_CL; ++kk) {
-        int a, b;
-        jc_pair(kk, r, a, b);
-        if (a == nP) { sP = kk; oP = 0; }
-        if (b == nP) { sP = kk; oP = 1; }
-        if (a == nQ) { sQ = kk; oQ = 0; }
-        if (b == nQ) { sQ = kk; oQ = 1; }
-    }
-    const double* src0 = cl.map_shared_rank(buf, (unsigned)sP) + oP * bsz;
-    const double* src1 = cl.map_shared_rank(buf, (unsigned)sQ) + oQ * bsz;
-    double stage[JC_STAGE];
-#pragma unroll
-    for (int it = 0; it < JC_STAGE; ++it) {
-        const int idx = (int)threadIdx.x + it * JC_THREADS;
-        if (idx < 2 * bsz) stage[it] = idx < bsz ? src0[idx] : src1[idx - bsz];
-    }
-    cl.sync();   // every CTA has read what it needs from buf
-#pragma unroll
-    for (int it = 0; it < JC_STAGE; ++it) {
-        const int idx = (int)threadIdx.x + it * JC_THREADS;
-        if (idx < 2 * bsz) buf[idx] = stage[it];
-    }
-}
-
-__global__ void __launch_bounds__(JC_THREADS) k_jacobi_cluster(double* __restrict__ Xc, double* __restrict__ V, int rows,
-                                                               int cols, int bs, double tol, const double* __restrict__ fro2,
-                                                               int max_sweeps, unsigned* __restrict__ ctl) {
-    extern __shared__ double jc_smem[];
-    __shared__ unsigned rotflag[2];
-    cgr::cluster_group cl = cgr::this_cluster();
-    const int k = (int)cl.block_rank();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int xsz = bs * rows, vsz = bs * cols;   // one block of Xc / of V
-    double* Xs = jc_smem;                          // [2][bs][rows]
-    double* Vs = Xs + 2 * xsz;                     // [2][bs][cols]
-    const double negl = 1e-36 * *fro2;
-    int P, Q;
-    jc_pair(k, 0, P, Q);
-    for (int idx = threadIdx.x; idx < 2 * xsz; idx += JC_THREADS) {
-        const int slot = idx / xsz, rem = idx - slot * xsz, i = rem / rows, e = rem - i * rows;
-        const int g = (slot ? Q : P) * bs + i;
-        Xs[idx] = g < cols ? Xc[(size_t)g * rows + e] : 0.0;
-    }
-    for (int idx = threadIdx.x; idx < 2 * vsz; idx += JC_THREADS) {
-        const int slot = idx / vsz, rem = idx - slot * vsz, i = rem / cols, e = rem - i * cols;
-        const int g = (slot ? Q : P) * bs + i;
-        Vs[idx] = g < cols ? V[(size_t)g * cols + e] : 0.0;
-    }
-    if (threadIdx.x == 0) { rotflag[0] = 0u; rotflag[1] = 0u; }
-    cl.sync();
-    int sweep = 0, r = 0;
-    const int half = bs / 2;
-    for (;;) {
-        const int par = sweep & 1;
-        if (r == 0) {
-            for (int t = 0; t < bs - 1; ++t) {   // pairs inside each block
-                if (warp < bs) {
-                    const int slot = warp / half, u = warp - slot * half;
-                    int i, j;
-                    if (u == 0) { i = t; j = bs - 1; }
-                    else { i = (t + u) % (bs - 1); j = (t - u + bs - 1) % (bs - 1); }
-                    if (i > j) { const int tmp = i; i = j; j = tmp; }
-                    double* xb0 = Xs + slot * xsz;
-                    double* vb0 = Vs + slot * vsz;
-                    if (jc_rotate(xb0 + i * rows, xb0 + j * rows, vb0 + i * cols, vb0 + j * cols, rows, cols, tol, negl, lane) &&
-                        lane == 0)
-                        rotflag[par] = 1u;
-                }
-                __syncthreads();
-            }
-        }
-        for (int t = 0; t < bs; ++t) {   // first block against second
-            if (warp < bs) {
-                const int i = warp, j = (warp + t) % bs;
-                double *xa = Xs + i * rows, *xb = Xs + xsz + j * rows;
-                double *va = Vs + i * cols, *vb = Vs + vsz + j * cols;
-                if (P > Q) {
-                    double* tmp = xa; xa = xb; xb = tmp;
-                    tmp = va; va = vb; vb = tmp;
-                }
-                if (jc_rotate(xa, xb, va, vb, rows, cols, tol, negl, lane) && lane == 0) rotflag[par] = 1u;
-            }
-            __syncthreads();
-        }
-        cl.sync();   // the round's rotations are complete and visible across the cluster
-        int nr = r + 1, nsweep = sweep;
-        if (nr == JC_NB - 1) {
-            // end of a sweep: every CTA reads every flag, so every CTA takes the same decision
-            unsigned any = 0u;
-            for (int kk = 0; kk < JC_CL; ++kk) any |= *cl.map_shared_rank(&rotflag[par], (unsigned)kk);
-            nsweep = sweep + 1;
-            if (any == 0u || nsweep >= max_sweeps) { sweep = nsweep; break; }
-            nr = 0;
-            if (threadIdx.x == 0) rotflag[par ^ 1] = 0u;   // read by nobody until the next sweep ends
-        }
-        jc_move(cl, Xs, xsz, k, r, nr);
-        jc_move(cl, Vs, vsz, k, r, nr);
-        __syncthreads();
-        jc_pair(k, nr, P, Q);
-        r = nr;
-        sweep = nsweep;
-    }
-    for (int idx = threadIdx.x; idx < 2 * xsz; idx += JC_THREADS) {
-        const int slot = idx / xsz, rem = idx - slot * xsz, i = rem / rows, e = rem - i * rows;
-        const int g = (slot ? Q : P) * bs + i;
-        if (g < cols) Xc[(size_t)g * rows + e] = Xs[idx];
-    }
-    for (int idx = threadIdx.x; idx < 2 * vsz; idx += JC_THREADS) {
-        const int slot = idx / vsz, rem = idx - slot * vsz, i = rem / cols, e = rem - i * cols;
-        const int g = (slot ? Q : P) * bs + i;
-        if (g < cols) V[(size_t)g * cols + e] = Vs[idx];
-    }
-    if (k == 0 && threadIdx.x == 0) ctl[2] = (unsigned)sweep;
-}
-
-// Launch shape of the cluster form, checked once per process: the GPU must be able to place
-// one cluster of JC_CL CTAs with 2 bs (rows + cols) doubles of shared memory each.
-static bool jc_available(int bs, int rows, int cols, size_t* smem) {
-    static std::once_flag once;
-    static bool ok = false;
-    const size_t max_smem = sizeof(double) * 2 * JC_MAXBS * 2 * JC_MAXDIM;
-    std::call_once(once, [&] {
-        if (cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem) != cudaSuccess) {
-            cudaGetLastError();
-            return;
-        }
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(JC_CL);
-        cfg.blockDim = dim3(JC_THREADS);
-        cfg.dynamicSmemBytes = max_smem;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = JC_CL;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        int nclusters = 0;
-        if (cudaOccupancyMaxActiveClusters(&nclusters, (const void*)k_jacobi_cluster, &cfg) != cudaSuccess) {
-            cudaGetLastError();
-            return;
-        }
-        ok = nclusters > 0;
-    });
-    *smem = sizeof(double) * 2 * (size_t)bs * (rows + cols);
-    return ok && rows <= JC_MAXDIM && cols <= JC_MAXDIM && bs <= JC_MAXBS && 2 * bs * rows <= JC_STAGE * JC_THREADS &&
-           2 * bs * cols <= JC_STAGE * JC_THREADS;
 }
 
 // Rotates the columns of Bm (trans = 0; Bm V = Xc) or of Bm^T (trans = 1; Bm^T V = Xc,
@@ -726,35 +579,25 @@ int jacobi_svd(const double* Bm, int brows, int bcols, int trans, double* Xc, do
     unsigned* rot = jac_ctl + 4;
     const int max_sweeps = 40;
     CM_CUDA(cudaMemsetAsync(ctl, 0, sizeof(unsigned) * (4 + max_sweeps), s));
-    int bs = (cols + JC_NB - 1) / JC_NB;
-    bs += bs & 1;
-    size_t jc_smem_bytes = 0;
-    bool use_cluster = jc_available(bs, rows, cols, &jc_smem_bytes);
-    if (use_cluster) {
-        ProfScope ps(CMSVD_PROF_JACOBI, s, 0.0, 0.0, 1);
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(JC_CL);
-        cfg.blockDim = dim3(JC_THREADS);
-        cfg.dynamicSmemBytes = jc_smem_bytes;
-        cfg.stream = s;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = JC_CL;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        CM_CUDA(cudaLaunchKernelEx(&cfg, k_jacobi_cluster, Xc, V, rows, cols, bs, tol, (const double*)fro2, max_sweeps, ctl));
-        note_launch();
-    }
-    int grid = np / 2;
-    if (!use_cluster) {
+    if (rows > JC_MAXDIM || cols > JC_MAXDIM) { set_error("Jacobi SVD supports at most %d rows and columns", JC_MAXDIM); return CMSVD_NOT_SUPPORTED; }
+    // block-cyclic form: nb blocks of JB columns (nb even), nb / 2 CTAs
+    int nb = (cols + JB - 1) / JB;
+    nb += nb & 1;
+    const int grid = nb / 2;
+    const size_t smem = sizeof(double) * 2 * JB * ((size_t)rows + cols);
+    {
+        static int set_attr = 0;
+        if (!set_attr) {
+            CM_CUDA(cudaFuncSetAttribute(k_jacobi_blk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(double) * 2 * JB * 2 * JC_MAXDIM)));
+            set_attr = 1;
+        }
         int per_sm = 0;
-        CM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_coop, 128, 0));
+        CM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_blk, 32 * JB, smem));
         if (per_sm * ctx->sm_count < grid) { set_error("Jacobi grid of %d CTAs cannot be co-resident", grid); return CMSVD_NOT_SUPPORTED; }
         ProfScope ps(CMSVD_PROF_JACOBI, s, 0.0, 0.0, 1);
-        void* args[] = {&Xc, &V, (void*)&rows, (void*)&cols, (void*)&np, (void*)&tol, &fro2, (void*)&max_sweeps, &ctl, &rot};
-        CM_CUDA(cudaLaunchCooperativeKernel((const void*)k_jacobi_coop, dim3(grid), dim3(128), args, 0, s));
+        void* args[] = {&Xc, &V, (void*)&rows, (void*)&cols, (void*)&nb, (void*)&tol, &fro2, (void*)&max_sweeps, &ctl, &rot};
+        CM_CUDA(cudaLaunchCooperativeKernel((const void*)k_jacobi_blk, dim3(grid), dim3(32 * JB), args, smem, s));
         note_launch();
     }
     unsigned h[4];
@@ -778,35 +621,190 @@ int jacobi_svd(const double* Bm, int brows, int bcols, int trans, double* Xc, do
 }
 
 // ----------------------------------------------------------------------------- orthogonalization
-// Deflation: with G = Q2^T Q2 = Rb^T Rb and Rb^T = Xj diag(sv) V^T... (Jacobi on Rb^T),
-// Rb = V diag(sv) W^T with W_j = Xj_j / sv_j, so G = W diag(sv^2) W^T. Keep the
-// directions with sv_k^2 > keep * sv_max^2: T3 = W_g diag(1/sv_g) (c x c') and
-// R3 = diag(sv_g) W_g^T (c' x c).
-__global__ void k_deflate(const double* __restrict__ Xj, const double* __restrict__ sv, const int* __restrict__ perm, int c,
-                          double keep, double* __restrict__ T3, double* __restrict__ R3, int* __restrict__ cp_out) {
-    __shared__ int cp;
+
+// min over max of the diagonal of an upper-triangular R (condition estimate of CholeskyQR)
+// Cooperative blocked form of k_chol for larger c (same result up to rounding order):
+// panels of CB = 32 rows. Per panel: CTA 0 factors the diagonal block; every thread of the
+// grid solves one column of the panel row R12 = R11^{-T} A12; the grid updates the upper
+// triangle of the trailing block, A22 -= R12^T R12. GB300 issues only 2 FP64 FMA per clock
+// per SM, so the c^3/6 multiply-adds are spread over the whole grid. The grid barrier
+// between phases is bounded (ctl[3] = 1 on timeout; every CTA then returns).
+constexpr int CB = 32;
+__global__ void __launch_bounds__(256) k_chol_coop(const double* __restrict__ G, int c, double shift_coef,
+                                                   double* __restrict__ R, int* flag, unsigned* ctl) {
+    __shared__ double sh_tr;
     const int t = threadIdx.x;
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + t, gthreads = (int64_t)gridDim.x * blockDim.x;
     if (t == 0) {
-        const double s0 = sv[perm[0]];
-        int k = 0;
-        while (k < c && sv[perm[k]] * sv[perm[k]] > keep * s0 * s0) ++k;
-        cp = k;
-        *cp_out = k;
+        double tr = 0.0;
+        for (int i = 0; i < c; ++i) tr += G[(size_t)i * c + i];
+        sh_tr = tr;
     }
     __syncthreads();
-    const int k = cp;
-    for (int e = t; e < c * k; e += blockDim.x) {
-        const int i = e / k, g = e % k;               // T3 row-major c x k
-        const int j = perm[g];
-        T3[e] = Xj[(size_t)j * c + i] / (sv[j] * sv[j]);
+    const double shift = shift_coef * sh_tr;
+    const double floor_ = 1e-300 + 1e-32 * sh_tr;
+    for (int64_t e = gtid; e < (int64_t)c * c; e += gthreads) {
+        const int i = (int)(e / c), j = (int)(e % c);
+        R[e] = j >= i ? G[e] + (i == j ? shift : 0.0) : 0.0;
     }
-    for (int e = t; e < k * c; e += blockDim.x) {
-        const int g = e / c, i = e % c;               // R3 row-major k x c
-        R3[e] = Xj[(size_t)perm[g] * c + i];
+    if (!grid_barrier(ctl, gridDim.x)) return;
+    for (int k0 = 0; k0 < c; k0 += CB) {
+        const int b = min(CB, c - k0), w = c - k0 - b;
+        if (blockIdx.x == 0) {   // diagonal block, right-looking in place
+            __shared__ double sh_piv;
+            for (int kk = k0; kk < k0 + b; ++kk) {
+                if (t == 0) {
+                    double p = R[(size_t)kk * c + kk];
+                    if (!(p > floor_)) {
+                        atomicOr(flag, 1);
+                        p = floor_;
+                    }
+                    p = sqrt(p);
+                    R[(size_t)kk * c + kk] = p;
+                    sh_piv = p;
+                }
+                __syncthreads();
+                const double piv = sh_piv;
+                for (int j = kk + 1 + t; j < k0 + b; j += blockDim.x) R[(size_t)kk * c + j] /= piv;
+                __syncthreads();
+                const int wb = k0 + b - kk - 1;
+                for (int e = t; e < wb * wb; e += blockDim.x) {
+                    const int i = kk + 1 + e / wb, j = kk + 1 + e % wb;
+                    if (j >= i) R[(size_t)i * c + j] = __fma_rn(-R[(size_t)kk * c + i], R[(size_t)kk * c + j], R[(size_t)i * c + j]);
+                }
+                __syncthreads();
+            }
+        }
+        if (!grid_barrier(ctl, gridDim.x)) return;
+        if (w == 0) break;
+        // panel row: column j of R12 solves R11^T x = A12(:, j) (forward substitution)
+        for (int64_t jj = gtid; jj < w; jj += gthreads) {
+            const int j = k0 + b + (int)jj;
+            for (int i = k0; i < k0 + b; ++i) {
+                double acc = R[(size_t)i * c + j];
+                for (int q = k0; q < i; ++q) acc = __fma_rn(-R[(size_t)q * c + i], R[(size_t)q * c + j], acc);
+                R[(size_t)i * c + j] = acc / R[(size_t)i * c + i];
+            }
+        }
+        if (!grid_barrier(ctl, gridDim.x)) return;
+        // trailing update of the upper triangle
+        for (int64_t e = gtid; e < (int64_t)w * w; e += gthreads) {
+            const int i = k0 + b + (int)(e / w), j = k0 + b + (int)(e % w);
+            if (j < i) continue;
+            double acc = R[(size_t)i * c + j];
+            for (int q = k0; q < k0 + b; ++q) acc = __fma_rn(-R[(size_t)q * c + i], R[(size_t)q * c + j], acc);
+            R[(size_t)i * c + j] = acc;
+        }
+        if (!grid_barrier(ctl, gridDim.x)) return;
     }
 }
 
-// min over max of the diagonal of an upper-triangular R (condition estimate of CholeskyQR)
+// Deflation by Cholesky with diagonal pivoting of G = T^T T (c <= 512, one CTA): at step k
+// the largest remaining diagonal entry is brought to position k; the factorization stops
+// when it is <= keep * max diag(G). Then P^T G P ~ L L^T with L (c x c') and a discarded
+// Schur complement of trace <= (c - c') keep max diag(G). Outputs, as k_deflate's:
+// T3 = P_1 L11^{-T} (c x c', so (T T3)^T (T T3) = I) and R3 = L^T P^T (c' x c, T ~ T T3 R3).
+// W and L are c x c scratch. Ties pick the smaller index, so the result is deterministic.
+__global__ void __launch_bounds__(1024) k_pchol_deflate(const double* __restrict__ G, int c, double keep,
+                                                        double* __restrict__ W, double* __restrict__ L,
+                                                        double* __restrict__ T3, double* __restrict__ R3,
+                                                        int* __restrict__ cp_out) {
+    __shared__ int perm[512];
+    __shared__ double rv[32];
+    __shared__ int ri[32];
+    __shared__ double sh_d0, sh_piv;
+    __shared__ int sh_j;
+    const int t = threadIdx.x, nt = blockDim.x, lane = t & 31, warp = t >> 5, nw = nt >> 5;
+    for (int e = t; e < c * c; e += nt) {
+        W[e] = G[e];
+        L[e] = 0.0;
+    }
+    for (int i = t; i < c; i += nt) perm[i] = i;
+    __syncthreads();
+    int k = 0;
+    for (; k <= c; ++k) {
+        // argmax of the remaining diagonal (k == 0 also gives max diag(G))
+        double best = -1.0;
+        int bi = c;
+        for (int i = k + t; i < c; i += nt) {
+            const double d = W[(size_t)i * c + i];
+            if (d > best) { best = d; bi = i; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+            if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if (lane == 0) { rv[warp] = best; ri[warp] = bi; }
+        __syncthreads();
+        if (t == 0) {
+            double bv = rv[0];
+            int bj = ri[0];
+            for (int w = 1; w < nw; ++w)
+                if (rv[w] > bv || (rv[w] == bv && ri[w] < bj)) { bv = rv[w]; bj = ri[w]; }
+            if (k == 0) sh_d0 = bv;
+            sh_piv = bv;
+            sh_j = bj;
+        }
+        __syncthreads();
+        const int j = sh_j;
+        const double d = sh_piv;
+        if (k == c || !(d > keep * sh_d0)) break;
+        if (j != k) {   // symmetric swap of rows/columns k and j, and of the rows of L done so far
+            for (int col = t; col < c; col += nt) {
+                const double a = W[(size_t)k * c + col];
+                W[(size_t)k * c + col] = W[(size_t)j * c + col];
+                W[(size_t)j * c + col] = a;
+            }
+            __syncthreads();
+            for (int row = t; row < c; row += nt) {
+                const double a = W[(size_t)row * c + k];
+                W[(size_t)row * c + k] = W[(size_t)row * c + j];
+                W[(size_t)row * c + j] = a;
+            }
+            for (int col = t; col < k; col += nt) {
+                const double a = L[(size_t)k * c + col];
+                L[(size_t)k * c + col] = L[(size_t)j * c + col];
+                L[(size_t)j * c + col] = a;
+            }
+            if (t == 0) {
+                const int a = perm[k];
+                perm[k] = perm[j];
+                perm[j] = a;
+            }
+            __syncthreads();
+        }
+        const double lkk = sqrt(d);
+        for (int i = k + t; i < c; i += nt) L[(size_t)i * c + k] = i == k ? lkk : W[(size_t)i * c + k] / lkk;
+        __syncthreads();
+        const int w = c - k - 1;
+        for (int e = t; e < w * w; e += nt) {
+            const int i = k + 1 + e / w, jj = k + 1 + e % w;
+            W[(size_t)i * c + jj] = __fma_rn(-L[(size_t)i * c + k], L[(size_t)jj * c + k], W[(size_t)i * c + jj]);
+        }
+        __syncthreads();
+    }
+    const int cp = k;
+    if (t == 0) *cp_out = cp;
+    // L11^{-1} (lower) into W, one column per thread by forward substitution
+    for (int jc = t; jc < cp; jc += nt) {
+        for (int i = jc; i < cp; ++i) {
+            double acc = i == jc ? 1.0 : 0.0;
+            for (int q = jc; q < i; ++q) acc = __fma_rn(-L[(size_t)i * c + q], W[(size_t)q * c + jc], acc);
+            W[(size_t)i * c + jc] = acc / L[(size_t)i * c + i];
+        }
+    }
+    __syncthreads();
+    for (int e = t; e < c * cp; e += nt) {       // T3 row-major c x cp: row perm[r] = row r of L11^{-T}
+        const int r = e / cp, i = e % cp;
+        T3[(size_t)perm[r] * cp + i] = (r < cp && i >= r) ? W[(size_t)i * c + r] : 0.0;
+    }
+    for (int e = t; e < cp * c; e += nt) {       // R3 row-major cp x c: R3[i][perm[r]] = L[r][i]
+        const int i = e / c, r = e % c;
+        R3[(size_t)i * c + perm[r]] = r >= i ? L[(size_t)r * c + i] : 0.0;
+    }
+}
+
 __global__ void k_diag_ratio(const double* __restrict__ R, int c, double* __restrict__ out) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     double lo = 1e300, hi = 0.0;
@@ -830,7 +828,29 @@ struct OrthCtx {
     size_t pcap;
     int* flag;       // device int
     int64_t n;
+    unsigned* ctl;   // 4 device words for the cooperative Cholesky
 };
+
+// Launches k_chol (c <= 64) or k_chol_coop; ctl: 4 device words of scratch.
+int chol_launch(cmsvd_context* ctx, cudaStream_t s, const double* G, int c, double coef, double* R, int* flag,
+                unsigned* ctl) {
+    CM_CUDA(cudaMemsetAsync(ctl, 0, 4 * sizeof(unsigned), s));
+    ProfScope ps(CMSVD_PROF_SMALL, s, 16.0 * c * c, c * (double)c * c / 3.0);
+    if (c <= 64) {
+        k_chol<<<1, 1024, 0, s>>>(G, c, coef, R, flag);
+        CM_LAUNCH();
+        return CMSVD_OK;
+    }
+    static int per_sm = -1;
+    if (per_sm < 0) CM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_coop, 256, 0));
+    int grid = ctx->sm_count < 128 ? ctx->sm_count : 128;
+    if (per_sm * ctx->sm_count < grid) grid = per_sm * ctx->sm_count;
+    if (grid < 1) { set_error("Cholesky grid cannot be co-resident"); return CMSVD_NOT_SUPPORTED; }
+    void* args[] = {(void*)&G, (void*)&c, (void*)&coef, (void*)&R, (void*)&flag, (void*)&ctl};
+    CM_CUDA(cudaLaunchCooperativeKernel((const void*)k_chol_coop, dim3(grid), dim3(256), args, 0, s));
+    note_launch();
+    return CMSVD_OK;
+}
 
 // R (cc x cc) with R^T R = G + shift I. base = 0: plain Cholesky first. A failed
 // attempt (non-positive pivot) is repeated with a 100x larger shift, starting from
@@ -840,13 +860,11 @@ int chol_adaptive(OrthCtx& o, int cc, bool shifted, double* R) {
     double coef = shifted ? 10.0 * (cc + sqrt((double)o.n)) * u : 0.0;
     for (int attempt = 0; attempt < 12; ++attempt) {
         CM_CUDA(cudaMemsetAsync(o.flag, 0, sizeof(int), o.s));
-        {
-            ProfScope ps(CMSVD_PROF_SMALL, o.s, 16.0 * cc * cc, cc * (double)cc * cc / 3.0);
-            k_chol<<<1, 1024, 0, o.s>>>(o.G, cc, coef, R, o.flag);
-            CM_LAUNCH();
-        }
-        CM_CUDA(cudaMemcpyAsync(o.ctx->pinned, o.flag, sizeof(int), cudaMemcpyDeviceToHost, o.s));
+        CM_TRY(chol_launch(o.ctx, o.s, o.G, cc, coef, R, o.flag, o.ctl));
+        CM_CUDA(cudaMemcpyAsync(o.ctx->pinned, o.flag, 4 * sizeof(int), cudaMemcpyDeviceToHost, o.s));
+        CM_CUDA(cudaMemcpyAsync(o.ctx->pinned + 4, o.ctl, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, o.s));
         CM_CUDA(cudaStreamSynchronize(o.s));
+        if (o.ctx->pinned[4 + 3]) { set_error("Cholesky grid barrier timed out"); return CMSVD_CUDA_ERROR; }
         if (o.ctx->pinned[0] == 0) return CMSVD_OK;
         coef = coef > 0.0 ? coef * 100.0 : 10.0 * (cc + sqrt((double)o.n)) * u;
     }
@@ -879,7 +897,7 @@ int cholqr_pass(OrthCtx& o, const double* Xin, int64_t ldi, int cc, bool shifted
 //   eigen-decomposed and the directions left at rounding level are deflated; two
 //   plain passes restore orthogonality to working precision.
 int orth_qr(const double* X, int64_t ldx, int64_t n, int c, double* Q, double* R, int* c_out, double* scratch, int* ints,
-            int deflate, cmsvd_context* ctx, double* Rcorr) {
+            int deflate, cmsvd_context* ctx, double* Rcorr, bool r_from_gram) {
     cudaStream_t s = ctx->s;
     double* T = scratch;
     double* G = T + (size_t)n * c;
@@ -889,35 +907,36 @@ int orth_qr(const double* X, int64_t ldx, int64_t n, int c, double* Q, double* R
     double* R4 = R3 + (size_t)c * c;
     double* R5 = R4 + (size_t)c * c;
     double* Ri = R5 + (size_t)c * c;
-    double* Rb = Ri + (size_t)c * c;
-    double* Xj = Rb + (size_t)c * c;
-    double* Vj = Xj + (size_t)c * c;
-    double* T3 = Vj + (size_t)c * c;
+    double* Wp = Ri + (size_t)c * c;     // pivoted-Cholesky scratch (c x c each)
+    double* Lp = Wp + (size_t)c * c;
+    double* T3 = Lp + (size_t)c * c;
     double* M1 = T3 + (size_t)c * c;
     double* M2 = M1 + (size_t)c * c;
-    double* sv = M2 + (size_t)c * c;
-    int* perm = (int*)(sv + c);
-    double* part = sv + 2 * (size_t)c;
-    unsigned* jctl = (unsigned*)(part + gram_partials_cap(c, ctx->sm_count));   // inside the 256-double tail
-    OrthCtx o{ctx, s, G, Ri, part, gram_partials_cap(c, ctx->sm_count), ints, n};
+    double* part = M2 + (size_t)c * c;
+    OrthCtx o{ctx, s, G, Ri, part, gram_partials_cap(c, ctx->sm_count), ints, n, (unsigned*)(ints + 4)};
     int* cp_dev = ints + 1;
-    int* flag2 = ints + 4;             // 16 bytes: ints[4..7]
     double* ratio = (double*)(ints + 2);
     if (!deflate) {
         // CholeskyQR2 attempt
         CM_TRY(gram(X, ldx, c, X, ldx, c, n, G, part, o.pcap, ctx->sm_count, s));
         CM_CUDA(cudaMemsetAsync(o.flag, 0, sizeof(int), s));
+        CM_TRY(chol_launch(ctx, s, G, c, 0.0, R1, o.flag, o.ctl));
         {
-            ProfScope ps(CMSVD_PROF_SMALL, s, 16.0 * c * c, c * (double)c * c / 3.0, 2);
-            k_chol<<<1, 1024, 0, s>>>(G, c, 0.0, R1, o.flag);
-            CM_LAUNCH();
+            ProfScope ps(CMSVD_PROF_SMALL, s, 8.0 * c, 0.0);
             k_diag_ratio<<<1, 32, 0, s>>>(R1, c, ratio);
             CM_LAUNCH();
         }
-        CM_CUDA(cudaMemcpyAsync(ctx->pinned, ints, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+        CM_CUDA(cudaMemcpyAsync(ctx->pinned, ints, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
         CM_CUDA(cudaStreamSynchronize(s));
+        if (ctx->pinned[4 + 3]) { set_error("Cholesky grid barrier timed out"); return CMSVD_CUDA_ERROR; }
         double rat;
         memcpy(&rat, ctx->pinned + 2, sizeof(double));
+        if (ctx->pinned[0] == 0 && r_from_gram && !Rcorr) {
+            // the caller bounded the Gram's rounding error below its accuracy target: R = R1
+            CM_CUDA(cudaMemcpyAsync(R, R1, sizeof(double) * (size_t)c * c, cudaMemcpyDeviceToDevice, s));
+            *c_out = c;
+            return CMSVD_OK;
+        }
         if (ctx->pinned[0] == 0 && rat > 1e-5) {
             // Q1 = X R1^{-1}; its Gram gives R2; Q = Q1 R2^{-1} is left implicit
             double* Q1 = Rcorr ? Q : T;
@@ -937,14 +956,13 @@ int orth_qr(const double* X, int64_t ldx, int64_t n, int c, double* Q, double* R
     // two shifted passes: X -> Q (R1), Q -> T (R2)
     CM_TRY(cholqr_pass(o, X, ldx, c, true, R1, Q));
     CM_TRY(cholqr_pass(o, Q, c, c, true, R2, T));
-    // deflation
+    // deflation: the directions of T left at rounding level (Gram pivots <= 1e-10 of the
+    // largest) are separated from the O(1) ones by a pivoted Cholesky of its Gram
     CM_TRY(gram(T, c, c, T, c, c, n, G, part, o.pcap, ctx->sm_count, s));
-    CM_TRY(chol_adaptive(o, c, true, Rb));
-    // the deflation only separates rounding-level directions (lambda < 1e-10) from O(1) ones
-    CM_TRY(jacobi_svd(Rb, c, c, 1, Xj, Vj, sv, perm, flag2, ctx, 1e-7, jctl));
+    if (c > 512) { set_error("orthogonalization supports at most 512 columns"); return CMSVD_NOT_SUPPORTED; }
     {
-        ProfScope ps(CMSVD_PROF_SMALL, s, 24.0 * c * c, 0.0);
-        k_deflate<<<1, 256, 0, s>>>(Xj, sv, perm, c, 1e-10, T3, R3, cp_dev);
+        ProfScope ps(CMSVD_PROF_SMALL, s, 40.0 * c * c, c * (double)c * c / 3.0);
+        k_pchol_deflate<<<1, 1024, 0, s>>>(G, c, 1e-10, Wp, Lp, T3, R3, cp_dev);
         CM_LAUNCH();
     }
     CM_CUDA(cudaMemcpyAsync(ctx->pinned, cp_dev, sizeof(int), cudaMemcpyDeviceToHost, s));

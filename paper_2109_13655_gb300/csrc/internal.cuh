@@ -109,6 +109,7 @@ struct cmsvd_result {
     double* res_u = nullptr;
     double* res_v = nullptr;
     double* tau = nullptr;
+    double* res_est = nullptr; // null unless the solve ran with estimate = 1
     cmsvd_stats stats{};
 };
 
@@ -165,6 +166,9 @@ int direct_moments(cmsvd_matrix* A, const cmsvd_params* p, const double2* quad, 
                    const double* X, int64_t ldx, double* S, int64_t lds, Arena& ws);
 int norm_estimate(cmsvd_matrix* A, Arena& ws, double* norm_out);
 
+// Persistent outputs of one solve (capacity L M each; U m x c, V n x c).
+struct RitzOut { double *sigma, *U, *V, *res_u, *res_v, *tau, *res_est; };
+
 // ----------------------------------------------------------------------------- dense (dense.cu)
 // G (c1 x c2, row-major) = X^T Y, X: n x c1 (ldx), Y: n x c2 (ldy). Deterministic.
 int gram(const double* X, int64_t ldx, int c1, const double* Y, int64_t ldy, int c2, int64_t n,
@@ -179,10 +183,12 @@ int gemm_nn(const double* X, int64_t ldx, const double* W, int64_t ldw, double* 
 // X is too ill-conditioned for it. ints: 8 device ints of scratch (8-byte aligned).
 // The orthonormal factor is returned implicitly: on exit Q holds Q' (n x c') and, when
 // Rcorr is not null, Rcorr holds the upper-triangular c' x c' matrix C with Q = Q' C.
-// With Rcorr null only R is wanted (Q is then scratch of n x c doubles).
+// With Rcorr null only R is wanted (Q is then scratch of n x c doubles). r_from_gram (only
+// with Rcorr null and deflate 0): when the plain Cholesky of X^T X succeeds, return its
+// factor as R; the caller has checked that the Gram's rounding error is small enough.
 size_t orth_scratch(int c, int64_t n, int sm_count);
 int orth_qr(const double* X, int64_t ldx, int64_t n, int c, double* Q, double* R, int* c_out, double* scratch, int* ints,
-            int deflate, cmsvd_context* ctx, double* Rcorr);
+            int deflate, cmsvd_context* ctx, double* Rcorr, bool r_from_gram = false);
 // One-sided Jacobi SVD of Bm (brows x bcols, row-major). trans = 0 rotates the columns of
 // Bm: Bm V = Xc (column-major brows x bcols), V bcols x bcols. trans = 1 rotates the
 // columns of Bm^T: Bm^T V = Xc (column-major bcols x brows), V brows x brows holds the

@@ -204,3 +204,63 @@ def window_interval(sig_desc: np.ndarray, first: int, count: int,
             a = 0.5 * (s[f + count - 1] + s[f + count])
             return float(a), float(b), f
     raise ValueError("no window with the requested gaps")
+
+
+def digits_like(m: int = 60000, side: int = 28, classes: int = 10, nnz_row: float = 150.0, seed: int = 8) -> CSR:
+    """A stand-in with the shape of the Experiment III matrix (Sec. 4.3: 60000 x 784 images of
+    handwritten digits, 149.9 nonzeros per row on average, nonnegative, scaled to ||A||_2 = 1).
+
+    Columns are the pixels of a side x side grid. Each class has a prototype of six Gaussian
+    strokes in the central 16 x 16 pixels. A row is one "drawing" of its class: every stroke
+    is moved by N(0, 1.5^2) pixels, its widths are scaled by exp(N(0, 0.15^2)) and its
+    amplitude drawn from U(0.6, 1). The row keeps its K brightest pixels, with
+    K = round(nnz_row exp(N(0, 0.2^2))) clipped to [60, 300]. The values are the intensities
+    relative to the row's maximum, quantized to k/255 with k >= 1. Smooth deformations of a
+    few prototypes give a spectrum that decays like that of real digit images. The matrix is
+    divided by its largest singular value. That value is found by 40 steps of power iteration
+    on A^T A; the matrix is nonnegative, so the top value is simple and well separated.
+    """
+    rng = np.random.default_rng(seed)
+    n = side * side
+    yy, xx = np.mgrid[0:side, 0:side].astype(np.float64)
+    yy, xx = yy.ravel(), xx.ravel()
+    ctr = (side - 1) / 2.0
+    ns = 6
+    proto = np.empty((classes, ns, 4))                      # cy, cx, sy, sx
+    proto[:, :, 0:2] = rng.uniform(ctr - 8.0, ctr + 8.0, size=(classes, ns, 2))
+    proto[:, :, 2:4] = rng.uniform(1.2, 3.5, size=(classes, ns, 2))
+    labels = rng.integers(0, classes, size=m)
+    K = np.clip(np.rint(nnz_row * np.exp(0.2 * rng.standard_normal(m))), 60, 300).astype(np.int64)
+    rows_l, cols_l, vals_l = [], [], []
+    chunk = 4096
+    for r0 in range(0, m, chunk):
+        r1 = min(m, r0 + chunk)
+        st = proto[labels[r0:r1]].copy()                      # (c, ns, 4)
+        st[:, :, 0:2] += 1.5 * rng.standard_normal((r1 - r0, ns, 2))
+        st[:, :, 2:4] *= np.exp(0.15 * rng.standard_normal((r1 - r0, ns, 2)))
+        amp = rng.uniform(0.6, 1.0, size=(r1 - r0, ns))
+        img = np.zeros((r1 - r0, n))
+        for k in range(ns):
+            dy = (yy[None, :] - st[:, k, 0:1]) / st[:, k, 2:3]
+            dx = (xx[None, :] - st[:, k, 1:2]) / st[:, k, 3:4]
+            img += amp[:, k:k + 1] * np.exp(-0.5 * (dy * dy + dx * dx))
+        srt = -np.sort(-img, axis=1)
+        thr = srt[np.arange(r1 - r0), K[r0:r1] - 1]
+        keep = img >= thr[:, None]
+        q = np.maximum(1.0, np.rint(255.0 * img / srt[:, :1])) / 255.0
+        rr, cc = np.nonzero(keep)
+        rows_l.append(rr + r0)
+        cols_l.append(cc)
+        vals_l.append(q[rr, cc])
+    A = csr_from_coo(m, n, np.concatenate(rows_l), np.concatenate(cols_l), np.concatenate(vals_l))
+    # ||A||_2 by power iteration on A^T A (sparse products written out with numpy)
+    rr = np.repeat(np.arange(m), np.diff(A.rowptr))
+    x = np.ones(n) / np.sqrt(n)
+    lam = 0.0
+    for _ in range(40):
+        y = np.bincount(rr, weights=A.vals * x[A.colidx], minlength=m)
+        z = np.bincount(A.colidx, weights=A.vals * y[rr], minlength=n)
+        lam = float(np.linalg.norm(z))
+        x = z / lam
+    A.vals = A.vals / np.sqrt(lam)
+    return A

@@ -7,7 +7,9 @@
 * the contour-integral limit of Thm. 1 (spectral projector) for both variants,
 * the Exp I filter statements (tests/golden/exp1_filter.txt),
 * triplets against numpy's dense SVD, and the Exp II model problems (Sec. 4.2),
-* the spurious index tau on the 2000 x 1000 workload (Sec. 3.4.2).
+* the spurious index tau on the 2000 x 1000 workload (Sec. 3.4.2),
+* the residual estimate through S_+ (Sec. 3.4.1): equal to the exact residual for the
+  linear variant, equal to the ln(A^T A) form for NT, and mu fixed by one exact residual.
 
 The mutation tests at the end plant plausible mistakes in the oracle and
 check that at least one of these pins fails.
@@ -283,6 +285,67 @@ def test_c1_tau_detects_spurious():
     assert np.all(r.all_tau[inside & ~spurious] > 1e-3)
 
 
+def estimate_errors(variant):
+    """Residual estimate through S_+ (Sec. 3.4.1) on Exp II model 1 with a deliberately small
+    subspace (L = 4, M = 2 for 40 wanted values), so that the residuals are O(0.1) and far
+    above rounding. Linear: the estimate must equal the exact residual (Prop. 1 makes
+    A^T A S_k = rho S_{k+1} + gamma S_k exact with scaled nodes). NT: r~ must equal
+    || ln(A^T A) v - ln(sigma^2) v || / sigma computed from a dense eigendecomposition."""
+    A, sig = synth.model_problem(1)
+    Vin = synth.gaussian_block(200, 4, 3)
+    r = O.solve_interval(A, 0.8, 1.2, 32, 4, 2, Vin, variant=variant, norm_A=sig.max(), with_estimate=True,
+                         tol_triplet=1.0)
+    assert r.sigma.size >= 4 and r.res_u.min() > 1e-3
+    if variant == "linear":
+        return np.max(np.abs(r.res_est - r.res_u) / r.res_u), r
+    lam, W = np.linalg.eigh(A.T @ A)
+    lnH = (W * np.log(lam)) @ W.T
+    direct = np.linalg.norm(lnH @ r.V - r.V * np.log(r.sigma ** 2), axis=0) / r.sigma / sig.max()
+    return np.max(np.abs(r.res_tilde - direct) / direct), r
+
+
+def test_residual_estimate_linear_equals_exact():
+    err, r = estimate_errors("linear")
+    assert err < 1e-10
+    # and at rounding-level residuals (the full Exp II setting) the two agree to 1e-15
+    A, sig = synth.model_problem(1)
+    rr = O.solve_interval(A, 0.8, 1.2, 32, 20, 4, synth.gaussian_block(200, 20, 3), norm_A=sig.max(),
+                          with_estimate=True)
+    assert rr.sigma.size == 40 and np.max(np.abs(rr.res_est - rr.res_u)) < 1e-14
+
+
+def test_residual_estimate_nt_log_form_and_mu():
+    err, r = estimate_errors("nt")
+    assert err < 1e-10
+    # mu is fixed by one exact residual (Eq. res_nonlinear): there the estimate is exact
+    ratio = r.res_est / r.res_u
+    assert np.min(np.abs(ratio - 1.0)) < 1e-12
+    # i' is the candidate with the largest r~: every other estimate scales r~ by the same mu
+    mu = r.res_est / r.res_tilde
+    assert np.max(np.abs(mu - mu[0])) <= 1e-12 * mu[0]
+
+
+def test_exp3_digits_standin():
+    """Sec. 4.3 shape (60000 x 784, ~150 nonzeros per row, ||A||_2 = 1): the exterior
+    interval holding the 21 largest values and the interior window of 17 values starting at
+    the 41st are found exactly by the NT variant, with L = 15, M = 4, N = 32 (Table 1's first
+    row), against numpy's dense SVD. The linear variant misses the exterior values."""
+    A = synth.digits_like()
+    s = np.linalg.svd(A.to_dense(), compute_uv=False)
+    assert abs(s[0] - 1.0) < 1e-12
+    Vin = synth.gaussian_block(A.n, 15, 5)
+    a, b = 0.5 * (s[20] + s[21]), 1.01 * s[0]
+    r = O.solve_interval(A, a, b, 32, 15, 4, Vin, variant="nt", norm_A=s[0])
+    assert r.sigma.size == 21
+    assert np.max(np.abs(r.sigma - s[:21][::-1]) / s[:21][::-1]) < 1e-13
+    rl = O.solve_interval(A, a, b, 32, 15, 4, Vin, variant="linear", norm_A=s[0])
+    assert rl.sigma.size < 21
+    a, b, _ = synth.window_interval(s, 40, 17)
+    r = O.solve_interval(A, a, b, 32, 15, 4, Vin, variant="nt", norm_A=s[0])
+    assert r.sigma.size == 17
+    assert np.max(np.abs(r.sigma - s[40:57][::-1]) / s[40:57][::-1]) < 1e-13
+
+
 # ----------------------------------------------------------------------------- mutations
 def _mutant_quadrature(kind):
     orig = O.quadrature
@@ -330,3 +393,17 @@ def test_mutation_moment_index_caught(monkeypatch):
     """Using the literal node instead of the scaled one in one factor breaks Prop. 1 (scaled form)."""
     monkeypatch.setattr(O, "moment_factor", lambda q, k, scaled=True: q.node ** k)
     assert prop1_error(scaled=True) > 1e-3
+
+
+def test_mutation_estimate_dropped_gamma_caught(monkeypatch):
+    """f(A^T A) v written as rho S_+ Z alone (the gamma v term dropped)."""
+    monkeypatch.setattr(O, "shifted_moment_operator", lambda q, Splus, Z, V: q.rho * (Splus @ Z))
+    assert estimate_errors("linear")[0] > 1e-3
+    assert estimate_errors("nt")[0] > 1e-3
+
+
+def test_mutation_estimate_log_of_sigma_caught(monkeypatch):
+    """g^{-1} applied to sigma instead of sigma^2 in the NT form."""
+    orig = O.spectral_map
+    monkeypatch.setattr(O, "spectral_map", lambda v, x: orig(v, x) if v == "linear" else np.log(np.sqrt(x)))
+    assert estimate_errors("nt")[0] > 1e-3
