@@ -46,7 +46,7 @@ def workload(name: str):
         s = bp.sigmas_desc()
         a, b, f = synth.window_interval(s, 50000, 200, min_rel_gap=1e-6, max_shift=10)
         cfg = dict(N=32, L=32, M=8, ell=2)
-        return dict(A=bp.A, a=a, b=b, t=200, norm_A=float(s[0]), cfg=cfg, seed=3,
+        return dict(name=name, A=bp.A, a=a, b=b, t=200, norm_A=float(s[0]), cfg=cfg, seed=3,
                     desc="200000x100000 CSR, 25000 permuted 8x4 N(0,1) blocks (nnz 800000), "
                          "200 interior sigma, N=32 L=32 M=8 ell=2")
     if name == "random_sparse_2000x1000":
@@ -54,7 +54,7 @@ def workload(name: str):
         s = np.linalg.svd(A.to_dense(), compute_uv=False)
         a, b, _ = synth.window_interval(s, 400, 20)
         cfg = dict(N=16, L=16, M=4, ell=1)
-        return dict(A=A, a=a, b=b, t=20, norm_A=float(s[0]), cfg=cfg, seed=1,
+        return dict(name=name, A=A, a=a, b=b, t=20, norm_A=float(s[0]), cfg=cfg, seed=1,
                     desc="2000x1000 CSR, 8 nnz/row N(0,1), sigma ranked 400-419, N=16 L=16 M=4")
     raise ValueError(name)
 
@@ -242,6 +242,8 @@ def run_ours(args, w, rank, world, local_rank):
     tmax, e2e_max = max_over_ranks([total_s, sum(e2e_ms) / len(e2e_ms)], dist, dev)
     krylov = measure_krylov(B, ctx, dev) if (rank == 0 and args.krylov) else None
     table2 = measure_table2(B, dev) if (rank == 0 and args.table2) else None
+    batched = measure_batched(B, dev) if (rank == 0 and args.batched) else None
+    serving = measure_serving(B) if (rank == 0 and args.serving) else None
     if rank == 0:
         value = job_throughput(args.steps, world, tmax)
         prof = aggregate_profile(stats)
@@ -271,6 +273,10 @@ def run_ours(args, w, rank, world, local_rank):
         }
         if table2 is not None:
             line["exp3_table2"] = table2
+        if batched is not None:
+            line["batched_workload"] = batched
+        if serving is not None:
+            line["serving_workload"] = serving
         if args.cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w)
         print(json.dumps(line), flush=True)
@@ -328,6 +334,141 @@ def measure_krylov(B, ctx, dev, steps=3):
         del ws
     M.close()
     return out
+
+
+def measure_batched(B, dev, contexts=8, reps=2):
+    """64 independent block-permuted problems (10 x 4 blocks, n log-uniform in [2000, 80000],
+    m = 2.5 n, N and L in {16, 32}, M = 4, half exterior, half interior, t = floor(L M / 3)):
+    one after another from one host thread, against one cmsvd_solve_batch call over
+    `contexts` streams. Device-resident inputs; every solve must return its t triplets with
+    residuals <= 1e-10."""
+    import torch
+    probs = synth.batched_problems(64, seed=4)
+    ctxs = [B.Context(torch.cuda.Stream()) for _ in range(contexts)]
+    mats = [B.Matrix.from_csr(ctxs[i % contexts], p["A"]) for i, p in enumerate(probs)]
+    prms = [B.params(N=p["N"], L=p["L"], M=p["M"], norm_A=float(p["sigma"][0])) for p in probs]
+    Vs = [torch.from_numpy(synth.gaussian_block(p["A"].n, p["L"], p["seed_v"])).to(dev) for p in probs]
+    wss = [M.workspace(q) for M, q in zip(mats, prms)]
+    handles = [M.handle for M in mats]
+    torch.cuda.synchronize()
+
+    def check(rs):
+        ok = True
+        for r, p in zip(rs, probs):
+            st = B.cmsvd_result_stats(r)
+            ok &= B.cmsvd_result_count(r) == p["t"] and st["max_res_u"] <= 1e-10 and st["max_res_v"] <= 1e-10
+            B.cmsvd_result_destroy(r)
+        return bool(ok)
+
+    def sequential():
+        rs = []
+        for i in range(len(probs)):
+            _, r = B.cmsvd_solve_interval(handles[i], probs[i]["a"], probs[i]["b"], prms[i], Vs[i], wss[i])
+            rs.append(r)
+        torch.cuda.synchronize()
+        return rs
+
+    def batched():
+        _, rs = B.cmsvd_solve_batch(handles, [p["a"] for p in probs], [p["b"] for p in probs], prms, Vs, wss)
+        torch.cuda.synchronize()
+        return rs
+
+    out = {}
+    for name, fn in (("sequential", sequential), ("batched", batched)):
+        valid = check(fn())                       # warm-up pass
+        times = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            rs = fn()
+            times.append(time.perf_counter() - t0)
+            valid &= check(rs)
+        best = min(times)
+        out[name] = {"solves_per_s": len(probs) / best, "s_per_batch": best, "all_valid": valid}
+    for M in mats:
+        M.close()
+    for c in ctxs:
+        c.close()
+    out["speedup"] = out["batched"]["solves_per_s"] / out["sequential"]["solves_per_s"]
+    out["description"] = (f"64 block-permuted problems (10x4 N(0,1) blocks, n in [2000, 80000] log-uniform, "
+                          f"sum n = {sum(p['A'].n for p in probs)}), N,L in {{16,32}}, M=4, half exterior/half "
+                          f"interior, t = floor(LM/3); batched = one cmsvd_solve_batch call over {contexts} "
+                          f"contexts (streams, one host thread each); wall clock, inputs resident")
+    return out
+
+
+def measure_serving(B, slots=8, rate=200.0, count=300, seed=5):
+    """Serving with continuous batching (cmsvd_server_*): 16 resident matrices with rows
+    log-uniform in [1e4, 2e5] and c in {8, 16, 32} nonzeros per row, realized as permuted
+    2c x c blocks of U(-1,1) values rounded to bf16 (m = 2n; known spectra). Requests pick a
+    matrix uniformly and a window of t in [10, 40] singular values at a uniform position;
+    N = 32, L = 32, M = 4. First the capacity: 96 requests submitted at once. Then a Poisson
+    stream of `count` requests at min(rate, 0.7 x capacity) per second. Latency is measured
+    from submit to result ready (host V_in in, host triplets out)."""
+    import threading
+    rng = np.random.default_rng(seed)
+    mats = []
+    for k in range(16):
+        rows = int(np.exp(rng.uniform(np.log(1e4), np.log(2e5))))
+        c = int(rng.choice([8, 16, 32]))
+        nb = max(1, rows // (2 * c))
+        mats.append(synth.block_permuted(nb, 2 * c, c, seed=int(rng.integers(1 << 30)), dist="uniform_bf16"))
+    spectra = [bp.sigmas_desc() for bp in mats]
+
+    def make(i):
+        mi = int(rng.integers(0, 16))
+        s = spectra[mi]
+        t = int(rng.integers(10, 41))
+        first = int(rng.integers(t + 5, s.size - 2 * t - 5))
+        a, b, _ = synth.window_interval(s, first, t, min_rel_gap=1e-6, max_shift=10)
+        truth = int(((s >= a) & (s <= b)).sum())
+        return (mi, a, b, truth, synth.gaussian_block(mats[mi].A.n, 32, 7000 + i))
+
+    srv = B.Server(slots=slots)
+    ids = [srv.add_matrix(bp.A) for bp in mats]
+    p = B.params(N=32, L=32, M=4)
+
+    def run(reqs, gaps):
+        tickets = [None] * len(reqs)
+        t0 = time.perf_counter()
+
+        def feeder():
+            nxt = t0
+            for i, (mi, a, b, truth, V) in enumerate(reqs):
+                nxt += gaps[i]
+                d = nxt - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                tickets[i] = srv.submit(ids[mi], a, b, p, V)
+
+        th = threading.Thread(target=feeder)
+        th.start()
+        lat, que, valid = [], [], True
+        for i in range(len(reqs)):
+            while tickets[i] is None:
+                time.sleep(0.0002)
+            done, nt, st, l_ms, q_ms = srv.wait(tickets[i])
+            stats = srv.take(tickets[i], ids[reqs[i][0]], nt, st).stats
+            valid &= (nt == reqs[i][3] and stats["max_res_u"] <= 1e-10 and stats["max_res_v"] <= 1e-10)
+            lat.append(l_ms)
+            que.append(q_ms)
+        t_end = time.perf_counter()
+        th.join()
+        return len(reqs) / (t_end - t0), lat, que, bool(valid)
+
+    run([make(i) for i in range(16)], np.zeros(16))                      # warm-up
+    cap, _, _, valid_cap = run([make(i) for i in range(96)], np.zeros(96))
+    lam = min(rate, 0.7 * cap)
+    reqs = [make(i) for i in range(count)]
+    thr, lat, que, valid = run(reqs, rng.exponential(1.0 / lam, size=count))
+    srv.close()
+    pct = lambda x, q: float(np.percentile(x, q))
+    return {"description": f"16 resident block-permuted matrices (rows 1e4-2e5 log-uniform, 8/16/32 nnz per row, "
+                           f"sum rows {sum(bp.A.m for bp in mats)}), windows of t in [10, 40], N=32 L=32 M=4, "
+                           f"{slots} slots, HBM budget 80% of free; latency = submit to host result",
+            "capacity_solves_per_s": cap, "capacity_all_valid": valid_cap,
+            "poisson_rate_per_s": lam, "requests": count, "solves_per_s": thr,
+            "latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99), "max": float(np.max(lat))},
+            "queue_ms": {"p50": pct(que, 50), "p99": pct(que, 99)}, "all_valid": valid}
 
 
 def measure_table2(B, dev):
@@ -390,6 +531,12 @@ def aggregate_profile(stats):
     return out
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, mean over the launches
+# of one solve of the 200000 x 100000 workload, one ncu capture) for the kernels whose code
+# has not changed since; None elsewhere.
+MEASURED_TRAFFIC = {("block_permuted_200000x100000", "gemm"): 154.6e6}
+
+
 def roofline(dom, prof, stats, w):
     """Roofline of the dominant kernel class: algorithmic bytes or FP64 flops per launch
     (counted by the library for every launch) over its event-timed duration."""
@@ -406,7 +553,8 @@ def roofline(dom, prof, stats, w):
     if ai > fp64_peak * 1e12 / (hbm * 1e9):
         ach = d["flops"] / sec / 1e12
         return {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": ach / fp64_peak, "traffic": None,
+                "frac": ach / fp64_peak, "traffic": MEASURED_TRAFFIC.get((w.get("name"), dom)),
+                "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
                 "peak_source": "FP64 FMA pipe: 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz (derived; probe measured 1.20)",
                 "flops_per_launch": d["flops"] / d["launches"], "ms_per_launch": d["ms"] / d["launches"]}
     ach = d["bytes"] / sec / 1e9
@@ -425,6 +573,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-krylov", dest="krylov", action="store_false",
                     help="skip the secondary FP64-vs-mixed measurement of the Krylov workload")
+    ap.add_argument("--no-batched", dest="batched", action="store_false",
+                    help="skip the secondary 64-problem batched measurement")
+    ap.add_argument("--no-serving", dest="serving", action="store_false",
+                    help="skip the secondary Poisson-arrival serving measurement")
     ap.add_argument("--table2", action="store_true",
                     help="also run the eight Exp III intervals on the digit-image stand-in (minutes)")
     args = ap.parse_args()

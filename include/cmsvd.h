@@ -40,7 +40,8 @@ typedef enum cmsvd_status {
     CMSVD_BREAKDOWN = 6,            /* NaN/Inf in a recurrence or a non-positive Cholesky pivot */
     CMSVD_SUBSPACE_SATURATED = 7,   /* warning: numerical rank of S^ equals L*M (Thm. 1: t may exceed L*M) */
     CMSVD_CUDA_ERROR = 8,           /* a CUDA runtime call failed */
-    CMSVD_NOT_SUPPORTED = 9         /* valid request outside what this build implements */
+    CMSVD_NOT_SUPPORTED = 9,        /* valid request outside what this build implements */
+    CMSVD_PENDING = 10              /* serving: the request has not finished yet */
 } cmsvd_status;
 
 typedef enum cmsvd_variant {
@@ -264,6 +265,58 @@ int cmsvd_solve_interval(cmsvd_matrix* A, double a, double b, const cmsvd_params
  * CMSVD_NOT_SUPPORTED when the solve ran with estimate = 0.
  */
 int cmsvd_result_copy_estimate(const cmsvd_result* r, double* res_est);
+
+/*
+ * Batched solves (no counterpart in the paper, which solves one problem at a time):
+ * count independent problems, problem i being cmsvd_solve_interval(A[i], a[i], b[i], &p[i],
+ * V_in[i], workspace[i], ws_bytes[i], &out[i]). Problems whose matrices share a context run
+ * one after another, in index order, on that context's stream. Problems on different
+ * contexts run concurrently, one host thread per context. To overlap many small problems,
+ * create several contexts and spread the matrices over them. Each problem needs its own
+ * workspace, because its result lives there until cmsvd_result_destroy. Results are
+ * identical to solving each problem alone.
+ * status[i] receives each problem's status and out[i] its result (NULL when it failed).
+ * Returns CMSVD_OK when every status is OK, NOT_CONVERGED or SUBSPACE_SATURATED. Otherwise
+ * it returns the first failing status, and cmsvd_last_error names the problem.
+ */
+int cmsvd_solve_batch(int count, cmsvd_matrix* const* A, const double* a, const double* b,
+                      const cmsvd_params* p, const double* const* V_in, void* const* workspace,
+                      const size_t* ws_bytes, cmsvd_result** out, int* status);
+
+/*
+ * Serving loop with continuous batching. The paper has no counterpart; it solves one
+ * problem at a time. A server owns `slots` contexts, each with its own stream and host
+ * worker thread, and a set of resident matrices.
+ * - Requests are interval-SVD solves on a resident matrix with host V_in. They queue in
+ *   arrival order.
+ * - The head request is admitted as soon as a slot is free and its workspace fits in the
+ *   HBM budget left after the resident matrices and the running requests. Admitted
+ *   requests run concurrently.
+ * - Each result is copied to host memory when its solve completes. It is identical to
+ *   solving the request alone with cmsvd_solve_interval.
+ * hbm_budget = 0 takes 80% of the free device memory at creation.
+ * Latency is measured from submit to result ready, and queueing from submit to admission.
+ */
+typedef struct cmsvd_server cmsvd_server;
+int cmsvd_server_create(int slots, size_t hbm_budget, cmsvd_server** out);
+int cmsvd_server_destroy(cmsvd_server* s);   /* stops the workers; requests not started are dropped */
+/* Uploads, validates and registers a matrix (as cmsvd_csr_create); *id names it in requests. */
+int cmsvd_server_add_matrix(cmsvd_server* s, int64_t m, int64_t n, int64_t nnz, const int64_t* rowptr,
+                            const int32_t* colidx, const double* vals, int vals_on_device, int* id);
+/* Queues a request; V_in (n x L, row-major, host memory) is copied. Returns at once with a
+ * ticket. CMSVD_OUT_OF_MEMORY when its workspace can never fit in the budget. */
+int cmsvd_server_submit(cmsvd_server* s, int id, double a, double b, const cmsvd_params* p,
+                        const double* V_in_host, int64_t* ticket);
+/* Waits up to timeout_ms (< 0: forever) for a request. CMSVD_PENDING if it has not finished;
+ * otherwise CMSVD_OK, with t = triplets found, solve_status = the solve's own status, and the
+ * latency and queueing times in ms (any output pointer may be NULL). */
+int cmsvd_server_wait(cmsvd_server* s, int64_t ticket, int timeout_ms, int64_t* t, int* solve_status,
+                      double* latency_ms, double* queue_ms);
+/* Copies a finished request's triplets to host buffers that hold `capacity` triplets
+ * (layouts of cmsvd_result_copy; any pointer may be NULL) and forgets the request.
+ * CMSVD_INVALID_ARG (nothing copied, request kept) when capacity < t. */
+int cmsvd_server_take(cmsvd_server* s, int64_t ticket, int64_t capacity, double* sigma, double* U, double* V,
+                      double* res_u, double* res_v, double* tau, cmsvd_stats* stats);
 
 /* Number of triplets found (t^). */
 int cmsvd_result_count(const cmsvd_result* r, int64_t* t);

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libcmsvd.so")
 
 OK, INVALID_ARG, INVALID_MATRIX, OUT_OF_MEMORY, WORKSPACE_TOO_SMALL, NOT_CONVERGED, BREAKDOWN, \
-    SUBSPACE_SATURATED, CUDA_ERROR, NOT_SUPPORTED = range(10)
+    SUBSPACE_SATURATED, CUDA_ERROR, NOT_SUPPORTED, PENDING = range(11)
 LINEAR, NT = 0, 1
 SOLVER_AUTO, SOLVER_KRYLOV, SOLVER_DIRECT = 0, 1, 2
 FP64, MIXED = 0, 1
@@ -79,6 +79,18 @@ _SIGS = {
     "cmsvd_result_count": (C.c_int, [_P, C.POINTER(_I64)]),
     "cmsvd_result_copy": (C.c_int, [_P, _P, _P, _P, _P, _P, _P]),
     "cmsvd_result_copy_estimate": (C.c_int, [_P, _P]),
+    "cmsvd_server_create": (C.c_int, [C.c_int, C.c_size_t, C.POINTER(_P)]),
+    "cmsvd_server_destroy": (C.c_int, [_P]),
+    "cmsvd_server_add_matrix": (C.c_int, [_P, C.c_int64, C.c_int64, C.c_int64, _P, _P, _P, C.c_int,
+                                          C.POINTER(C.c_int)]),
+    "cmsvd_server_submit": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, C.POINTER(cmsvd_params), _P,
+                                      C.POINTER(C.c_int64)]),
+    "cmsvd_server_wait": (C.c_int, [_P, C.c_int64, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int),
+                                    C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "cmsvd_server_take": (C.c_int, [_P, C.c_int64, C.c_int64, _P, _P, _P, _P, _P, _P, C.POINTER(cmsvd_stats)]),
+    "cmsvd_solve_batch": (C.c_int, [C.c_int, C.POINTER(_P), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                    C.POINTER(cmsvd_params), C.POINTER(_P), C.POINTER(_P), C.POINTER(C.c_size_t),
+                                    C.POINTER(_P), C.POINTER(C.c_int)]),
     "cmsvd_result_stats": (C.c_int, [_P, C.POINTER(cmsvd_stats)]),
     "cmsvd_result_destroy": (C.c_int, [_P]),
 }
@@ -267,6 +279,108 @@ def cmsvd_result_destroy(r: int) -> None:
     _check(lib().cmsvd_result_destroy(_P(r)), "cmsvd_result_destroy")
 
 
+def cmsvd_solve_batch(A: list, a: list, b: list, p: list, V_in: list, workspace: list) -> tuple[list, list]:
+    """Raw batched call. Returns (status per problem, result handle per problem)."""
+    n = len(A)
+    arrP = (_P * n)(*[_P(x) for x in A])
+    arrA = (C.c_double * n)(*a)
+    arrB = (C.c_double * n)(*b)
+    arrp = (cmsvd_params * n)(*p)
+    arrV = (_P * n)(*[_P(_ptr(v)) for v in V_in])
+    arrW = (_P * n)(*[_P(_ptr(w)) for w in workspace])
+    arrS = (C.c_size_t * n)(*[w.numel() * w.element_size() for w in workspace])
+    outs = (_P * n)()
+    st = (C.c_int * n)()
+    s = lib().cmsvd_solve_batch(n, arrP, arrA, arrB, arrp, arrV, arrW, arrS, outs, st)
+    if s not in (OK, NOT_CONVERGED, SUBSPACE_SATURATED):
+        for o in outs:
+            if o:
+                cmsvd_result_destroy(o)
+    _check(s, "cmsvd_solve_batch", allow=(NOT_CONVERGED, SUBSPACE_SATURATED))
+    return list(st), [o or 0 for o in outs]
+
+
+def _triplets_from(r: int, m: int, n: int, status: int, want_estimate: bool) -> "Triplets":
+    try:
+        t = cmsvd_result_count(r)
+        out = [np.zeros(t), np.zeros((t, m)), np.zeros((t, n)), np.zeros(t), np.zeros(t), np.zeros(t)]
+        cmsvd_result_copy(r, *out)
+        est = None
+        if want_estimate:
+            est = np.zeros(t)
+            cmsvd_result_copy_estimate(r, est)
+        st = cmsvd_result_stats(r)
+    finally:
+        cmsvd_result_destroy(r)
+    return Triplets(out[0], out[1].T.copy(), out[2].T.copy(), out[3], out[4], out[5], st, status, est)
+
+
+class Server:
+    """Serving loop with continuous batching (cmsvd_server_*): resident matrices, requests
+    with host V_in, admission by slot and HBM budget, results copied back to the host."""
+
+    def __init__(self, slots: int = 4, hbm_budget: int = 0):
+        h = _P()
+        _check(lib().cmsvd_server_create(slots, hbm_budget, C.byref(h)), "cmsvd_server_create")
+        self.handle = h.value
+        self.shapes = []
+
+    def add_matrix(self, A) -> int:
+        i = C.c_int()
+        rp = np.ascontiguousarray(A.rowptr, dtype=np.int64)
+        ci = np.ascontiguousarray(A.colidx, dtype=np.int32)
+        va = np.ascontiguousarray(A.vals, dtype=np.float64)
+        _check(lib().cmsvd_server_add_matrix(_P(self.handle), A.m, A.n, A.nnz, _P(rp.ctypes.data), _P(ci.ctypes.data),
+                                             _P(va.ctypes.data), 0, C.byref(i)), "cmsvd_server_add_matrix")
+        self.shapes.append((A.m, A.n))
+        return i.value
+
+    def submit(self, mid: int, a: float, b: float, p: cmsvd_params, V_in: np.ndarray) -> int:
+        t = C.c_int64()
+        V = np.ascontiguousarray(V_in, dtype=np.float64)
+        _check(lib().cmsvd_server_submit(_P(self.handle), mid, a, b, C.byref(p), _P(V.ctypes.data), C.byref(t)),
+               "cmsvd_server_submit")
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        """(done, t, solve_status, latency_ms, queue_ms)."""
+        t, st, lat, q = C.c_int64(), C.c_int(), C.c_double(), C.c_double()
+        s = lib().cmsvd_server_wait(_P(self.handle), ticket, timeout_ms, C.byref(t), C.byref(st), C.byref(lat),
+                                    C.byref(q))
+        if s == PENDING:
+            return False, 0, PENDING, 0.0, 0.0
+        _check(s, "cmsvd_server_wait")
+        return True, t.value, st.value, lat.value, q.value
+
+    def take(self, ticket: int, mid: int, t: int, status: int = 0) -> "Triplets":
+        m, n = self.shapes[mid]
+        out = [np.zeros(t), np.zeros((t, m)), np.zeros((t, n)), np.zeros(t), np.zeros(t), np.zeros(t)]
+        st = cmsvd_stats()
+        _check(lib().cmsvd_server_take(_P(self.handle), ticket, t, *[_P(x.ctypes.data) for x in out], C.byref(st)),
+               "cmsvd_server_take")
+        return Triplets(out[0], out[1].T.copy(), out[2].T.copy(), out[3], out[4], out[5], st.as_dict(), status)
+
+    def close(self):
+        if self.handle:
+            lib().cmsvd_server_destroy(_P(self.handle))
+        self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve_batch(problems: list) -> list:
+    """problems: list of (Matrix, a, b, params, V_in device tensor). Spread the matrices over
+    several Contexts for the problems to overlap on the GPU (see cmsvd_solve_batch)."""
+    ws = [M.workspace(p) for (M, a, b, p, V) in problems]
+    st, rs = cmsvd_solve_batch([M.handle for (M, *_r) in problems], [x[1] for x in problems],
+                               [x[2] for x in problems], [x[3] for x in problems], [x[4] for x in problems], ws)
+    return [_triplets_from(r, M.m, M.n, s, bool(p.estimate)) for r, s, (M, a, b, p, V) in zip(rs, st, problems)]
+
+
 # ----------------------------------------------------------------------------- convenience
 @dataclass
 class Triplets:
@@ -354,15 +468,4 @@ class Matrix:
     def solve_interval(self, a, b, p: cmsvd_params, V_in, workspace=None) -> Triplets:
         ws = workspace if workspace is not None else self.workspace(p)
         status, r = cmsvd_solve_interval(self.handle, a, b, p, V_in, ws)
-        try:
-            t = cmsvd_result_count(r)
-            out = [np.zeros(t), np.zeros((t, self.m)), np.zeros((t, self.n)), np.zeros(t), np.zeros(t), np.zeros(t)]
-            cmsvd_result_copy(r, *out)
-            est = None
-            if p.estimate:
-                est = np.zeros(t)
-                cmsvd_result_copy_estimate(r, est)
-            st = cmsvd_result_stats(r)
-        finally:
-            cmsvd_result_destroy(r)
-        return Triplets(out[0], out[1].T.copy(), out[2].T.copy(), out[3], out[4], out[5], st, status, est)
+        return _triplets_from(r, self.m, self.n, status, bool(p.estimate))

@@ -207,6 +207,7 @@ const char* cmsvd_status_string(int status) {
         case CMSVD_SUBSPACE_SATURATED: return "subspace saturated";
         case CMSVD_CUDA_ERROR: return "CUDA error";
         case CMSVD_NOT_SUPPORTED: return "not supported";
+        case CMSVD_PENDING: return "pending";
         default: return "unknown status";
     }
 }

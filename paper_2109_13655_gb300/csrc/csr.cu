@@ -1,6 +1,7 @@
 // CSR storage of A and A^T, validation, and the SpMM Y = A X that every
 // shifted solve (Alg. 1 steps 1-2, as H X = A^T (A X)) and step 4 (A V~) use.
 #include "internal.cuh"
+#include <cub/device/device_radix_sort.cuh>
 #include <cstdarg>
 #include <cstdio>
 
@@ -106,6 +107,37 @@ __global__ void k_validate(const int64_t* __restrict__ rowptr, const int32_t* __
     if (local) atomicOr(bad, local);
 }
 
+__global__ void k_max_row(const int64_t* __restrict__ rowptr, int64_t m, unsigned long long* __restrict__ out) {
+    unsigned long long best = 0;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < m; r += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long len = (unsigned long long)(rowptr[r + 1] - rowptr[r]);
+        best = len > best ? len : best;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long v = __shfl_xor_sync(0xffffffffu, best, o);
+        best = v > best ? v : best;
+    }
+    if ((threadIdx.x & 31) == 0 && best) atomicMax(out, best);
+}
+
+// Longest row of a CSR already on the device (sets A->max_row).
+static int csr_row_stats(cmsvd_context* ctx, Csr* A) {
+    unsigned long long* d = nullptr;
+    CM_CUDA(cudaMalloc(&d, sizeof(unsigned long long)));
+    int st = CMSVD_OK;
+    auto chk = [&](cudaError_t e, const char* w) { if (e != cudaSuccess && st == CMSVD_OK) st = cuda_fail(e, w, __FILE__, __LINE__); };
+    chk(cudaMemsetAsync(d, 0, sizeof(unsigned long long), ctx->s), "memset");
+    k_max_row<<<grid_for(A->m, 256, ctx->sm_count * 8), 256, 0, ctx->s>>>(A->rowptr, A->m, d);
+    chk(cudaGetLastError(), "k_max_row");
+    unsigned long long h = 0;
+    chk(cudaMemcpyAsync(ctx->pinned, d, sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->s), "copy");
+    chk(cudaStreamSynchronize(ctx->s), "sync");
+    memcpy(&h, ctx->pinned, sizeof(h));
+    cudaFree(d);
+    A->max_row = (int64_t)h;
+    return st;
+}
+
 int csr_upload_validate(cmsvd_context* ctx, int64_t m, int64_t n, int64_t nnz, const int64_t* rowptr,
                         const int32_t* colidx, const double* vals, int where, Csr* out) {
     cudaStream_t s = ctx->s;
@@ -144,6 +176,8 @@ int csr_upload_validate(cmsvd_context* ctx, int64_t m, int64_t n, int64_t nnz, c
                   "columns, 8 non-finite value, 16 rowptr ends)", bad);
         return CMSVD_INVALID_MATRIX;
     }
+    st = csr_row_stats(ctx, &A);
+    if (st != CMSVD_OK) { csr_free(&A); return st; }
     *out = A;
     return CMSVD_OK;
 }
@@ -203,68 +237,94 @@ __global__ void k_scan_inclusive(int64_t* v, int64_t len) {
     for (int64_t i = lo; i < hi; ++i) { run += v[i]; v[i] = run; }
 }
 
-__global__ void k_scatter_t(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
-                            const double* __restrict__ vals, int64_t m, unsigned long long* cursor,
-                            int32_t* __restrict__ tcol, double* __restrict__ tval) {
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride) {
-        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
-            unsigned long long pos = atomicAdd(&cursor[colidx[p]], 1ull);
-            tcol[pos] = (int32_t)i;
-            tval[pos] = vals[p];
-        }
+// Row index of every nonzero (int32; m < 2^31).
+__global__ void k_row_ids(const int64_t* __restrict__ rowptr, int64_t m, int32_t* __restrict__ rid) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride)
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) rid[p] = (int32_t)i;
+}
+
+// A^T entries in (column, row) order from the stable column sort of A's nonzeros.
+__global__ void k_gather_t(const int32_t* __restrict__ order, const int32_t* __restrict__ rid,
+                           const double* __restrict__ vals, int64_t nnz, int32_t* __restrict__ tcol,
+                           double* __restrict__ tval) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nnz; p += stride) {
+        const int32_t o = order[p];
+        tcol[p] = rid[o];
+        tval[p] = vals[o];
     }
+}
+
+__global__ void k_iota(int32_t* __restrict__ x, int64_t n) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) x[i] = (int32_t)i;
 }
 
 // The scatter order inside a column depends on atomics; sorting each column by
 // row index makes the transpose (and every SpMM with it) deterministic.
-__global__ void k_sort_segments(const int64_t* __restrict__ ptr, int64_t nseg, int32_t* key, double* val) {
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nseg; c += stride) {
-        int64_t s = ptr[c], e = ptr[c + 1];
-        for (int64_t i = s + 1; i < e; ++i) {
-            int32_t k = key[i];
-            double v = val[i];
-            int64_t j = i - 1;
-            while (j >= s && key[j] > k) { key[j + 1] = key[j]; val[j + 1] = val[j]; --j; }
-            key[j + 1] = k;
-            val[j + 1] = v;
-        }
-    }
-}
 
+// A^T in CSR. Row pointers from per-column counts and a scan; the entries from a stable
+// radix sort of A's nonzeros by column (A's storage order is row-major and row-sorted, so
+// the rows of every column come out ascending). Deterministic, O(nnz) work per digit pass,
+// whatever the row lengths of A^T.
 int csr_transpose(cmsvd_context* ctx, const Csr& A, Csr* At) {
     cudaStream_t s = ctx->s;
+    if (A.nnz >= ((int64_t)1 << 31) || A.m >= ((int64_t)1 << 31)) {
+        set_error("the transpose supports fewer than 2^31 rows and nonzeros");
+        return CMSVD_NOT_SUPPORTED;
+    }
+    const int nnz = (int)A.nnz;
     Csr T;
     T.m = A.n; T.n = A.m; T.nnz = A.nnz;
     CM_CUDA(cudaMalloc(&T.rowptr, sizeof(int64_t) * (T.m + 1)));
-    if (cudaMalloc(&T.colidx, sizeof(int32_t) * (A.nnz > 0 ? A.nnz : 1)) != cudaSuccess ||
-        cudaMalloc(&T.vals, sizeof(double) * (A.nnz > 0 ? A.nnz : 1)) != cudaSuccess) {
+    if (cudaMalloc(&T.colidx, sizeof(int32_t) * (nnz > 0 ? nnz : 1)) != cudaSuccess ||
+        cudaMalloc(&T.vals, sizeof(double) * (nnz > 0 ? nnz : 1)) != cudaSuccess) {
         csr_free(&T);
         set_error("out of device memory for the transpose");
-        return CMSVD_OUT_OF_MEMORY;
-    }
-    unsigned long long* cursor = nullptr;
-    if (cudaMalloc(&cursor, sizeof(unsigned long long) * (T.m + 1)) != cudaSuccess) {
-        csr_free(&T);
-        set_error("out of device memory for the transpose cursor");
         return CMSVD_OUT_OF_MEMORY;
     }
     int st = CMSVD_OK;
     auto chk = [&](cudaError_t e, const char* w) { if (e != cudaSuccess && st == CMSVD_OK) st = cuda_fail(e, w, __FILE__, __LINE__); };
     chk(cudaMemsetAsync(T.rowptr, 0, sizeof(int64_t) * (T.m + 1), s), "memset");
-    int gcap = ctx->sm_count * 8;
+    const int gcap = ctx->sm_count * 8;
     k_col_count<<<grid_for(A.nnz, 256, gcap), 256, 0, s>>>(A.colidx, A.nnz, (unsigned long long*)T.rowptr);
     chk(cudaGetLastError(), "k_col_count");
     k_scan_inclusive<<<1, 1024, 0, s>>>(T.rowptr, T.m + 1);
     chk(cudaGetLastError(), "k_scan");
-    chk(cudaMemcpyAsync(cursor, T.rowptr, sizeof(int64_t) * (T.m + 1), cudaMemcpyDeviceToDevice, s), "copy");
-    k_scatter_t<<<grid_for(A.m, 256, gcap), 256, 0, s>>>(A.rowptr, A.colidx, A.vals, A.m, cursor, T.colidx, T.vals);
-    chk(cudaGetLastError(), "k_scatter");
-    k_sort_segments<<<grid_for(T.m, 256, gcap), 256, 0, s>>>(T.rowptr, T.m, T.colidx, T.vals);
-    chk(cudaGetLastError(), "k_sort");
+    if (nnz > 0 && st == CMSVD_OK) {
+        int32_t *keys_out = nullptr, *idx_in = nullptr, *idx_out = nullptr, *rid = nullptr;
+        void* tmp = nullptr;
+        size_t tmp_bytes = 0;
+        int end_bit = 1;
+        while (end_bit < 31 && ((int64_t)1 << end_bit) < A.n) ++end_bit;
+        chk(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, A.colidx, keys_out, idx_in, idx_out, nnz, 0, end_bit, s),
+            "radix sort size");
+        if (st == CMSVD_OK && (cudaMalloc(&keys_out, sizeof(int32_t) * nnz) != cudaSuccess ||
+                               cudaMalloc(&idx_in, sizeof(int32_t) * nnz) != cudaSuccess ||
+                               cudaMalloc(&idx_out, sizeof(int32_t) * nnz) != cudaSuccess ||
+                               cudaMalloc(&rid, sizeof(int32_t) * nnz) != cudaSuccess ||
+                               cudaMalloc(&tmp, tmp_bytes > 0 ? tmp_bytes : 1) != cudaSuccess)) {
+            cudaGetLastError();
+            set_error("out of device memory for the transpose sort");
+            st = CMSVD_OUT_OF_MEMORY;
+        }
+        if (st == CMSVD_OK) {
+            k_iota<<<grid_for(A.nnz, 256, gcap), 256, 0, s>>>(idx_in, A.nnz);
+            chk(cudaGetLastError(), "k_iota");
+            k_row_ids<<<grid_for(A.m, 256, gcap), 256, 0, s>>>(A.rowptr, A.m, rid);
+            chk(cudaGetLastError(), "k_row_ids");
+            chk(cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, A.colidx, keys_out, idx_in, idx_out, nnz, 0, end_bit, s),
+                "radix sort");
+            k_gather_t<<<grid_for(A.nnz, 256, gcap), 256, 0, s>>>(idx_out, rid, A.vals, A.nnz, T.colidx, T.vals);
+            chk(cudaGetLastError(), "k_gather_t");
+        }
+        chk(cudaStreamSynchronize(s), "sync");
+        for (void* ptr : {(void*)keys_out, (void*)idx_in, (void*)idx_out, (void*)rid, tmp})
+            if (ptr) cudaFree(ptr);
+    }
     chk(cudaStreamSynchronize(s), "sync");
-    cudaFree(cursor);
+    if (st == CMSVD_OK) st = csr_row_stats(ctx, &T);
     if (st != CMSVD_OK) { csr_free(&T); return st; }
     *At = T;
     return CMSVD_OK;
@@ -315,6 +375,58 @@ __global__ void __launch_bounds__(256) k_spmm(const int64_t* __restrict__ rowptr
     }
 }
 
+// Long rows (a few rows holding most nonzeros, e.g. the transpose of a matrix whose
+// columns are image pixels): one CTA per row. Its 256 / LPR groups take contiguous,
+// equal slices of the row, and their partial sums are added in slice order, so the
+// result is deterministic (the summation order differs from k_spmm's).
+template <typename T, int LPR, int CPL>
+__global__ void __launch_bounds__(256) k_spmm_rowcta(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                                                     const T* __restrict__ vals, int64_t rows, int L,
+                                                     const T* __restrict__ X, int64_t ldx, T* __restrict__ Y,
+                                                     int64_t ldy) {
+    constexpr int G = 256 / LPR;
+    __shared__ T part[G][LPR * CPL];
+    const int lane = threadIdx.x % LPR, g = threadIdx.x / LPR;
+    const unsigned mask = LPR == 32 ? 0xffffffffu : (((1u << LPR) - 1u) << ((threadIdx.x & 31) / LPR * LPR));
+    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+        const int64_t rs = rowptr[r], re = rowptr[r + 1];
+        const int64_t slice = (re - rs + G - 1) / G;
+        const int64_t s = rs + g * slice < re ? rs + g * slice : re;
+        const int64_t e = s + slice < re ? s + slice : re;
+        for (int c0 = 0; c0 < L; c0 += LPR * CPL) {
+            T acc[CPL];
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) acc[q] = (T)0;
+            for (int64_t p0 = s; p0 < e; p0 += LPR) {
+                const int64_t p = p0 + lane;
+                int32_t mc = 0;
+                T mv = (T)0;
+                if (p < e) { mc = colidx[p]; mv = vals[p]; }
+                const int cnt = (int)((e - p0) < LPR ? (e - p0) : LPR);
+                for (int k = 0; k < cnt; ++k) {
+                    const int32_t col = __shfl_sync(mask, mc, k, LPR);
+                    const T v = __shfl_sync(mask, mv, k, LPR);
+                    const T* xr = X + (int64_t)col * ldx + c0 + lane;
+#pragma unroll
+                    for (int q = 0; q < CPL; ++q)
+                        if (c0 + lane + q * LPR < L) acc[q] = fma_rn_t(v, __ldg(xr + q * LPR), acc[q]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) part[g][lane + q * LPR] = acc[q];
+            __syncthreads();
+            for (int c = threadIdx.x; c < LPR * CPL; c += blockDim.x) {
+                if (c0 + c < L) {
+                    T sum = part[0][c];
+                    for (int h = 1; h < G; ++h) sum += part[h][c];
+                    Y[r * ldy + c0 + c] = sum;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
 template <typename T>
 static int spmm_t(const Csr& A, const T* vals, int L, const T* X, int64_t ldx, T* Y, int64_t ldy, cudaStream_t s) {
     if (A.m == 0 || L <= 0) return CMSVD_OK;
@@ -322,6 +434,15 @@ static int spmm_t(const Csr& A, const T* vals, int L, const T* X, int64_t ldx, T
     const double e = (double)sizeof(T);
     ProfScope ps(CMSVD_PROF_SPMM, s, (e + 4.0) * A.nnz + 8.0 * (A.m + 1) + e * L * (A.n + A.m), 2.0 * A.nnz * L);
     const int dev_sms = 152;
+    if (A.max_row > 2048) {
+        const unsigned grid = (unsigned)(A.m < dev_sms * 8 ? A.m : dev_sms * 8);
+        if (L <= 8) k_spmm_rowcta<T, 8, 1><<<grid, 256, 0, s>>>(A.rowptr, A.colidx, vals, A.m, L, X, ldx, Y, ldy);
+        else if (L <= 16) k_spmm_rowcta<T, 16, 1><<<grid, 256, 0, s>>>(A.rowptr, A.colidx, vals, A.m, L, X, ldx, Y, ldy);
+        else if (L <= 32) k_spmm_rowcta<T, 32, 1><<<grid, 256, 0, s>>>(A.rowptr, A.colidx, vals, A.m, L, X, ldx, Y, ldy);
+        else k_spmm_rowcta<T, 32, 4><<<grid, 256, 0, s>>>(A.rowptr, A.colidx, vals, A.m, L, X, ldx, Y, ldy);
+        CM_LAUNCH();
+        return CMSVD_OK;
+    }
     if (L <= 8) {
         k_spmm<T, 8, 1><<<grid_for(A.m, 256 / 8, dev_sms * 32), 256, 0, s>>>(A.rowptr, A.colidx, vals, A.m, L, X, ldx, Y, ldy);
     } else if (L <= 16) {

@@ -360,28 +360,22 @@ __device__ __forceinline__ void block_sum3_128(double& a, double& b, double& c, 
     c = (sh[2][0] + sh[2][1]) + (sh[2][2] + sh[2][3]);
 }
 
-// Cooperative form: one launch runs every sweep. All CTAs are co-resident
-// (cudaLaunchCooperativeKernel refuses otherwise) and meet at a grid barrier after
-// each round. The barrier spins with an iteration limit: past it the kernel sets
-// ctl[3] (timeout), and every CTA leaves at the next barrier. ctl: [0] arrivals,
-// [1] generation, [2] sweeps done, [3] timeout; rot[s] = 1 when sweep s rotated.
+// Grid barrier for cooperative launches (all CTAs co-resident: cudaLaunchCooperativeKernel
+// refuses otherwise). ctl[0] counts arrivals and only grows: the k-th barrier is passed
+// once it reaches k * nblocks, so one atomic per CTA suffices. The wait polls with an
+// iteration limit: past it the kernel sets ctl[3] (timeout), and every CTA leaves at the
+// next barrier. ctl: [0] arrivals, [2] sweeps done (Jacobi), [3] timeout.
 __device__ __forceinline__ bool grid_barrier(unsigned* ctl, unsigned nblocks) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned* gen = ctl + 1;
+        volatile unsigned* cnt = ctl;
         volatile unsigned* err = ctl + 3;
-        const unsigned g = *gen;
-        __threadfence();
-        if (atomicAdd(ctl, 1u) == nblocks - 1) {
-            atomicExch(ctl, 0u);
-            __threadfence();
-            atomicAdd(ctl + 1, 1u);
-        } else {
-            long long it = 0;
-            while (*gen == g && *err == 0) {
-                if (++it > 20000000LL) { atomicExch(ctl + 3, 1u); break; }   // >= 0.8 s
-                if (it > 2048) __nanosleep(40);   // poll hot first: a round lasts microseconds
-            }
+        __threadfence();                                   // this CTA's writes before its arrival
+        const unsigned target = (atomicAdd(ctl, 1u) / nblocks + 1u) * nblocks;
+        long long it = 0;
+        while ((int)(*cnt - target) < 0 && *err == 0) {
+            if (++it > 20000000LL) { atomicExch(ctl + 3, 1u); break; }   // >= 0.8 s
+            if (it > 2048) __nanosleep(40);   // poll hot first: a round lasts microseconds
         }
         __threadfence();
     }
@@ -391,113 +385,87 @@ __device__ __forceinline__ bool grid_barrier(unsigned* ctl, unsigned nblocks) {
 
 constexpr int JC_MAXDIM = 512;              // L M <= 512
 
-// Block-cyclic cooperative form: columns are grouped in blocks of JB; CTA k holds two
-// blocks per round (round-robin over the NB blocks), stages them and their V columns in
-// shared memory, rotates every column of the first against every column of the second
-// (JB inner rounds of JB disjoint pairs, one warp per pair) and, in round 0, the pairs
-// inside each block, then writes them back. A sweep needs NB - 1 grid barriers instead of
-// cols - 1, and each CTA does JB^2 rotations per barrier. Every column pair meets once per
-// sweep, as in the cyclic method.
-constexpr int JB = 4;
-__device__ __forceinline__ bool jb_rotate(double* xa, double* xb, double* va, double* vb, int rows, int cols, double tol,
-                                          double negl, int lane) {
-    double al = 0.0, be = 0.0, ga = 0.0;
-    for (int e = lane; e < rows; e += 32) {
-        const double a = xa[e], b = xb[e];
-        al = __fma_rn(a, a, al);
-        be = __fma_rn(b, b, be);
-        ga = __fma_rn(a, b, ga);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {   // butterfly: every lane ends with the same sums
-        al += __shfl_xor_sync(0xffffffffu, al, o);
-        be += __shfl_xor_sync(0xffffffffu, be, o);
-        ga += __shfl_xor_sync(0xffffffffu, ga, o);
-    }
-    if (!(fabs(ga) > tol * sqrt(al * be) && al > negl && be > negl)) return false;
-    const double zeta = (be - al) / (2.0 * ga);
-    const double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-    const double cs = 1.0 / sqrt(1.0 + tt * tt), sn = cs * tt;
-    for (int e = lane; e < rows; e += 32) {
-        const double a = xa[e], b = xb[e];
-        xa[e] = cs * a - sn * b;
-        xb[e] = sn * a + cs * b;
-    }
-    for (int e = lane; e < cols; e += 32) {
-        const double a = va[e], b = vb[e];
-        va[e] = cs * a - sn * b;
-        vb[e] = sn * a + cs * b;
-    }
-    return true;
-}
+// Cooperative form for 97..512 columns: one CTA per pair of a round (round-robin ordering,
+// the pairs of a round are disjoint), all sweeps in one launch, a bounded grid barrier
+// between rounds. Each thread holds its rows of both columns and both V columns in
+// registers, so a round costs one L2 round trip. GB300 runs an FP64 warp instruction in
+// 16 clocks whatever its active lanes, so only warp 0 computes the rotation angle and
+// shares it through shared memory. (Measured alternatives, slower on this part: an 8-CTA
+// thread-block cluster keeping column blocks in shared memory, 25-36 ms per 256 x 256
+// SVD, FP64-bound on its 8 SMs; block-cyclic cooperative kernels with 2 or 4 columns per
+// block, 31 and 21 ms; this form, 16 ms.)
+constexpr int JC_RPT = JC_MAXDIM / 128;      // rows (and V entries) per thread
 
-__global__ void __launch_bounds__(32 * JB) k_jacobi_blk(double* __restrict__ Xc, double* __restrict__ V, int rows, int cols,
-                                                        int nb, double tol, const double* __restrict__ fro2, int max_sweeps,
-                                                        unsigned* ctl, unsigned* rot) {
-    extern __shared__ double jb_smem[];
-    double* Xs = jb_smem;                        // [2][JB][rows]
-    double* Vs = Xs + 2 * JB * rows;             // [2][JB][cols]
-    __shared__ int any_rot;
+__global__ void __launch_bounds__(128) k_jacobi_coop(double* __restrict__ Xc, double* __restrict__ V, int rows, int cols,
+                                                     int np, double tol, const double* __restrict__ fro2, int max_sweeps,
+                                                     unsigned* ctl, unsigned* rot) {
+    __shared__ double sh[3][4];
+    __shared__ double sh_cs, sh_sn;
+    __shared__ int sh_ok;
     const double negl = 1e-36 * *fro2;
-    const int k = blockIdx.x, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int xsz = JB * rows, vsz = JB * cols;
+    const int k = blockIdx.x;
     int sweep = 0;
     for (; sweep < max_sweeps; ++sweep) {
-        for (int round = 0; round < nb - 1; ++round) {
-            int P, Q;
-            if (k == 0) { P = round; Q = nb - 1; }
-            else { P = (round + k) % (nb - 1); Q = (round - k + (nb - 1)) % (nb - 1); }
-            for (int idx = threadIdx.x; idx < 2 * xsz; idx += blockDim.x) {
-                const int slot = idx / xsz, rem = idx - slot * xsz, i = rem / rows, e = rem - i * rows;
-                const int g = (slot ? Q : P) * JB + i;
-                Xs[idx] = g < cols ? __ldcg(Xc + (size_t)g * rows + e) : 0.0;
-            }
-            for (int idx = threadIdx.x; idx < 2 * vsz; idx += blockDim.x) {
-                const int slot = idx / vsz, rem = idx - slot * vsz, i = rem / cols, e = rem - i * cols;
-                const int g = (slot ? Q : P) * JB + i;
-                Vs[idx] = g < cols ? __ldcg(V + (size_t)g * cols + e) : 0.0;
-            }
-            if (threadIdx.x == 0) any_rot = 0;
-            __syncthreads();
-            bool rotated = false;
-            if (round == 0) {
-                for (int t = 0; t < JB - 1; ++t) {   // pairs inside each block
-                    const int slot = warp / (JB / 2), u = warp - slot * (JB / 2);
-                    int i, j;
-                    if (u == 0) { i = t; j = JB - 1; }
-                    else { i = (t + u) % (JB - 1); j = (t - u + JB - 1) % (JB - 1); }
-                    if (i > j) { const int tmp = i; i = j; j = tmp; }
-                    double* xb0 = Xs + slot * xsz;
-                    double* vb0 = Vs + slot * vsz;
-                    rotated |= jb_rotate(xb0 + i * rows, xb0 + j * rows, vb0 + i * cols, vb0 + j * cols, rows, cols, tol, negl, lane);
-                    __syncthreads();
+        for (int round = 0; round < np - 1; ++round) {
+            int p, q;
+            if (k == 0) { p = round; q = np - 1; }
+            else { p = (round + k) % (np - 1); q = (round - k + (np - 1)) % (np - 1); }
+            if (p < cols && q < cols) {
+                if (p > q) { const int t = p; p = q; q = t; }
+                double* xp = Xc + (size_t)p * rows;
+                double* xq = Xc + (size_t)q * rows;
+                double* vp = V + (size_t)p * cols;
+                double* vq = V + (size_t)q * cols;
+                double xa[JC_RPT], xb[JC_RPT], va[JC_RPT], vb[JC_RPT];
+#pragma unroll
+                for (int u = 0; u < JC_RPT; ++u) {
+                    const int i = threadIdx.x + 128 * u;
+                    xa[u] = i < rows ? __ldcg(xp + i) : 0.0;
+                    xb[u] = i < rows ? __ldcg(xq + i) : 0.0;
+                    va[u] = i < cols ? __ldcg(vp + i) : 0.0;
+                    vb[u] = i < cols ? __ldcg(vq + i) : 0.0;
                 }
-            }
-            for (int t = 0; t < JB; ++t) {           // first block against second
-                const int i = warp, j = (warp + t) % JB;
-                double *xa = Xs + i * rows, *xb = Xs + xsz + j * rows;
-                double *va = Vs + i * cols, *vb = Vs + vsz + j * cols;
-                if (P > Q) {
-                    double* tmp = xa; xa = xb; xb = tmp;
-                    tmp = va; va = vb; vb = tmp;
+                double al = 0.0, be = 0.0, ga = 0.0;
+#pragma unroll
+                for (int u = 0; u < JC_RPT; ++u) {
+                    al = __fma_rn(xa[u], xa[u], al);
+                    be = __fma_rn(xb[u], xb[u], be);
+                    ga = __fma_rn(xa[u], xb[u], ga);
                 }
-                rotated |= jb_rotate(xa, xb, va, vb, rows, cols, tol, negl, lane);
+                block_sum3_128(al, be, ga, sh);
+                if (threadIdx.x < 32) {
+                    int ok = fabs(ga) > tol * sqrt(al * be) && al > negl && be > negl;
+                    double cs = 1.0, sn = 0.0;
+                    if (ok) {
+                        const double zeta = (be - al) / (2.0 * ga);
+                        const double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+                        cs = 1.0 / sqrt(1.0 + tt * tt);
+                        sn = cs * tt;
+                    }
+                    if (threadIdx.x == 0) {
+                        sh_ok = ok;
+                        sh_cs = cs;
+                        sh_sn = sn;
+                    }
+                }
                 __syncthreads();
-            }
-            if (rotated && lane == 0) any_rot = 1;
-            __syncthreads();
-            if (any_rot) {
-                for (int idx = threadIdx.x; idx < 2 * xsz; idx += blockDim.x) {
-                    const int slot = idx / xsz, rem = idx - slot * xsz, i = rem / rows, e = rem - i * rows;
-                    const int g = (slot ? Q : P) * JB + i;
-                    if (g < cols) Xc[(size_t)g * rows + e] = Xs[idx];
+                if (sh_ok) {
+                    const double cs = sh_cs, sn = sh_sn;
+#pragma unroll
+                    for (int u = 0; u < JC_RPT; ++u) {
+                        const int i = threadIdx.x + 128 * u;
+                        if (i < rows) {
+                            xp[i] = cs * xa[u] - sn * xb[u];
+                            xq[i] = sn * xa[u] + cs * xb[u];
+                        }
+                        if (i < cols) {
+                            vp[i] = cs * va[u] - sn * vb[u];
+                            vq[i] = sn * va[u] + cs * vb[u];
+                        }
+                    }
+                    if (threadIdx.x == 0) atomicExch(rot + sweep, 1u);
                 }
-                for (int idx = threadIdx.x; idx < 2 * vsz; idx += blockDim.x) {
-                    const int slot = idx / vsz, rem = idx - slot * vsz, i = rem / cols, e = rem - i * cols;
-                    const int g = (slot ? Q : P) * JB + i;
-                    if (g < cols) V[(size_t)g * cols + e] = Vs[idx];
-                }
-                if (threadIdx.x == 0) atomicExch(rot + sweep, 1u);
+                __syncthreads();   // sh, sh_ok reused by the next round
             }
             if (!grid_barrier(ctl, gridDim.x)) return;
         }
@@ -580,24 +548,14 @@ int jacobi_svd(const double* Bm, int brows, int bcols, int trans, double* Xc, do
     const int max_sweeps = 40;
     CM_CUDA(cudaMemsetAsync(ctl, 0, sizeof(unsigned) * (4 + max_sweeps), s));
     if (rows > JC_MAXDIM || cols > JC_MAXDIM) { set_error("Jacobi SVD supports at most %d rows and columns", JC_MAXDIM); return CMSVD_NOT_SUPPORTED; }
-    // block-cyclic form: nb blocks of JB columns (nb even), nb / 2 CTAs
-    int nb = (cols + JB - 1) / JB;
-    nb += nb & 1;
-    const int grid = nb / 2;
-    const size_t smem = sizeof(double) * 2 * JB * ((size_t)rows + cols);
+    const int grid = np / 2;
     {
-        static int set_attr = 0;
-        if (!set_attr) {
-            CM_CUDA(cudaFuncSetAttribute(k_jacobi_blk, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(sizeof(double) * 2 * JB * 2 * JC_MAXDIM)));
-            set_attr = 1;
-        }
         int per_sm = 0;
-        CM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_blk, 32 * JB, smem));
+        CM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_coop, 128, 0));
         if (per_sm * ctx->sm_count < grid) { set_error("Jacobi grid of %d CTAs cannot be co-resident", grid); return CMSVD_NOT_SUPPORTED; }
         ProfScope ps(CMSVD_PROF_JACOBI, s, 0.0, 0.0, 1);
-        void* args[] = {&Xc, &V, (void*)&rows, (void*)&cols, (void*)&nb, (void*)&tol, &fro2, (void*)&max_sweeps, &ctl, &rot};
-        CM_CUDA(cudaLaunchCooperativeKernel((const void*)k_jacobi_blk, dim3(grid), dim3(32 * JB), args, smem, s));
+        void* args[] = {&Xc, &V, (void*)&rows, (void*)&cols, (void*)&np, (void*)&tol, &fro2, (void*)&max_sweeps, &ctl, &rot};
+        CM_CUDA(cudaLaunchCooperativeKernel((const void*)k_jacobi_coop, dim3(grid), dim3(128), args, 0, s));
         note_launch();
     }
     unsigned h[4];
@@ -702,13 +660,15 @@ __global__ void __launch_bounds__(256) k_chol_coop(const double* __restrict__ G,
 // Deflation by Cholesky with diagonal pivoting of G = T^T T (c <= 512, one CTA): at step k
 // the largest remaining diagonal entry is brought to position k; the factorization stops
 // when it is <= keep * max diag(G). Then P^T G P ~ L L^T with L (c x c') and a discarded
-// Schur complement of trace <= (c - c') keep max diag(G). Outputs, as k_deflate's:
-// T3 = P_1 L11^{-T} (c x c', so (T T3)^T (T T3) = I) and R3 = L^T P^T (c' x c, T ~ T T3 R3).
-// W and L are c x c scratch. Ties pick the smaller index, so the result is deterministic.
+// Schur complement of trace <= (c - c') keep max diag(G). Only the upper triangle of the
+// working copy W is kept (the symmetric swap reads the mirrored entries). Outputs:
+// R3 = L^T P^T (c' x c, row-major; T ~ (T T3) R3), Lt = L11^T (c' x c', row-major, in W),
+// perm (the pivot order, c ints, in the L scratch) and c'. T3 = P_1 L11^{-T} is formed by
+// k_pchol_t3 from the inverse of Lt, so that (T T3)^T (T T3) = I.
+// Ties pick the smaller index, so the result is deterministic.
 __global__ void __launch_bounds__(1024) k_pchol_deflate(const double* __restrict__ G, int c, double keep,
                                                         double* __restrict__ W, double* __restrict__ L,
-                                                        double* __restrict__ T3, double* __restrict__ R3,
-                                                        int* __restrict__ cp_out) {
+                                                        double* __restrict__ R3, int* __restrict__ cp_out) {
     __shared__ int perm[512];
     __shared__ double rv[32];
     __shared__ int ri[32];
@@ -750,17 +710,14 @@ __global__ void __launch_bounds__(1024) k_pchol_deflate(const double* __restrict
         const int j = sh_j;
         const double d = sh_piv;
         if (k == c || !(d > keep * sh_d0)) break;
-        if (j != k) {   // symmetric swap of rows/columns k and j, and of the rows of L done so far
-            for (int col = t; col < c; col += nt) {
-                const double a = W[(size_t)k * c + col];
-                W[(size_t)k * c + col] = W[(size_t)j * c + col];
-                W[(size_t)j * c + col] = a;
-            }
-            __syncthreads();
-            for (int row = t; row < c; row += nt) {
-                const double a = W[(size_t)row * c + k];
-                W[(size_t)row * c + k] = W[(size_t)row * c + j];
-                W[(size_t)row * c + j] = a;
+        if (j != k) {   // symmetric swap of indices k < j on the upper triangle
+            for (int x = k + 1 + t; x < c; x += nt) {
+                if (x == j) continue;
+                double* a = W + (size_t)k * c + x;
+                double* b = x < j ? W + (size_t)x * c + j : W + (size_t)j * c + x;
+                const double tmp = *a;
+                *a = *b;
+                *b = tmp;
             }
             for (int col = t; col < k; col += nt) {
                 const double a = L[(size_t)k * c + col];
@@ -768,40 +725,48 @@ __global__ void __launch_bounds__(1024) k_pchol_deflate(const double* __restrict
                 L[(size_t)j * c + col] = a;
             }
             if (t == 0) {
-                const int a = perm[k];
+                const double a = W[(size_t)k * c + k];
+                W[(size_t)k * c + k] = W[(size_t)j * c + j];
+                W[(size_t)j * c + j] = a;
+                const int pa = perm[k];
                 perm[k] = perm[j];
-                perm[j] = a;
+                perm[j] = pa;
             }
             __syncthreads();
         }
         const double lkk = sqrt(d);
-        for (int i = k + t; i < c; i += nt) L[(size_t)i * c + k] = i == k ? lkk : W[(size_t)i * c + k] / lkk;
+        for (int i = k + t; i < c; i += nt) L[(size_t)i * c + k] = i == k ? lkk : W[(size_t)k * c + i] / lkk;
         __syncthreads();
         const int w = c - k - 1;
         for (int e = t; e < w * w; e += nt) {
             const int i = k + 1 + e / w, jj = k + 1 + e % w;
-            W[(size_t)i * c + jj] = __fma_rn(-L[(size_t)i * c + k], L[(size_t)jj * c + k], W[(size_t)i * c + jj]);
+            if (jj >= i)
+                W[(size_t)i * c + jj] = __fma_rn(-L[(size_t)i * c + k], L[(size_t)jj * c + k], W[(size_t)i * c + jj]);
         }
         __syncthreads();
     }
     const int cp = k;
     if (t == 0) *cp_out = cp;
-    // L11^{-1} (lower) into W, one column per thread by forward substitution
-    for (int jc = t; jc < cp; jc += nt) {
-        for (int i = jc; i < cp; ++i) {
-            double acc = i == jc ? 1.0 : 0.0;
-            for (int q = jc; q < i; ++q) acc = __fma_rn(-L[(size_t)i * c + q], W[(size_t)q * c + jc], acc);
-            W[(size_t)i * c + jc] = acc / L[(size_t)i * c + i];
-        }
-    }
-    __syncthreads();
-    for (int e = t; e < c * cp; e += nt) {       // T3 row-major c x cp: row perm[r] = row r of L11^{-T}
-        const int r = e / cp, i = e % cp;
-        T3[(size_t)perm[r] * cp + i] = (r < cp && i >= r) ? W[(size_t)i * c + r] : 0.0;
-    }
     for (int e = t; e < cp * c; e += nt) {       // R3 row-major cp x c: R3[i][perm[r]] = L[r][i]
         const int i = e / c, r = e % c;
         R3[(size_t)i * c + perm[r]] = r >= i ? L[(size_t)r * c + i] : 0.0;
+    }
+    for (int e = t; e < cp * cp; e += nt) {      // Lt = L11^T, row-major cp x cp, into W
+        const int i = e / cp, jj = e % cp;
+        W[e] = jj >= i ? L[(size_t)jj * c + i] : 0.0;
+    }
+    __syncthreads();
+    int* perm_out = (int*)L;
+    for (int i = t; i < c; i += nt) perm_out[i] = perm[i];
+}
+
+// T3 (c x cp, row-major) = P_1 L11^{-T}: row perm[r] is row r of Lti = (L11^T)^{-1} for r < cp,
+// the other rows are zero.
+__global__ void k_pchol_t3(const double* __restrict__ Lti, int cp, const int* __restrict__ perm, int c,
+                           double* __restrict__ T3) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < c * cp; e += gridDim.x * blockDim.x) {
+        const int r = e / cp, i = e % cp;
+        T3[(size_t)perm[r] * cp + i] = r < cp ? Lti[(size_t)r * cp + i] : 0.0;
     }
 }
 
@@ -961,8 +926,8 @@ int orth_qr(const double* X, int64_t ldx, int64_t n, int c, double* Q, double* R
     CM_TRY(gram(T, c, c, T, c, c, n, G, part, o.pcap, ctx->sm_count, s));
     if (c > 512) { set_error("orthogonalization supports at most 512 columns"); return CMSVD_NOT_SUPPORTED; }
     {
-        ProfScope ps(CMSVD_PROF_SMALL, s, 40.0 * c * c, c * (double)c * c / 3.0);
-        k_pchol_deflate<<<1, 1024, 0, s>>>(G, c, 1e-10, Wp, Lp, T3, R3, cp_dev);
+        ProfScope ps(CMSVD_PROF_SMALL, s, 40.0 * c * c, c * (double)c * c / 6.0);
+        k_pchol_deflate<<<1, 1024, 0, s>>>(G, c, 1e-10, Wp, Lp, R3, cp_dev);
         CM_LAUNCH();
     }
     CM_CUDA(cudaMemcpyAsync(ctx->pinned, cp_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -970,6 +935,12 @@ int orth_qr(const double* X, int64_t ldx, int64_t n, int c, double* Q, double* R
     const int cp = ctx->pinned[0];
     *c_out = cp;
     if (cp <= 0) return CMSVD_OK;
+    CM_TRY(trinv(o, Wp, cp));   // (L11^T)^{-1} into o.Ri
+    {
+        ProfScope ps(CMSVD_PROF_SMALL, s, 16.0 * c * cp, 0.0);
+        k_pchol_t3<<<(c * cp + 255) / 256, 256, 0, s>>>(o.Ri, cp, (const int*)Lp, c, T3);
+        CM_LAUNCH();
+    }
     // first plain pass without forming Q3 = T T3: its Gram is T3^T (T^T T) T3, from the Gram
     // of T computed above (error amplified by at most 1 / lambda_min of the kept directions,
     // <= 1e10 u, which only affects Q4's orthogonality), so Q4 = T (T3 R4^{-1}) is one GEMM

@@ -62,6 +62,7 @@ struct Csr {
     int32_t* colidx = nullptr;   // device, nnz
     double* vals = nullptr;      // device, nnz
     float* vals_f = nullptr;     // device, nnz: FP32 copy for the mixed-precision Krylov path (made on demand)
+    int64_t max_row = 0;         // longest row (nonzeros); long rows switch the SpMM to one CTA per row
 };
 
 struct Components {             // connected components of the column graph (A^T A)

@@ -264,3 +264,43 @@ def digits_like(m: int = 60000, side: int = 28, classes: int = 10, nnz_row: floa
         x = z / lam
     A.vals = A.vals / np.sqrt(lam)
     return A
+
+
+def batched_problems(count: int = 64, seed: int = 4, n_min: int = 2000, n_max: int = 80000):
+    """Many independent problems of the block-permuted kind (10 x 4 N(0,1) blocks, m = 2.5 n).
+
+    n_i = 4 round(exp(U(ln n_min, ln n_max)) / 4). L_i is drawn from {16, 32}, N = 32 and
+    M = 4. (With N = 16 the oracle saturates the L M = 128 subspace on exterior windows and
+    finds none of their values: the 16-point filter decays too slowly below a.) t0 = floor(L M / 3) (L M ~ 3 t, as in Sec. 4.3). Every second problem is exterior:
+    b = 1.01 sigma_max, and a sits at the midpoint of the widest relative gap below the t-th
+    largest value, t within t0 +- 10. The others are interior: a window of t0 values at a
+    uniform position, moved by at most 10 places to the position whose two bounding gaps have
+    the widest smaller relative gap. An endpoint close to a singular value leaves that value's
+    filter near 1/2 (Sec. 4, Exp I). With N = 16 that saturates the L M subspace, and the
+    oracle itself then finds nothing. Returns a list of dicts with keys A, sigma (descending),
+    a, b, t, N, L, M, kind, seed_v (the seed of V_in).
+    """
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(4 * round(np.exp(rng.uniform(np.log(n_min), np.log(n_max))) / 4))
+        rng.choice([16, 32])                        # (former N draw, kept so the stream stays aligned)
+        N = 32
+        L = int(rng.choice([16, 32]))
+        M = 4
+        t0 = (L * M) // 3
+        bp = block_permuted(n // 4, 10, 4, seed=int(rng.integers(1 << 30)))
+        s = bp.sigmas_desc()
+        rel_gap = (s[:-1] - s[1:]) / s[1:]          # gap below s[k], relative
+        if i % 2 == 0:
+            t = max(range(t0 - 10, t0 + 11), key=lambda k: (rel_gap[k - 1], -abs(k - t0)))
+            a, b, kind = 0.5 * (s[t - 1] + s[t]), 1.01 * float(s[0]), "exterior"
+        else:
+            t = t0
+            first0 = int(rng.integers(t + 20, s.size - 2 * t - 20))
+            first = max(range(first0 - 10, first0 + 11),
+                        key=lambda f: (min(rel_gap[f - 1], rel_gap[f + t - 1]), -abs(f - first0)))
+            a, b = 0.5 * (s[first + t - 1] + s[first + t]), 0.5 * (s[first - 1] + s[first])
+            kind = "interior"
+        out.append(dict(A=bp.A, sigma=s, a=float(a), b=float(b), t=t, N=N, L=L, M=M, kind=kind, seed_v=1000 + i))
+    return out

@@ -71,6 +71,24 @@ def test_spmm_parity(B, ctx, L):
     M.close()
 
 
+@pytest.mark.parametrize("L", [3, 15, 32, 120])
+def test_spmm_long_rows(B, ctx, L):
+    """Rows far longer than 2048 nonzeros (the transpose of a tall matrix: 20 rows of ~5000)
+    take the one-CTA-per-row kernel, deterministically. The bound scales with the row length:
+    a sum of n = 5000 products carries ~sqrt(n) u of sum |a||x| (1e-14 for rows of 17)."""
+    A = synth.random_sparse(20000, 20, 5, seed=L)
+    M = B.Matrix.from_csr(ctx, A)
+    Ad = A.to_dense()
+    X = np.random.default_rng(4).standard_normal((20000, L))
+    Yt = M.spmm(dev(X), transpose=True)
+    ref = Ad.T @ X
+    assert np.max(np.abs(Yt.cpu().numpy() - ref) / (np.abs(Ad.T) @ np.abs(X) + 1e-300)) < 2e-13
+    assert torch.equal(Yt, M.spmm(dev(X), transpose=True))
+    Z = np.random.default_rng(5).standard_normal((20, L))
+    assert np.max(np.abs(M.spmm(dev(Z)).cpu().numpy() - Ad @ Z) / (np.abs(Ad) @ np.abs(Z) + 1e-300)) < 1e-14
+    M.close()
+
+
 def test_spmm_transpose_deterministic(B, ctx):
     A = synth.random_sparse(3000, 1000, 12, seed=5)
     M = B.Matrix.from_csr(ctx, A)
