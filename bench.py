@@ -253,7 +253,7 @@ def run_ours(args, w, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "description": w["desc"], **cfg, "t": w["t"],
-                       "solver": {0: "auto", 1: "krylov", 2: "direct"}[stats[-1]["solver_used"]],
+                       "solver": {0: "auto", 1: "krylov", 2: "direct", 3: "dense"}[stats[-1]["solver_used"]],
                        "l2": "flushed (256 MiB write) before every step, outside the timed window",
                        "parallelism": f"replicas x{world}"},
             "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)),
@@ -506,6 +506,7 @@ def measure_table2(B, dev):
             B.cmsvd_result_destroy(r)
         err = float(np.max(np.abs(sig - truth) / truth)) if k == truth.size and k else None
         rows.append({"kind": kind, "a": float(a), "b": float(b), "t": int(truth.size), "L": L, "found": int(k),
+                     "solver": {1: "krylov", 2: "direct", 3: "dense"}.get(st["solver_used"], "?"),
                      "ms_steps_1_2": st["ms_solve"], "ms_step_3": st["ms_truncate"], "ms_step_4": st["ms_qr"],
                      "ms_step_5": st["ms_ritz"], "ms_total": 1e3 * wall, "lanczos_steps": int(st["krylov_iters"]),
                      "sigma_rel_err": err, "max_res": st["max_res_u"]})

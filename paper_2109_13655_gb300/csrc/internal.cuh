@@ -165,6 +165,9 @@ int krylov_moments(cmsvd_matrix* A, const cmsvd_params* p, const double2* quad, 
 size_t direct_workspace(const cmsvd_matrix* A, const cmsvd_params* p);
 int direct_moments(cmsvd_matrix* A, const cmsvd_params* p, const double2* quad, int Mk,
                    const double* X, int64_t ldx, double* S, int64_t lds, Arena& ws);
+size_t dense_workspace(const cmsvd_matrix* A, const cmsvd_params* p);
+int dense_moments(cmsvd_matrix* A, const cmsvd_params* p, const double2* quad, int Mk,
+                  const double* X, int64_t ldx, double* S, int64_t lds, Arena& ws);
 int norm_estimate(cmsvd_matrix* A, Arena& ws, double* norm_out);
 
 // Persistent outputs of one solve (capacity L M each; U m x c, V n x c).

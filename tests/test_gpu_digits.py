@@ -41,8 +41,9 @@ def interval(s, kind, t):
     return a, b
 
 
+@pytest.mark.parametrize("solver", ["auto", "krylov"])
 @pytest.mark.parametrize("kind,t,L", [("exterior", 21, 15), ("interior", 17, 15)])
-def test_digits_like_table1(B, digits, kind, t, L):
+def test_digits_like_table1(B, digits, kind, t, L, solver):
     A, s = digits
     assert A.m == 60000 and A.n == 784 and 140 <= A.nnz / A.m <= 160 and A.vals.min() > 0
     a, b = interval(s, kind, t)
@@ -52,9 +53,10 @@ def test_digits_like_table1(B, digits, kind, t, L):
     ref = O.solve_interval(A, a, b, 32, L, 4, Vin, variant="nt", norm_A=s[0])
     ctx = B.Context()
     M = B.Matrix.from_csr(ctx, A)
-    out = M.solve_interval(a, b, B.params(N=32, L=L, M=4, variant="nt", norm_A=s[0]),
+    out = M.solve_interval(a, b, B.params(N=32, L=L, M=4, variant="nt", norm_A=s[0], solver=solver),
                            torch.from_numpy(Vin).cuda())
-    assert out.stats["solver_used"] == B.SOLVER_KRYLOV and out.stats["converged"] == 1
+    want = B.SOLVER_DENSE if solver == "auto" else B.SOLVER_KRYLOV    # n = 784: AUTO is the dense solver
+    assert out.stats["solver_used"] == want and out.stats["converged"] == 1
     assert out.sigma.size == ref.sigma.size == t
     assert np.max(np.abs(out.sigma - truth) / truth) <= 1e-10
     assert np.max(np.abs(out.sigma - ref.sigma) / ref.sigma) <= 1e-10

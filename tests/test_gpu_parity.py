@@ -196,17 +196,21 @@ def compare(out, ref, truth=None, vec_tol=1e-7, spectrum=None, norm_A=1.0, res_t
     assert np.max(np.abs(out.V.T @ out.V - np.eye(out.sigma.size))) <= 1e-10
 
 
-def test_solve_random_sparse_2000x1000(B, ctx):
-    """The 2000 x 1000, 8 nnz/row workload: sigma ranked 400-419, N=16, L=16, M=4."""
+@pytest.mark.parametrize("solver", ["auto", "krylov"])
+def test_solve_random_sparse_2000x1000(B, ctx, solver):
+    """The 2000 x 1000, 8 nnz/row workload: sigma ranked 400-419, N=16, L=16, M=4. AUTO takes
+    the dense direct solver (n = 1000 <= 1024, one connected component); the Krylov solver is
+    checked on the same case."""
     A = synth.random_sparse(2000, 1000, 8, seed=0)
     s = np.linalg.svd(A.to_dense(), compute_uv=False)
     a, b, _ = synth.window_interval(s, 400, 20)
     Vin = synth.gaussian_block(1000, 16, 1)
     ref = O.solve_interval(A, a, b, 16, 16, 4, Vin, norm_A=s[0])
     M = B.Matrix.from_csr(ctx, A)
-    out = M.solve_interval(a, b, B.params(N=16, L=16, M=4), dev(Vin))
+    out = M.solve_interval(a, b, B.params(N=16, L=16, M=4, solver=solver), dev(Vin))
     assert out.status in (B.OK,)
-    assert out.stats["solver_used"] == B.SOLVER_KRYLOV and out.stats["converged"] == 1
+    want = B.SOLVER_DENSE if solver == "auto" else B.SOLVER_KRYLOV
+    assert out.stats["solver_used"] == want and out.stats["converged"] == 1
     assert abs(out.stats["norm_A"] - s[0]) <= 1e-8 * s[0]
     compare(out, ref, truth=s[400:420][::-1])
     M.close()
@@ -235,6 +239,31 @@ def test_solve_model_problems(B, ctx, which, variant, refine):
         assert out.stats["refine_rounds"] <= refine
         assert out.stats["refine_residual"] <= 1e-8
     compare(out, ref, truth=truth, vec_tol=1e-6, spectrum=sig, norm_A=sig.max(), res_tol=tt)
+    M.close()
+
+
+@pytest.mark.parametrize("which,variant", [(1, "linear"), (1, "nt"), (2, "nt")])
+def test_solve_model_problems_dense(B, ctx, which, variant):
+    """Exp II (Sec. 4.2) with the dense direct solver: A^T A (200 x 200) eigendecomposed once,
+    every shifted solve exact, as in the oracle."""
+    Ad, sig = synth.model_problem(which)
+    a, b = (0.8, 1.2) if which == 1 else (10 ** -3.025, 10 ** -1.025)
+    truth = sig[(sig >= a) & (sig <= b)]
+    Vin = synth.gaussian_block(200, 20, 3)
+    tt = 1e-10 if which == 1 else 1e-9
+    ref = O.solve_interval(Ad, a, b, 32, 20, 4, Vin, variant=variant, norm_A=sig.max(), tol_triplet=tt)
+    M = B.Matrix.from_csr(ctx, synth.csr_from_dense(Ad))
+    out = M.solve_interval(a, b, B.params(N=32, L=20, M=4, variant=variant, solver="dense", tol_triplet=tt), dev(Vin))
+    assert out.stats["solver_used"] == B.SOLVER_DENSE
+    compare(out, ref, truth=truth, vec_tol=1e-6, spectrum=sig, norm_A=sig.max(), res_tol=tt)
+    M.close()
+
+
+def test_dense_solver_rejects_wide_matrix(B, ctx):
+    A = synth.random_sparse(3000, 1500, 4, seed=3)
+    M = B.Matrix.from_csr(ctx, A)
+    with pytest.raises(RuntimeError):
+        M.solve_interval(1.0, 2.0, B.params(N=16, L=8, M=4, solver="dense"), dev(synth.gaussian_block(1500, 8, 1)))
     M.close()
 
 
