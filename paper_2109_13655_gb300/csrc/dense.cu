@@ -402,8 +402,10 @@ constexpr int JC_MAXDIM = 1024;             // L M <= 512; the dense direct solv
 // thread-block cluster keeping column blocks in shared memory, 25-36 ms per 256 x 256
 // SVD, FP64-bound on its 8 SMs; block-cyclic cooperative kernels with 2 or 4 columns per
 // block, 31 and 21 ms; this form, 16 ms.)
-constexpr int JC_RPT = JC_MAXDIM / 128;      // rows (and V entries) per thread
-
+// RPT: rows (and V entries) per thread, the smallest of 2, 4, 8 with 128 RPT >= rows, cols
+// (the FP64 FMAs of the dot products run on every register slot, so a larger RPT than
+// needed costs FP64 issue slots).
+template <int RPT>
 __global__ void __launch_bounds__(128) k_jacobi_coop(double* __restrict__ Xc, double* __restrict__ V, int rows, int cols,
                                                      int np, double tol, const double* __restrict__ fro2, int max_sweeps,
                                                      unsigned* ctl, unsigned* rot) {
@@ -424,9 +426,9 @@ __global__ void __launch_bounds__(128) k_jacobi_coop(double* __restrict__ Xc, do
                 double* xq = Xc + (size_t)q * rows;
                 double* vp = V + (size_t)p * cols;
                 double* vq = V + (size_t)q * cols;
-                double xa[JC_RPT], xb[JC_RPT], va[JC_RPT], vb[JC_RPT];
+                double xa[RPT], xb[RPT], va[RPT], vb[RPT];
 #pragma unroll
-                for (int u = 0; u < JC_RPT; ++u) {
+                for (int u = 0; u < RPT; ++u) {
                     const int i = threadIdx.x + 128 * u;
                     xa[u] = i < rows ? __ldcg(xp + i) : 0.0;
                     xb[u] = i < rows ? __ldcg(xq + i) : 0.0;
@@ -435,7 +437,7 @@ __global__ void __launch_bounds__(128) k_jacobi_coop(double* __restrict__ Xc, do
                 }
                 double al = 0.0, be = 0.0, ga = 0.0;
 #pragma unroll
-                for (int u = 0; u < JC_RPT; ++u) {
+                for (int u = 0; u < RPT; ++u) {
                     al = __fma_rn(xa[u], xa[u], al);
                     be = __fma_rn(xb[u], xb[u], be);
                     ga = __fma_rn(xa[u], xb[u], ga);
@@ -460,7 +462,7 @@ __global__ void __launch_bounds__(128) k_jacobi_coop(double* __restrict__ Xc, do
                 if (sh_ok) {
                     const double cs = sh_cs, sn = sh_sn;
 #pragma unroll
-                    for (int u = 0; u < JC_RPT; ++u) {
+                    for (int u = 0; u < RPT; ++u) {
                         const int i = threadIdx.x + 128 * u;
                         if (i < rows) {
                             xp[i] = cs * xa[u] - sn * xb[u];
@@ -558,12 +560,15 @@ int jacobi_svd(const double* Bm, int brows, int bcols, int trans, double* Xc, do
     if (rows > JC_MAXDIM || cols > JC_MAXDIM) { set_error("Jacobi SVD supports at most %d rows and columns", JC_MAXDIM); return CMSVD_NOT_SUPPORTED; }
     const int grid = np / 2;
     {
+        const int mx = rows > cols ? rows : cols;
+        const void* fn = mx <= 256 ? (const void*)k_jacobi_coop<2>
+                       : mx <= 512 ? (const void*)k_jacobi_coop<4> : (const void*)k_jacobi_coop<8>;
         int per_sm = 0;
-        CM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_coop, 128, 0));
+        CM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 128, 0));
         if (per_sm * ctx->sm_count < grid) { set_error("Jacobi grid of %d CTAs cannot be co-resident", grid); return CMSVD_NOT_SUPPORTED; }
         ProfScope ps(CMSVD_PROF_JACOBI, s, 0.0, 0.0, 1);
         void* args[] = {&Xc, &V, (void*)&rows, (void*)&cols, (void*)&np, (void*)&tol, &fro2, (void*)&max_sweeps, &ctl, &rot};
-        CM_CUDA(cudaLaunchCooperativeKernel((const void*)k_jacobi_coop, dim3(grid), dim3(128), args, 0, s));
+        CM_CUDA(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(128), args, 0, s));
         note_launch();
     }
     unsigned h[4];

@@ -74,3 +74,22 @@ def test_context_without_gpu_fails_cleanly(lib):
     assert st == B.CUDA_ERROR
     assert h.value is None
     assert len(lib.cmsvd_last_error()) > 0
+
+
+def test_batch_and_server_argument_checks(lib):
+    """Host-side argument validation of the batched and serving entry points (no GPU work)."""
+    import ctypes as C
+    st = (C.c_int * 1)()
+    assert lib.cmsvd_solve_batch(-1, None, None, None, None, None, None, None, None, None) == B.INVALID_ARG
+    assert lib.cmsvd_solve_batch(1, None, None, None, None, None, None, None, None, st) == B.INVALID_ARG
+    assert lib.cmsvd_solve_batch(0, None, None, None, None, None, None, None, None, None) == B.OK
+    h = C.c_void_p()
+    assert lib.cmsvd_server_create(0, 0, C.byref(h)) == B.INVALID_ARG
+    assert lib.cmsvd_server_create(65, 0, C.byref(h)) == B.INVALID_ARG
+    assert lib.cmsvd_server_create(1, 0, None) == B.INVALID_ARG
+    assert lib.cmsvd_server_destroy(None) == B.OK
+    assert lib.cmsvd_server_wait(None, 1, 0, None, None, None, None) == B.INVALID_ARG
+    assert lib.cmsvd_server_take(None, 1, 0, None, None, None, None, None, None, None) == B.INVALID_ARG
+    assert lib.cmsvd_server_submit(None, 0, 0.1, 0.2, None, None, None) == B.INVALID_ARG
+    assert lib.cmsvd_status_string(B.PENDING) == b"pending"
+    assert lib.cmsvd_result_copy_estimate(None, None) == B.INVALID_ARG

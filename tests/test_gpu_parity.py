@@ -277,7 +277,7 @@ def test_solve_mixed_precision(B, ctx, case):
         a, b, _ = synth.window_interval(s, 400, 20)
         Vin = synth.gaussian_block(1000, 16, 1)
         ref = O.solve_interval(A, a, b, 16, 16, 4, Vin, norm_A=s[0])
-        p = B.params(N=16, L=16, M=4, precision=B.MIXED)
+        p = B.params(N=16, L=16, M=4, solver="krylov", precision=B.MIXED)
         truth, spec, nA = s[400:420][::-1], s, s[0]
     else:
         which, variant = (1, "linear") if case == "model1" else (2, "nt")
