@@ -244,6 +244,7 @@ def run_ours(args, w, rank, world, local_rank):
     table2 = measure_table2(B, dev) if (rank == 0 and args.table2) else None
     batched = measure_batched(B, dev) if (rank == 0 and args.batched) else None
     serving = measure_serving(B) if (rank == 0 and args.serving) else None
+    spmm_big = measure_spmm(B, dev) if (rank == 0 and args.spmm) else None
     if rank == 0:
         value = job_throughput(args.steps, world, tmax)
         prof = aggregate_profile(stats)
@@ -277,6 +278,8 @@ def run_ours(args, w, rank, world, local_rank):
             line["batched_workload"] = batched
         if serving is not None:
             line["serving_workload"] = serving
+        if spmm_big is not None:
+            line["spmm_roofline"] = spmm_big
         if args.cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w)
         print(json.dumps(line), flush=True)
@@ -471,6 +474,50 @@ def measure_serving(B, slots=8, rate=200.0, count=300, seed=5):
             "queue_ms": {"p50": pct(que, 50), "p99": pct(que, 99)}, "all_valid": valid}
 
 
+def measure_spmm(B, dev, reps=10):
+    """The CSR SpMM at full scale: the 2,000,000 x 1,000,000 block-permuted matrix (62500
+    dense 32 x 16 blocks, 32M nonzeros, rows and columns permuted) against an L = 32 block,
+    A X and A^T Y, in FP64 and in FP32 (the mixed path's SpMM). Algorithmic bytes per call:
+    (e + 4) nnz + 8 (rows + 1) + e L (m + n) with e the element size (A once, X once, Y once);
+    achieved = bytes / CUDA-event time, against the measured HBM copy bandwidth. In FP64 the
+    2 L flops per nonzero (1.75 flop/B) exceed GB300's FP64 balance (~0.18 flop/B), so the
+    FP64 SpMM is bound by the FP64 pipe, not by HBM; TFLOP/s is reported beside GB/s."""
+    import torch
+    bp = synth.block_permuted(62500, 32, 16, seed=6, dist="uniform_bf16")
+    A = bp.A
+    ctx = B.Context()
+    M = B.Matrix.from_csr(ctx, A)
+    L = 32
+    X = torch.randn(A.n, L, dtype=torch.float64, device=dev)
+    Y = torch.randn(A.m, L, dtype=torch.float64, device=dev)
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    hbm = json.load(open(peaks_path)).get("hbm_gbs", 6780.4) if os.path.exists(peaks_path) else 6780.4
+    X32, Y32 = X.float(), Y.float()
+    out = {}
+    for name, fn, rows, e in (("A_X", lambda: M.spmm(X), A.m, 8), ("At_Y", lambda: M.spmm(Y, transpose=True), A.n, 8),
+                              ("A_X_fp32", lambda: M.spmm_f32(X32), A.m, 4),
+                              ("At_Y_fp32", lambda: M.spmm_f32(Y32, transpose=True), A.n, 4)):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        byts = (e + 4.0) * A.nnz + 8.0 * (rows + 1) + e * L * (A.m + A.n)
+        flops = 2.0 * A.nnz * L
+        out[name] = {"ms": ms, "algorithmic_bytes": byts, "GB_per_s": byts / ms / 1e6, "frac_of_hbm": byts / ms / 1e6 / hbm,
+                     "TFLOP_per_s": flops / ms / 1e9}
+    M.close()
+    ctx.close()
+    out["description"] = (f"2000000x1000000 CSR (nnz {A.nnz}, 62500 permuted 32x16 blocks), L = 32, FP64; "
+                          f"HBM peak {hbm} GB/s (measured copy)")
+    return out
+
+
 def measure_table2(B, dev):
     """Exp III (Sec. 4.3, Tables 1-2) on the digit-image stand-in: the eight intervals of
     Table 1 (exterior [a, 1.01] with t = 21, 40, 79, 153; interior windows of t = 17, 39, 85,
@@ -578,6 +625,8 @@ def main():
                     help="skip the secondary 64-problem batched measurement")
     ap.add_argument("--no-serving", dest="serving", action="store_false",
                     help="skip the secondary Poisson-arrival serving measurement")
+    ap.add_argument("--no-spmm", dest="spmm", action="store_false",
+                    help="skip the secondary full-scale SpMM bandwidth measurement")
     ap.add_argument("--table2", action="store_true",
                     help="also run the eight Exp III intervals on the digit-image stand-in (minutes)")
     args = ap.parse_args()

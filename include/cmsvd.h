@@ -185,6 +185,14 @@ int cmsvd_spmm(cmsvd_matrix* A, int transpose, int64_t L, const double* X, int64
                double* Y, int64_t ldy);
 
 /*
+ * The same product in FP32, the SpMM of the mixed-precision Krylov path: FP32 values of A
+ * (a copy made on the device at the first call and kept with the matrix), FP32 X and Y,
+ * FP32 accumulation in each row's storage order. Layouts and errors as cmsvd_spmm.
+ */
+int cmsvd_spmm_f32(cmsvd_matrix* A, int transpose, int64_t L, const float* X, int64_t ldx,
+                   float* Y, int64_t ldy);
+
+/*
  * Quadrature of Sec. 4 for j = 1..N/2 (the points with Im > 0, Sec. 3.1),
  * computed on the device. Outputs are host arrays of N/2 complex values,
  * interleaved (re, im): shift[j] = z_j (linear) or exp(t_j) (NT);

@@ -67,6 +67,7 @@ _SIGS = {
     "cmsvd_csr_destroy": (C.c_int, [_P]),
     "cmsvd_csr_shape": (C.c_int, [_P, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I64)]),
     "cmsvd_spmm": (C.c_int, [_P, C.c_int, _I64, _P, _I64, _P, _I64]),
+    "cmsvd_spmm_f32": (C.c_int, [_P, C.c_int, _I64, _P, _I64, _P, _I64]),
     "cmsvd_quadrature": (C.c_int, [_P, C.c_double, C.c_double, C.c_int32, C.c_int32, C.c_double, _P, _P, _P]),
     "cmsvd_workspace_size": (C.c_int, [_P, C.POINTER(cmsvd_params), C.POINTER(C.c_size_t)]),
     "cmsvd_gram_workspace_size": (C.c_int, [_P, _I64, C.c_int32, C.c_int32, C.POINTER(C.c_size_t)]),
@@ -193,6 +194,12 @@ def cmsvd_spmm(A: int, transpose: bool, X, Y) -> None:
     """Y = A X (or A^T X); X, Y float64 CUDA tensors, row-major blocks."""
     L = X.shape[1]
     _check(lib().cmsvd_spmm(_P(A), int(transpose), L, _ptr(X), X.stride(0), _ptr(Y), Y.stride(0)), "cmsvd_spmm")
+
+
+def cmsvd_spmm_f32(A: int, transpose: bool, X, Y) -> None:
+    """Y = A X (or A^T X) in FP32; X, Y float32 CUDA tensors, row-major blocks."""
+    L = X.shape[1]
+    _check(lib().cmsvd_spmm_f32(_P(A), int(transpose), L, _ptr(X), X.stride(0), _ptr(Y), Y.stride(0)), "cmsvd_spmm_f32")
 
 
 def cmsvd_quadrature(ctx: int, a: float, b: float, N: int, variant="linear", alpha: float = 0.1):
@@ -456,6 +463,13 @@ class Matrix:
         rows = self.n if transpose else self.m
         Y = torch.empty((rows, X.shape[1]), dtype=torch.float64, device=X.device)
         cmsvd_spmm(self.handle, transpose, X, Y)
+        return Y
+
+    def spmm_f32(self, X, transpose: bool = False):
+        import torch
+        rows = self.n if transpose else self.m
+        Y = torch.empty((rows, X.shape[1]), dtype=torch.float32, device=X.device)
+        cmsvd_spmm_f32(self.handle, transpose, X, Y)
         return Y
 
     def moments(self, a, b, p: cmsvd_params, V_in, workspace=None):

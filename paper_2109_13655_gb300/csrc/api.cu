@@ -334,6 +334,15 @@ int cmsvd_spmm(cmsvd_matrix* A, int transpose, int64_t L, const double* X, int64
     return leave(A->ctx);
 }
 
+int cmsvd_spmm_f32(cmsvd_matrix* A, int transpose, int64_t L, const float* X, int64_t ldx, float* Y, int64_t ldy) {
+    if (!A || !X || !Y) { set_error("NULL argument"); return CMSVD_INVALID_ARG; }
+    if (L < 1 || L > 4096 || ldx < L || ldy < L) { set_error("need 1 <= L <= 4096, ldx >= L, ldy >= L"); return CMSVD_INVALID_ARG; }
+    CM_TRY(enter(A->ctx));
+    CM_TRY(csr_make_fp32(A));
+    CM_TRY(spmm(transpose ? A->At : A->A, (int)L, X, ldx, Y, ldy, A->ctx->s));
+    return leave(A->ctx);
+}
+
 int cmsvd_quadrature(cmsvd_context* ctx, double a, double b, int32_t N, int32_t variant, double alpha, double* shift,
                      double* weight, double* scaled) {
     if (!ctx) { set_error("NULL context"); return CMSVD_INVALID_ARG; }

@@ -120,7 +120,54 @@ __global__ void k_max_row(const int64_t* __restrict__ rowptr, int64_t m, unsigne
     if ((threadIdx.x & 31) == 0 && best) atomicMax(out, best);
 }
 
-// Longest row of a CSR already on the device (sets A->max_row).
+__global__ void k_first_col(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx, int64_t m,
+                            int32_t* __restrict__ key, int32_t* __restrict__ idx) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < m; r += (int64_t)gridDim.x * blockDim.x) {
+        key[r] = rowptr[r + 1] > rowptr[r] ? colidx[rowptr[r]] : 0x7fffffff;
+        idx[r] = (int32_t)r;
+    }
+}
+
+// SpMM processing order: rows sorted (stably) by their first column, so that rows that
+// gather the same rows of X run close together and find them in L2 (a permuted block
+// matrix otherwise re-reads X from DRAM for every row). Each row's own sum is unchanged,
+// so the SpMM result is bitwise the same in any order.
+static int csr_row_order(cmsvd_context* ctx, Csr* A) {
+    if (A->m <= 1 || A->m >= ((int64_t)1 << 31)) return CMSVD_OK;
+    const int m = (int)A->m;
+    int32_t *key = nullptr, *key_out = nullptr, *idx = nullptr;
+    void* tmp = nullptr;
+    size_t tmp_bytes = 0;
+    int st = CMSVD_OK;
+    auto chk = [&](cudaError_t e, const char* w) { if (e != cudaSuccess && st == CMSVD_OK) st = cuda_fail(e, w, __FILE__, __LINE__); };
+    chk(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, key, key_out, idx, A->row_order, m, 0, 31, ctx->s),
+        "row order sort size");
+    if (st == CMSVD_OK && (cudaMalloc(&key, sizeof(int32_t) * m) != cudaSuccess ||
+                           cudaMalloc(&key_out, sizeof(int32_t) * m) != cudaSuccess ||
+                           cudaMalloc(&idx, sizeof(int32_t) * m) != cudaSuccess ||
+                           cudaMalloc(&A->row_order, sizeof(int32_t) * m) != cudaSuccess ||
+                           cudaMalloc(&tmp, tmp_bytes > 0 ? tmp_bytes : 1) != cudaSuccess)) {
+        cudaGetLastError();
+        set_error("out of device memory for the SpMM row order");
+        st = CMSVD_OUT_OF_MEMORY;
+    }
+    if (st == CMSVD_OK) {
+        k_first_col<<<grid_for(A->m, 256, ctx->sm_count * 8), 256, 0, ctx->s>>>(A->rowptr, A->colidx, A->m, key, idx);
+        chk(cudaGetLastError(), "k_first_col");
+        chk(cub::DeviceRadixSort::SortPairs(tmp, tmp_bytes, key, key_out, idx, A->row_order, m, 0, 31, ctx->s),
+            "row order sort");
+        chk(cudaStreamSynchronize(ctx->s), "sync");
+    }
+    for (void* ptr : {(void*)key, (void*)key_out, (void*)idx, tmp})
+        if (ptr) cudaFree(ptr);
+    if (st != CMSVD_OK && A->row_order) {
+        cudaFree(A->row_order);
+        A->row_order = nullptr;
+    }
+    return st;
+}
+
+// Longest row of a CSR already on the device (sets A->max_row), and the SpMM row order.
 static int csr_row_stats(cmsvd_context* ctx, Csr* A) {
     unsigned long long* d = nullptr;
     CM_CUDA(cudaMalloc(&d, sizeof(unsigned long long)));
@@ -135,6 +182,7 @@ static int csr_row_stats(cmsvd_context* ctx, Csr* A) {
     memcpy(&h, ctx->pinned, sizeof(h));
     cudaFree(d);
     A->max_row = (int64_t)h;
+    if (st == CMSVD_OK) st = csr_row_order(ctx, A);
     return st;
 }
 
@@ -187,7 +235,8 @@ void csr_free(Csr* A) {
     if (A->colidx) cudaFree(A->colidx);
     if (A->vals) cudaFree(A->vals);
     if (A->vals_f) cudaFree(A->vals_f);
-    A->rowptr = nullptr; A->colidx = nullptr; A->vals = nullptr; A->vals_f = nullptr;
+    if (A->row_order) cudaFree(A->row_order);
+    A->rowptr = nullptr; A->colidx = nullptr; A->vals = nullptr; A->vals_f = nullptr; A->row_order = nullptr;
 }
 
 __global__ void k_to_fp32(const double* __restrict__ x, int64_t n, float* __restrict__ y) {
@@ -342,12 +391,13 @@ template <typename T, int LPR, int CPL>
 __global__ void __launch_bounds__(256) k_spmm(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
                                               const T* __restrict__ vals, int64_t rows, int L,
                                               const T* __restrict__ X, int64_t ldx, T* __restrict__ Y,
-                                              int64_t ldy) {
+                                              int64_t ldy, const int32_t* __restrict__ order) {
     const int lane = threadIdx.x % LPR;
     const int64_t group = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LPR;
     const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / LPR;
     const unsigned mask = LPR == 32 ? 0xffffffffu : (((1u << LPR) - 1u) << ((threadIdx.x & 31) / LPR * LPR));
-    for (int64_t r = group; r < rows; r += ngroups) {
+    for (int64_t rr = group; rr < rows; rr += ngroups) {
+        const int64_t r = order ? (int64_t)order[rr] : rr;
         const int64_t s = rowptr[r], e = rowptr[r + 1];
         for (int c0 = 0; c0 < L; c0 += LPR * CPL) {
             T acc[CPL];
@@ -383,12 +433,13 @@ template <typename T, int LPR, int CPL>
 __global__ void __launch_bounds__(256) k_spmm_rowcta(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
                                                      const T* __restrict__ vals, int64_t rows, int L,
                                                      const T* __restrict__ X, int64_t ldx, T* __restrict__ Y,
-                                                     int64_t ldy) {
+                                                     int64_t ldy, const int32_t* __restrict__ order) {
     constexpr int G = 256 / LPR;
     __shared__ T part[G][LPR * CPL];
     const int lane = threadIdx.x % LPR, g = threadIdx.x / LPR;
     const unsigned mask = LPR == 32 ? 0xffffffffu : (((1u << LPR) - 1u) << ((threadIdx.x & 31) / LPR * LPR));
-    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+    for (int64_t rr = blockIdx.x; rr < rows; rr += gridDim.x) {
+        const int64_t r = order ? (int64_t)order[rr] : rr;
         const int64_t rs = rowptr[r], re = rowptr[r + 1];
         const int64_t slice = (re - rs + G - 1) / G;
         const int64_t s = rs + g * slice < re ? rs + g * slice : re;
@@ -436,21 +487,21 @@ static int spmm_t(const Csr& A, const T* vals, int L, const T* X, int64_t ldx, T
     const int dev_sms = 152;
     if (A.max_row > 2048) {
         const unsigned grid = (unsigned)(A.m < dev_sms * 8 ? A.m : dev_sms * 8);
-        if (L <= 8) k_spmm_rowcta<T, 8, 1><<<grid, 256, 0, s>>>(A.rowptr, A.colidx, vals, A.m, L, X, ldx, Y, ldy);
-        else if (L <= 16) k_spmm_rowcta<T, 16, 1><<<grid, 256, 0, s>>>(A.rowptr, A.colidx, vals, A.m, L, X, ldx, Y, ldy);
-        else if (L <= 32) k_spmm_rowcta<T, 32, 1><<<grid, 256, 0, s>>>(A.rowptr, A.colidx, vals, A.m, L, X, ldx, Y, ldy);
-        else k_spmm_rowcta<T, 32, 4><<<grid, 256, 0, s>>>(A.rowptr, A.colidx, vals, A.m, L, X, ldx, Y, ldy);
+        if (L <= 8) k_spmm_rowcta<T, 8, 1><<<grid, 256, 0, s>>>(A.rowptr, A.colidx, vals, A.m, L, X, ldx, Y, ldy, A.row_order);
+        else if (L <= 16) k_spmm_rowcta<T, 16, 1><<<grid, 256, 0, s>>>(A.rowptr, A.colidx, vals, A.m, L, X, ldx, Y, ldy, A.row_order);
+        else if (L <= 32) k_spmm_rowcta<T, 32, 1><<<grid, 256, 0, s>>>(A.rowptr, A.colidx, vals, A.m, L, X, ldx, Y, ldy, A.row_order);
+        else k_spmm_rowcta<T, 32, 4><<<grid, 256, 0, s>>>(A.rowptr, A.colidx, vals, A.m, L, X, ldx, Y, ldy, A.row_order);
         CM_LAUNCH();
         return CMSVD_OK;
     }
     if (L <= 8) {
-        k_spmm<T, 8, 1><<<grid_for(A.m, 256 / 8, dev_sms * 32), 256, 0, s>>>(A.rowptr, A.colidx, vals, A.m, L, X, ldx, Y, ldy);
+        k_spmm<T, 8, 1><<<grid_for(A.m, 256 / 8, dev_sms * 32), 256, 0, s>>>(A.rowptr, A.colidx, vals, A.m, L, X, ldx, Y, ldy, A.row_order);
     } else if (L <= 16) {
-        k_spmm<T, 16, 1><<<grid_for(A.m, 256 / 16, dev_sms * 32), 256, 0, s>>>(A.rowptr, A.colidx, vals, A.m, L, X, ldx, Y, ldy);
+        k_spmm<T, 16, 1><<<grid_for(A.m, 256 / 16, dev_sms * 32), 256, 0, s>>>(A.rowptr, A.colidx, vals, A.m, L, X, ldx, Y, ldy, A.row_order);
     } else if (L <= 32) {
-        k_spmm<T, 32, 1><<<grid_for(A.m, 8, dev_sms * 32), 256, 0, s>>>(A.rowptr, A.colidx, vals, A.m, L, X, ldx, Y, ldy);
+        k_spmm<T, 32, 1><<<grid_for(A.m, 8, dev_sms * 32), 256, 0, s>>>(A.rowptr, A.colidx, vals, A.m, L, X, ldx, Y, ldy, A.row_order);
     } else {
-        k_spmm<T, 32, 4><<<grid_for(A.m, 8, dev_sms * 32), 256, 0, s>>>(A.rowptr, A.colidx, vals, A.m, L, X, ldx, Y, ldy);
+        k_spmm<T, 32, 4><<<grid_for(A.m, 8, dev_sms * 32), 256, 0, s>>>(A.rowptr, A.colidx, vals, A.m, L, X, ldx, Y, ldy, A.row_order);
     }
     CM_LAUNCH();
     return CMSVD_OK;

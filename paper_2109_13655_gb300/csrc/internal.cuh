@@ -63,6 +63,7 @@ struct Csr {
     double* vals = nullptr;      // device, nnz
     float* vals_f = nullptr;     // device, nnz: FP32 copy for the mixed-precision Krylov path (made on demand)
     int64_t max_row = 0;         // longest row (nonzeros); long rows switch the SpMM to one CTA per row
+    int32_t* row_order = nullptr; // device, m: rows sorted by their first column (SpMM processing order)
 };
 
 struct Components {             // connected components of the column graph (A^T A)

@@ -89,6 +89,29 @@ def test_spmm_long_rows(B, ctx, L):
     M.close()
 
 
+@pytest.mark.parametrize("L", [1, 16, 33, 120])
+def test_spmm_f32_parity(B, ctx, L):
+    """FP32 SpMM (mixed path): FP32 values and accumulation in row order. Bound: a sum of
+    k products of FP32-rounded operands is within ~(k + 2) u32 sum |a||x| of the exact sum
+    (rows here hold at most 17 nonzeros; long rows of ~5000 in the transpose below)."""
+    A = ragged_sparse(777, 301, seed=L)
+    M = B.Matrix.from_csr(ctx, A)
+    X = np.random.default_rng(1).standard_normal((301, L)).astype(np.float32)
+    Y = M.spmm_f32(torch.from_numpy(X).cuda()).cpu().numpy().astype(np.float64)
+    Ad = A.to_dense()
+    ref = Ad @ X.astype(np.float64)
+    scale = np.abs(Ad) @ np.abs(X.astype(np.float64)) + 1e-300
+    assert np.max(np.abs(Y - ref) / scale) < 20 * 2.0 ** -24
+    Bl = synth.random_sparse(20000, 20, 5, seed=L)
+    Ml = B.Matrix.from_csr(ctx, Bl)
+    Z = np.random.default_rng(2).standard_normal((20000, L)).astype(np.float32)
+    Yt = Ml.spmm_f32(torch.from_numpy(Z).cuda(), transpose=True).cpu().numpy().astype(np.float64)
+    Bd = Bl.to_dense()
+    assert np.max(np.abs(Yt - Bd.T @ Z) / (np.abs(Bd.T) @ np.abs(Z) + 1e-300)) < 400 * 2.0 ** -24
+    M.close()
+    Ml.close()
+
+
 def test_spmm_transpose_deterministic(B, ctx):
     A = synth.random_sparse(3000, 1000, 12, seed=5)
     M = B.Matrix.from_csr(ctx, A)
