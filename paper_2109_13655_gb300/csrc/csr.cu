@@ -387,6 +387,42 @@ int csr_transpose(cmsvd_context* ctx, const Csr& A, Csr* At) {
 __device__ __forceinline__ double fma_rn_t(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float fma_rn_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
+// One chunk of up to LPR nonzeros of a row, broadcast from the lanes that loaded them:
+// the X rows of SPMM_ILP nonzeros are gathered before their multiply-adds, so that many
+// gathers are in flight (a gather whose address comes from a shuffle otherwise waits for
+// the previous multiply-add). The multiply-adds stay in the row's storage order.
+constexpr int SPMM_ILP = 8;
+template <typename T, int LPR, int CPL>
+__device__ __forceinline__ void spmm_chunk(unsigned mask, int32_t mc, T mv, int cnt, const T* __restrict__ X,
+                                           int64_t ldx, int c0, int lane, int L, T (&acc)[CPL]) {
+    int k0 = 0;
+    for (; k0 + SPMM_ILP <= cnt; k0 += SPMM_ILP) {   // full groups: gathers first, then the multiply-adds
+        T xv[SPMM_ILP][CPL];
+        T vv[SPMM_ILP];
+#pragma unroll
+        for (int u = 0; u < SPMM_ILP; ++u) {
+            const int32_t col = __shfl_sync(mask, mc, k0 + u, LPR);
+            vv[u] = __shfl_sync(mask, mv, k0 + u, LPR);
+            const T* xr = X + (int64_t)col * ldx + c0 + lane;
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) xv[u][q] = c0 + lane + q * LPR < L ? __ldg(xr + q * LPR) : (T)0;
+        }
+#pragma unroll
+        for (int u = 0; u < SPMM_ILP; ++u)
+#pragma unroll
+            for (int q = 0; q < CPL; ++q)
+                if (c0 + lane + q * LPR < L) acc[q] = fma_rn_t(vv[u], xv[u][q], acc[q]);
+    }
+    for (; k0 < cnt; ++k0) {                          // the rest (short rows take only this path)
+        const int32_t col = __shfl_sync(mask, mc, k0, LPR);
+        const T v = __shfl_sync(mask, mv, k0, LPR);
+        const T* xr = X + (int64_t)col * ldx + c0 + lane;
+#pragma unroll
+        for (int q = 0; q < CPL; ++q)
+            if (c0 + lane + q * LPR < L) acc[q] = fma_rn_t(v, __ldg(xr + q * LPR), acc[q]);
+    }
+}
+
 template <typename T, int LPR, int CPL>
 __global__ void __launch_bounds__(256) k_spmm(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
                                               const T* __restrict__ vals, int64_t rows, int L,
@@ -409,14 +445,7 @@ __global__ void __launch_bounds__(256) k_spmm(const int64_t* __restrict__ rowptr
                 T mv = (T)0;
                 if (p < e) { mc = colidx[p]; mv = vals[p]; }
                 const int cnt = (int)((e - p0) < LPR ? (e - p0) : LPR);
-                for (int k = 0; k < cnt; ++k) {
-                    const int32_t col = __shfl_sync(mask, mc, k, LPR);
-                    const T v = __shfl_sync(mask, mv, k, LPR);
-                    const T* xr = X + (int64_t)col * ldx + c0 + lane;
-#pragma unroll
-                    for (int q = 0; q < CPL; ++q)
-                        if (c0 + lane + q * LPR < L) acc[q] = fma_rn_t(v, __ldg(xr + q * LPR), acc[q]);
-                }
+                spmm_chunk<T, LPR, CPL>(mask, mc, mv, cnt, X, ldx, c0, lane, L, acc);
             }
 #pragma unroll
             for (int q = 0; q < CPL; ++q)
@@ -454,14 +483,7 @@ __global__ void __launch_bounds__(256) k_spmm_rowcta(const int64_t* __restrict__
                 T mv = (T)0;
                 if (p < e) { mc = colidx[p]; mv = vals[p]; }
                 const int cnt = (int)((e - p0) < LPR ? (e - p0) : LPR);
-                for (int k = 0; k < cnt; ++k) {
-                    const int32_t col = __shfl_sync(mask, mc, k, LPR);
-                    const T v = __shfl_sync(mask, mv, k, LPR);
-                    const T* xr = X + (int64_t)col * ldx + c0 + lane;
-#pragma unroll
-                    for (int q = 0; q < CPL; ++q)
-                        if (c0 + lane + q * LPR < L) acc[q] = fma_rn_t(v, __ldg(xr + q * LPR), acc[q]);
-                }
+                spmm_chunk<T, LPR, CPL>(mask, mc, mv, cnt, X, ldx, c0, lane, L, acc);
             }
 #pragma unroll
             for (int q = 0; q < CPL; ++q) part[g][lane + q * LPR] = acc[q];
