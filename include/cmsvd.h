@@ -40,7 +40,7 @@ typedef enum cmsvd_status {
     CMSVD_BREAKDOWN = 6,            /* NaN/Inf in a recurrence or a non-positive Cholesky pivot */
     CMSVD_SUBSPACE_SATURATED = 7,   /* warning: numerical rank of S^ equals L*M (Thm. 1: t may exceed L*M) */
     CMSVD_CUDA_ERROR = 8,           /* a CUDA runtime call failed */
-    CMSVD_NOT_SUPPORTED = 9,        /* valid request outside what this build implements */
+    CMSVD_NOT_SUPPORTED = 9,        /* valid request outside what this library implements */
     CMSVD_PENDING = 10              /* serving: the request has not finished yet */
 } cmsvd_status;
 
