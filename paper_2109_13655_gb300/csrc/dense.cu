@@ -15,7 +15,7 @@ namespace cmsvd {
 constexpr int GT = 64;   // output tile
 constexpr int GK = 16;   // rows per slab
 
-__global__ void __launch_bounds__(256) k_gram_partial(const double* __restrict__ X, int64_t ldx, int c1,
+__global__ void __launch_bounds__(256, 4) k_gram_partial(const double* __restrict__ X, int64_t ldx, int c1,
                                                       const double* __restrict__ Y, int64_t ldy, int c2, int64_t n,
                                                       int64_t rows_per_chunk, int sym, double* __restrict__ partials) {
     __shared__ double Xs[GK][GT];
@@ -30,6 +30,51 @@ __global__ void __launch_bounds__(256) k_gram_partial(const double* __restrict__
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    if (sym && blockIdx.x == blockIdx.y) {
+        // Diagonal tile of a symmetric Gram: only its 136 upper 4 x 4 blocks are computed,
+        // one per thread in row-major order of the upper triangle, so warps 5-7 skip the
+        // multiply-adds (GB300 charges an FP64 warp instruction whatever its active lanes).
+        // The lower entries are mirrored when the partials are summed. Every computed entry
+        // runs the same multiply-adds in the same order as in the general path.
+        const bool active = tid < 136;
+        int by = 0, rem = tid;
+        if (active)
+            while (rem >= 16 - by) { rem -= 16 - by; ++by; }
+        const int bx = by + rem;
+        for (int64_t r = r0; r < r1; r += GK) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int e = tid + 256 * q, rr = e / GT, cc = e % GT;
+                Xs[rr][cc] = (r + rr < r1 && ti + cc < c1) ? X[(r + rr) * ldx + ti + cc] : 0.0;
+            }
+            __syncthreads();
+            if (active) {
+#pragma unroll
+                for (int k = 0; k < GK; ++k) {
+                    double a[4], b[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) a[i] = Xs[k][4 * by + i];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) b[j] = Xs[k][4 * bx + j];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) acc[i][j] = __fma_rn(a[i], b[j], acc[i][j]);
+                }
+            }
+            __syncthreads();
+        }
+        if (active) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int gi = ti + 4 * by + i, gj = tj + 4 * bx + j;
+                    if (gi < c1 && gj < c2) partials[((size_t)blockIdx.z * c1 + gi) * c2 + gj] = acc[i][j];
+                }
+        }
+        return;
+    }
     for (int64_t r = r0; r < r1; r += GK) {
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
@@ -70,7 +115,7 @@ __global__ void k_sum_partials(const double* __restrict__ partials, int nchunks,
     const int64_t count = (int64_t)c1 * c2;
     if (e >= count) return;
     int i = (int)(e / c2), j = (int)(e % c2);
-    if (sym && i / GT > j / GT) { const int t = i; i = j; j = t; }
+    if (sym && i > j) { const int t = i; i = j; j = t; }   // lower entries mirror the upper ones
     const int64_t src = (int64_t)i * c2 + j;
     double s = 0.0;
     for (int c = 0; c < nchunks; ++c) s += partials[(size_t)c * count + src];

@@ -140,6 +140,8 @@ def test_gram_parity(B, ctx, n, c1, c2):
     G2 = torch.empty_like(G)
     B.cmsvd_gram(ctx.handle, X, Y, G2, ws)
     assert torch.equal(G, G2)                                 # deterministic
+    if c1 == c2:
+        assert torch.equal(G, G.T)                            # symmetric Gram: exactly symmetric
 
 
 # ----------------------------------------------------------------------------- quadrature (row a1)
