@@ -1,8 +1,11 @@
 // Dense FP64 kernels of the Rayleigh-Ritz part (Alg. 1 steps 3-5):
 //   - Gram G = X^T Y of tall-skinny blocks (deterministic split-n reduction),
 //   - Z = X W for tall X and small W,
-//   - shifted CholeskyQR3 (X = Q R) used for the rank truncation of S^ (step 3)
-//     and for qr(A V~) (step 4),
+//   - Cholesky (one CTA, or a cooperative blocked form), triangular inverse,
+//   - the orthogonalization X = Q R of the rank truncation of S^ (step 3): two shifted
+//     CholeskyQR passes, deflation by a pivoted Cholesky, a congruence polish and one
+//     pass from the data; and of qr(A V~) (step 4): one Cholesky of the Gram when its
+//     rounding is provably negligible, else CholeskyQR2, else the deflated form,
 //   - one-sided Jacobi SVD of a small square matrix (SVD of R in step 3 and of B
 //     in step 5), which keeps the high relative accuracy of small singular values.
 // FP64 on this part runs on the FP64 pipe (no FP64 tensor-core path is used).
@@ -916,9 +919,10 @@ int cholqr_pass(OrthCtx& o, const double* Xin, int64_t ldi, int cc, bool shifted
 //   deflate = 0: when the first plain Cholesky succeeds and diag(R) spans less than
 //   1e5 (cond(X) well below 1/sqrt(u)), CholeskyQR2 is used (c' = c).
 //   Otherwise: two shifted CholeskyQR passes bring every direction of X whose
-//   singular value exceeds ~1e-14 ||X|| to O(1); the Gram of the result is
-//   eigen-decomposed and the directions left at rounding level are deflated; two
-//   plain passes restore orthogonality to working precision.
+//   singular value exceeds ~1e-14 ||X|| to O(1); a pivoted Cholesky of the Gram of the
+//   result deflates the directions left at rounding level; a congruence polish (from
+//   that same Gram) and one plain pass from the data restore orthogonality to working
+//   precision.
 int orth_qr(const double* X, int64_t ldx, int64_t n, int c, double* Q, double* R, int* c_out, double* scratch, int* ints,
             int deflate, cmsvd_context* ctx, double* Rcorr, bool r_from_gram) {
     cudaStream_t s = ctx->s;

@@ -1,7 +1,7 @@
 // Rayleigh-Ritz extraction, Alg. 1 / Alg. 2 steps 3-5:
-//   step 3  S^ = Q_S R_S (shifted CholeskyQR3), R_S = P_R Sigma_S W_R^T (Jacobi),
-//           keep sigma_S,i > delta sigma_S,1; V~ = U_S1 = Q_S P_R(:, 1:r)   (Eq. low-rank)
-//   step 4  A V~ = U~ B (shifted CholeskyQR3)                                (Eq. avub)
+//   step 3  S^ = Q_S R_S (orth_qr: shifted CholeskyQR, deflation), R_S = P_R Sigma_S W_R^T
+//           (Jacobi), keep sigma_S,i > delta sigma_S,1; V~ = U_S1 = Q_S P_R(:, 1:r)  (Eq. low-rank)
+//   step 4  A V~ = U~ B, B only (U~ p is formed as A v / phi)                   (Eq. avub)
 //   step 5  B = P Phi Q^T (Jacobi); candidates phi_i in [a, b] that pass the
 //           spurious test tau_i = q^T q / q^T Sigma_S1^{-1} q (Sec. 3.4.2);
 //           u = U~ p, v = V~ q; exact residuals ||A^T u - phi v||, ||A v - phi u||
