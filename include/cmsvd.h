@@ -311,7 +311,9 @@ int cmsvd_solve_batch(int count, cmsvd_matrix* const* A, const double* a, const 
  */
 typedef struct cmsvd_server cmsvd_server;
 int cmsvd_server_create(int slots, size_t hbm_budget, cmsvd_server** out);
-int cmsvd_server_destroy(cmsvd_server* s);   /* stops the workers; requests not started are dropped */
+/* Stops the workers (a running solve finishes first); requests not started are dropped.
+ * Call it only after every cmsvd_server_wait on this server has returned. */
+int cmsvd_server_destroy(cmsvd_server* s);
 /* Uploads, validates and registers a matrix (as cmsvd_csr_create); *id names it in requests. */
 int cmsvd_server_add_matrix(cmsvd_server* s, int64_t m, int64_t n, int64_t nnz, const int64_t* rowptr,
                             const int32_t* colidx, const double* vals, int vals_on_device, int* id);

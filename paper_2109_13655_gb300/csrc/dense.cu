@@ -867,8 +867,8 @@ int chol_launch(cmsvd_context* ctx, cudaStream_t s, const double* G, int c, doub
         CM_LAUNCH();
         return CMSVD_OK;
     }
-    static int per_sm = -1;
-    if (per_sm < 0) CM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_coop, 256, 0));
+    int per_sm = 0;   // queried per call: cheap, and safe when several host threads solve at once
+    CM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_chol_coop, 256, 0));
     int grid = ctx->sm_count < 128 ? ctx->sm_count : 128;
     if (per_sm * ctx->sm_count < grid) grid = per_sm * ctx->sm_count;
     if (grid < 1) { set_error("Cholesky grid cannot be co-resident"); return CMSVD_NOT_SUPPORTED; }
