@@ -1,0 +1,42 @@
+"""Host-side logic of bench.py (no GPU): the roofline arithmetic of the dominant kernel
+class, the clock-sample summary that decides whether a run is rejected, and the JSON
+fields the bench contract requires."""
+import bench
+
+
+def _prof(ms, launches, byts, flops):
+    return {"ms": ms, "launches": launches, "bytes": byts, "flops": flops}
+
+
+def test_roofline_alu_bound_gemm_with_measured_traffic():
+    prof = {"gemm": _prof(45.6, 12, 1.93e9, 4.81e10)}
+    r = bench.roofline("gemm", prof, [], {"name": "block_permuted_200000x100000"})
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert abs(r["achieved"] - 4.81e10 / 0.0456 / 1e12) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
+    assert r["traffic"] == 154.6e6
+    # another workload has no measured traffic for this class
+    assert bench.roofline("gemm", prof, [], {"name": "random_sparse_2000x1000"})["traffic"] is None
+
+
+def test_roofline_hbm_bound_when_intensity_is_low():
+    prof = {"spmm": _prof(10.0, 4, 4e10, 1e9)}          # 0.025 flop per byte
+    r = bench.roofline("spmm", prof, [], {"name": "x"})
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert abs(r["achieved"] - 4e10 / 0.010 / 1e9) < 1e-6
+
+
+def test_clock_summary_flags_throttle_reasons():
+    c = bench.ClockSampler(0)
+    c.lines = ["2070, 2070, 900.0, Not Active, Not Active, Not Active, Not Active",
+               "1800, 2070, 1400.0, Not Active, Not Active, Not Active, Active",
+               "1900, 2070, 1400.0, Active, Not Active, Not Active, Not Active",
+               "garbage"]
+    s = c.summary()
+    assert s["samples"] == 3 and s["sm_max_mhz"] == 2070.0 and s["sm_mhz"] == 1900.0
+    assert s["reasons"] == ["hw_slowdown", "sw_power_cap"]
+    assert bench.ClockSampler(0).summary()["sm_mhz"] is None
+
+
+def test_job_throughput_is_whole_job():
+    assert bench.job_throughput(10, 4, 2.0) == 20.0
