@@ -57,8 +57,11 @@ struct cmsvd_server {
     size_t budget = 0, in_use = 0;
     std::vector<cudaStream_t> streams;          // per slot: the stream its requests' copies run on
     std::vector<cmsvd_context*> ctx;
+    cudaStream_t ustream = nullptr;             // uploads of new matrices, apart from the slots,
+    cmsvd_context* uctx = nullptr;              // so that they never share a context with a solve
     std::vector<SrvMatrix> mats;
-    std::mutex mu;
+    std::mutex mu;                              // queue, requests, matrix table, budget
+    std::mutex umu;                             // uploads (the upload context)
     std::condition_variable cv_work, cv_done;
     std::deque<std::shared_ptr<SrvReq>> queue;
     std::map<int64_t, std::shared_ptr<SrvReq>> reqs;
@@ -73,7 +76,11 @@ void process(cmsvd_server* S, int slot, SrvReq& r) {
     using namespace cmsvd;
     cudaSetDevice(S->device);
     cudaStream_t s = S->streams[slot];
-    cmsvd_matrix* A = S->mats[r.mid].views[slot];
+    cmsvd_matrix* A = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);   // mats may grow while requests run
+        A = S->mats[r.mid].views[slot];
+    }
     const size_t vbytes = sizeof(double) * r.vin.size();
     void* ws = nullptr;
     double* vin_d = nullptr;
@@ -179,6 +186,15 @@ int cmsvd_server_create(int slots, size_t hbm_budget, cmsvd_server** out) {
         S->streams.push_back(st);
         S->ctx.push_back(c);
     }
+    {
+        int e = cudaStreamCreateWithFlags(&S->ustream, cudaStreamNonBlocking) == cudaSuccess
+                    ? cmsvd_context_create(S->ustream, &S->uctx) : CMSVD_CUDA_ERROR;
+        if (e != CMSVD_OK) {
+            cmsvd_server_destroy(S);
+            if (e == CMSVD_CUDA_ERROR) set_error("stream or context creation failed");
+            return e;
+        }
+    }
     for (int i = 0; i < slots; ++i) S->workers.emplace_back(worker, S, i);
     *out = S;
     return CMSVD_OK;
@@ -198,6 +214,8 @@ int cmsvd_server_destroy(cmsvd_server* S) {
     }
     for (auto* c : S->ctx) cmsvd_context_destroy(c);
     for (auto st : S->streams) cudaStreamDestroy(st);
+    if (S->uctx) cmsvd_context_destroy(S->uctx);
+    if (S->ustream) cudaStreamDestroy(S->ustream);
     delete S;
     return CMSVD_OK;
 }
@@ -207,10 +225,16 @@ int cmsvd_server_add_matrix(cmsvd_server* S, int64_t m, int64_t n, int64_t nnz, 
     using namespace cmsvd;
     if (!S || !id) { set_error("NULL argument"); return CMSVD_INVALID_ARG; }
     cmsvd_matrix* base = nullptr;
-    CM_TRY(cmsvd_csr_create(S->ctx[0], m, n, nnz, rowptr, colidx, vals, vals_on_device, &base));
+    std::lock_guard<std::mutex> ulk(S->umu);   // one upload at a time on the upload context
+    CM_TRY(cmsvd_csr_create(S->uctx, m, n, nnz, rowptr, colidx, vals, vals_on_device, &base));
     // build what solves would otherwise create lazily, so that the per-slot views only read it
     int st = components_build(base);
     if (st == CMSVD_OK) st = csr_make_fp32(base);
+    // the slots' streams read these arrays without waiting on the upload stream
+    if (st == CMSVD_OK && cudaStreamSynchronize(S->uctx->s) != cudaSuccess) {
+        set_error("upload of the matrix failed");
+        st = CMSVD_CUDA_ERROR;
+    }
     if (st != CMSVD_OK) { cmsvd_csr_destroy(base); return st; }
     SrvMatrix sm;
     sm.base = base;
@@ -243,9 +267,13 @@ int cmsvd_server_submit(cmsvd_server* S, int id, double a, double b, const cmsvd
                         int64_t* ticket) {
     using namespace cmsvd;
     if (!S || !p || !V_in_host || !ticket) { set_error("NULL argument"); return CMSVD_INVALID_ARG; }
-    if (id < 0 || id >= (int)S->mats.size()) { set_error("unknown matrix id %d", id); return CMSVD_INVALID_ARG; }
+    cmsvd_matrix* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (id < 0 || id >= (int)S->mats.size()) { set_error("unknown matrix id %d", id); return CMSVD_INVALID_ARG; }
+        base = S->mats[id].base;
+    }
     auto r = std::make_shared<SrvReq>();
-    cmsvd_matrix* base = S->mats[id].base;
     size_t ws = 0;
     CM_TRY(cmsvd_workspace_size(base, p, &ws));
     if (p->L < 1 || p->L > 128) { set_error("L must be in [1, 128]"); return CMSVD_INVALID_ARG; }
