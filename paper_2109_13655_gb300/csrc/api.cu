@@ -2,9 +2,7 @@
 #include "internal.cuh"
 #include <cmath>
 #include <cstdlib>
-#include <map>
 #include <new>
-#include <tuple>
 
 namespace cmsvd {
 const char* last_error();
@@ -14,38 +12,6 @@ int rayleigh_ritz(cmsvd_matrix* M, const double* S, int64_t lds, int c, double a
 }  // namespace cmsvd
 
 using namespace cmsvd;
-
-// ----------------------------------------------------------------------------- graph cache
-// Instantiated graphs keyed by the buffers and shape they were captured for; a
-// graph is only replayed for a call with the same buffers, which are valid then.
-namespace {
-using GraphKey = std::tuple<const void*, const void*, const void*, int, int>;
-using GraphMap = std::map<GraphKey, cudaGraphExec_t>;
-}  // namespace
-
-namespace cmsvd {
-cudaGraphExec_t graph_cache_get(cmsvd_context* ctx, const void* a, const void* b, const void* c, int x, int y) {
-    if (!ctx->graphs) return nullptr;
-    auto* m = (GraphMap*)ctx->graphs;
-    auto it = m->find(GraphKey(a, b, c, x, y));
-    return it == m->end() ? nullptr : it->second;
-}
-void graph_cache_put(cmsvd_context* ctx, const void* a, const void* b, const void* c, int x, int y, cudaGraphExec_t g) {
-    if (!ctx->graphs) ctx->graphs = new (std::nothrow) GraphMap();
-    auto* m = (GraphMap*)ctx->graphs;
-    if (!m) { cudaGraphExecDestroy(g); return; }
-    if (m->size() >= 64) graph_cache_clear(ctx), m = (GraphMap*)(ctx->graphs = new (std::nothrow) GraphMap());
-    if (!m) { cudaGraphExecDestroy(g); return; }
-    (*m)[GraphKey(a, b, c, x, y)] = g;
-}
-void graph_cache_clear(cmsvd_context* ctx) {
-    auto* m = (GraphMap*)ctx->graphs;
-    if (!m) return;
-    for (auto& kv : *m) cudaGraphExecDestroy(kv.second);
-    delete m;
-    ctx->graphs = nullptr;
-}
-}  // namespace cmsvd
 
 namespace {
 
@@ -273,7 +239,6 @@ int cmsvd_context_create(void* stream, cmsvd_context** out) {
 int cmsvd_context_destroy(cmsvd_context* c) {
     if (!c) return CMSVD_OK;
     if (c->s) cudaStreamSynchronize(c->s);
-    graph_cache_clear(c);
     if (c->s) cudaStreamDestroy(c->s);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
     if (c->ev_out) cudaEventDestroy(c->ev_out);

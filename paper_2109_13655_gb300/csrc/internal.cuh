@@ -92,7 +92,6 @@ struct cmsvd_context {
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     int sm_count = 0;
     int* pinned = nullptr;             // host-pinned flags for polling
-    void* graphs = nullptr;            // cache of instantiated graphs (api.cu)
 };
 
 struct cmsvd_matrix {
@@ -203,8 +202,5 @@ int orth_qr(const double* X, int64_t ldx, int64_t n, int c, double* Q, double* R
 // jac_ctl: 64 device words of scratch for the cooperative sweeps.
 int jacobi_svd(const double* Bm, int brows, int bcols, int trans, double* Xc, double* V, double* sv, int* perm,
                int* flag2, cmsvd_context* ctx, double tol, unsigned* jac_ctl);
-cudaGraphExec_t graph_cache_get(cmsvd_context* ctx, const void* a, const void* b, const void* c, int x, int y);
-void graph_cache_put(cmsvd_context* ctx, const void* a, const void* b, const void* c, int x, int y, cudaGraphExec_t g);
-void graph_cache_clear(cmsvd_context* ctx);
 
 }  // namespace cmsvd

@@ -22,7 +22,7 @@ namespace {
 using Clock = std::chrono::steady_clock;
 
 struct SrvMatrix {
-    cmsvd_matrix* base = nullptr;               // owns the device data (created on slot 0)
+    cmsvd_matrix* base = nullptr;               // owns the device data (made on the upload context)
     std::vector<cmsvd_matrix*> views;           // one shallow copy per slot, bound to its context
     size_t bytes = 0;
 };
