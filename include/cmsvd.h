@@ -314,7 +314,9 @@ int cmsvd_server_create(int slots, size_t hbm_budget, cmsvd_server** out);
 /* Stops the workers (a running solve finishes first); requests not started are dropped.
  * Call it only after every cmsvd_server_wait on this server has returned. */
 int cmsvd_server_destroy(cmsvd_server* s);
-/* Uploads, validates and registers a matrix (as cmsvd_csr_create); *id names it in requests. */
+/* Uploads, validates and registers a matrix (as cmsvd_csr_create); *id names it in requests.
+ * Safe to call while requests run. CMSVD_OUT_OF_MEMORY (nothing registered) when the matrix
+ * does not fit in the budget beside the resident matrices and the largest queued request. */
 int cmsvd_server_add_matrix(cmsvd_server* s, int64_t m, int64_t n, int64_t nnz, const int64_t* rowptr,
                             const int32_t* colidx, const double* vals, int vals_on_device, int* id);
 /* Queues a request; V_in (n x L, row-major, host memory) is copied. Returns at once with a

@@ -7,6 +7,7 @@
 // allocator for the length of the solve. Every solve is the same computation as a single
 // cmsvd_solve_interval call, so a result does not depend on the requests it ran beside.
 #include "internal.cuh"
+#include <algorithm>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -251,10 +252,16 @@ int cmsvd_server_add_matrix(cmsvd_server* S, int64_t m, int64_t n, int64_t nnz, 
         sm.views.push_back(v);
     }
     std::lock_guard<std::mutex> lk(S->mu);
-    if (S->in_use + sm.bytes > S->budget) {
+    // a queued request was admitted against the matrices resident at its submission; the new
+    // matrix must still leave it room, or the queue would stall behind it for good
+    size_t resident = 0, queued = 0;
+    for (auto& x : S->mats) resident += x.bytes;
+    for (auto& q : S->queue) queued = std::max(queued, q->ws);
+    if (S->in_use + sm.bytes > S->budget || resident + sm.bytes + queued > S->budget) {
         for (auto* x : sm.views) delete x;
         cmsvd_csr_destroy(base);
-        set_error("matrix of %zu bytes exceeds the remaining HBM budget", sm.bytes);
+        set_error("matrix of %zu bytes exceeds what the HBM budget leaves beside the resident matrices and queued requests",
+                  sm.bytes);
         return CMSVD_OUT_OF_MEMORY;
     }
     S->in_use += sm.bytes;   // resident matrices stay counted in in_use
