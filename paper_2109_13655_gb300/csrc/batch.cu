@@ -33,21 +33,26 @@ extern "C" int cmsvd_solve_batch(int count, cmsvd_matrix* const* A, const double
     }
     std::vector<std::vector<int>> work;
     for (auto& g : groups) work.push_back(g.second);
-    std::vector<std::string> errs(work.size());
+    std::vector<std::string> errs(count);   // per problem: the error text of its thread
     auto run = [&](size_t w) {
         for (int i : work[w]) {
             status[i] = cmsvd_solve_interval(A[i], a[i], b[i], p + i, V_in[i], workspace[i], ws_bytes[i], out + i);
-            if (!acceptable(status[i]) && errs[w].empty()) errs[w] = std::string("problem ") + std::to_string(i) + ": " + cmsvd_last_error();
+            if (!acceptable(status[i])) errs[i] = cmsvd_last_error();
         }
     };
     std::vector<std::thread> threads;
-    for (size_t w = 1; w < work.size(); ++w) threads.emplace_back(run, w);
+    for (size_t w = 1; w < work.size(); ++w) {
+        try {
+            threads.emplace_back(run, w);
+        } catch (...) {
+            run(w);   // no thread to be had: run this context's problems here
+        }
+    }
     if (!work.empty()) run(0);
     for (auto& t : threads) t.join();
     for (int i = 0; i < count; ++i) {
         if (!acceptable(status[i])) {
-            for (auto& e : errs)
-                if (!e.empty()) { set_error("%s", e.c_str()); break; }
+            set_error("problem %d: %s", i, errs[i].c_str());
             return status[i];
         }
     }

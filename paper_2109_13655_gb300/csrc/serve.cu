@@ -97,17 +97,24 @@ void process(cmsvd_server* S, int slot, SrvReq& r) {
         r.status = cmsvd_solve_interval(A, r.a, r.b, &r.p, vin_d, ws, r.ws, &res);
         if (!acceptable(r.status)) r.err = cmsvd_last_error();
         if (res) {
-            r.t = res->t;
-            r.m = res->m;
-            r.n = res->n;
-            r.sigma.resize(r.t);
-            r.U.resize((size_t)r.t * r.m);
-            r.V.resize((size_t)r.t * r.n);
-            r.ru.resize(r.t);
-            r.rv.resize(r.t);
-            r.tau.resize(r.t);
-            cmsvd_result_copy(res, r.sigma.data(), r.U.data(), r.V.data(), r.ru.data(), r.rv.data(), r.tau.data());
-            cmsvd_result_stats(res, &r.st);
+            try {
+                r.t = res->t;
+                r.m = res->m;
+                r.n = res->n;
+                r.sigma.resize(r.t);
+                r.U.resize((size_t)r.t * r.m);
+                r.V.resize((size_t)r.t * r.n);
+                r.ru.resize(r.t);
+                r.rv.resize(r.t);
+                r.tau.resize(r.t);
+                cmsvd_result_copy(res, r.sigma.data(), r.U.data(), r.V.data(), r.ru.data(), r.rv.data(), r.tau.data());
+                cmsvd_result_stats(res, &r.st);
+            } catch (...) {
+                r.t = 0;
+                r.sigma.clear(), r.U.clear(), r.V.clear(), r.ru.clear(), r.rv.clear(), r.tau.clear();
+                r.status = CMSVD_OUT_OF_MEMORY;
+                r.err = "host allocation of the result failed";
+            }
             cmsvd_result_destroy(res);
         }
     }
@@ -196,7 +203,13 @@ int cmsvd_server_create(int slots, size_t hbm_budget, cmsvd_server** out) {
             return e;
         }
     }
-    for (int i = 0; i < slots; ++i) S->workers.emplace_back(worker, S, i);
+    try {
+        for (int i = 0; i < slots; ++i) S->workers.emplace_back(worker, S, i);
+    } catch (...) {
+        cmsvd_server_destroy(S);   // joins the workers already started
+        set_error("could not start the worker threads");
+        return CMSVD_OUT_OF_MEMORY;
+    }
     *out = S;
     return CMSVD_OK;
 }
@@ -280,15 +293,21 @@ int cmsvd_server_submit(cmsvd_server* S, int id, double a, double b, const cmsvd
         if (id < 0 || id >= (int)S->mats.size()) { set_error("unknown matrix id %d", id); return CMSVD_INVALID_ARG; }
         base = S->mats[id].base;
     }
-    auto r = std::make_shared<SrvReq>();
     size_t ws = 0;
     CM_TRY(cmsvd_workspace_size(base, p, &ws));
     if (p->L < 1 || p->L > 128) { set_error("L must be in [1, 128]"); return CMSVD_INVALID_ARG; }
+    std::shared_ptr<SrvReq> r;
+    try {
+        r = std::make_shared<SrvReq>();
+        r->vin.assign(V_in_host, V_in_host + (size_t)base->A.n * p->L);
+    } catch (...) {
+        set_error("host allocation failed");
+        return CMSVD_OUT_OF_MEMORY;
+    }
     r->mid = id;
     r->a = a;
     r->b = b;
     r->p = *p;
-    r->vin.assign(V_in_host, V_in_host + (size_t)base->A.n * p->L);
     r->ws = ws + sizeof(double) * r->vin.size();
     std::lock_guard<std::mutex> lk(S->mu);
     size_t resident = 0;
