@@ -153,7 +153,9 @@ int cmsvd_params_default(cmsvd_params* p);
  * passed as void*; NULL means the legacy default stream). The stream is
  * borrowed, not owned. The library also creates one internal stream of its
  * own for graph capture; work on it is ordered after and before the caller's
- * stream by events, so callers only ever synchronize their own stream.
+ * stream by events, so callers only ever synchronize their own stream. This
+ * holds on error returns too: the caller's stream waits for whatever the failed
+ * call had already queued.
  */
 int cmsvd_context_create(void* stream, cmsvd_context** out);
 int cmsvd_context_destroy(cmsvd_context* ctx);   /* NULL is accepted */

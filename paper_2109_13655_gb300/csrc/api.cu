@@ -121,6 +121,33 @@ int leave(cmsvd_context* ctx) {
     return CMSVD_OK;
 }
 
+// An entry point's work runs on the context's internal stream between enter() and leave().
+// A Session joins the caller's stream back even when the call returns early with an error,
+// so that what the caller queues next (freeing its buffers, say) waits for the kernels
+// already queued on the internal stream.
+struct Session {
+    cmsvd_context* c = nullptr;
+    Session() = default;
+    Session(const Session&) = delete;
+    Session& operator=(const Session&) = delete;
+    ~Session() {
+        if (c) {
+            cudaEventRecord(c->ev_out, c->s);
+            cudaStreamWaitEvent(c->user, c->ev_out, 0);
+        }
+    }
+    int open(cmsvd_context* ctx) {
+        CM_TRY(enter(ctx));
+        c = ctx;
+        return CMSVD_OK;
+    }
+    int close() {
+        cmsvd_context* x = c;
+        c = nullptr;
+        return leave(x);
+    }
+};
+
 int ensure_norm(cmsvd_matrix* A, const cmsvd_params* p, Arena& ws, double* normA) {
     if (p->norm_A > 0.0) { *normA = p->norm_A; return CMSVD_OK; }
     if (A->norm_est <= 0.0) {
@@ -257,7 +284,8 @@ int cmsvd_csr_create(cmsvd_context* ctx, int64_t m, int64_t n, int64_t nnz, cons
         return CMSVD_INVALID_ARG;
     }
     if (!rowptr || (nnz > 0 && (!colidx || !vals))) { set_error("NULL CSR array"); return CMSVD_INVALID_ARG; }
-    CM_TRY(enter(ctx));
+    Session se;
+    CM_TRY(se.open(ctx));
     cmsvd_matrix* M = new (std::nothrow) cmsvd_matrix();
     if (!M) { set_error("host allocation failed"); return CMSVD_OUT_OF_MEMORY; }
     M->ctx = ctx;
@@ -268,7 +296,7 @@ int cmsvd_csr_create(cmsvd_context* ctx, int64_t m, int64_t n, int64_t nnz, cons
         delete M;
         return st;
     }
-    CM_TRY(leave(ctx));
+    CM_TRY(se.close());
     *out = M;
     return CMSVD_OK;
 }
@@ -294,18 +322,20 @@ int cmsvd_csr_shape(const cmsvd_matrix* A, int64_t* m, int64_t* n, int64_t* nnz)
 int cmsvd_spmm(cmsvd_matrix* A, int transpose, int64_t L, const double* X, int64_t ldx, double* Y, int64_t ldy) {
     if (!A || !X || !Y) { set_error("NULL argument"); return CMSVD_INVALID_ARG; }
     if (L < 1 || L > 4096 || ldx < L || ldy < L) { set_error("need 1 <= L <= 4096, ldx >= L, ldy >= L"); return CMSVD_INVALID_ARG; }
-    CM_TRY(enter(A->ctx));
+    Session se;
+    CM_TRY(se.open(A->ctx));
     CM_TRY(spmm(transpose ? A->At : A->A, (int)L, X, ldx, Y, ldy, A->ctx->s));
-    return leave(A->ctx);
+    return se.close();
 }
 
 int cmsvd_spmm_f32(cmsvd_matrix* A, int transpose, int64_t L, const float* X, int64_t ldx, float* Y, int64_t ldy) {
     if (!A || !X || !Y) { set_error("NULL argument"); return CMSVD_INVALID_ARG; }
     if (L < 1 || L > 4096 || ldx < L || ldy < L) { set_error("need 1 <= L <= 4096, ldx >= L, ldy >= L"); return CMSVD_INVALID_ARG; }
-    CM_TRY(enter(A->ctx));
+    Session se;
+    CM_TRY(se.open(A->ctx));
     CM_TRY(csr_make_fp32(A));
     CM_TRY(spmm(transpose ? A->At : A->A, (int)L, X, ldx, Y, ldy, A->ctx->s));
-    return leave(A->ctx);
+    return se.close();
 }
 
 int cmsvd_quadrature(cmsvd_context* ctx, double a, double b, int32_t N, int32_t variant, double alpha, double* shift,
@@ -316,7 +346,8 @@ int cmsvd_quadrature(cmsvd_context* ctx, double a, double b, int32_t N, int32_t 
         set_error("invalid quadrature arguments");
         return CMSVD_INVALID_ARG;
     }
-    CM_TRY(enter(ctx));
+    Session se;
+    CM_TRY(se.open(ctx));
     const int J = N / 2;
     double2* d = nullptr;
     CM_CUDA(cudaMalloc(&d, sizeof(double2) * 3 * J));
@@ -338,7 +369,7 @@ int cmsvd_quadrature(cmsvd_context* ctx, double a, double b, int32_t N, int32_t 
     free(h);
     cudaFree(d);
     if (st != CMSVD_OK) return st;
-    return leave(ctx);
+    return se.close();
 }
 
 int cmsvd_gram_workspace_size(cmsvd_context* ctx, int64_t n, int32_t c1, int32_t c2, size_t* bytes) {
@@ -358,10 +389,11 @@ int cmsvd_gram(cmsvd_context* ctx, int64_t n, int32_t c1, int32_t c2, const doub
     if (!X || !Y || !G || !workspace) { set_error("NULL argument"); return CMSVD_INVALID_ARG; }
     if (ldx < c1 || ldy < c2) { set_error("need ldx >= c1 and ldy >= c2"); return CMSVD_INVALID_ARG; }
     if (ws_bytes < need) { set_error("workspace %zu < %zu bytes", ws_bytes, need); return CMSVD_WORKSPACE_TOO_SMALL; }
-    CM_TRY(enter(ctx));
+    Session se;
+    CM_TRY(se.open(ctx));
     CM_TRY(gram(X, ldx, c1, Y, ldy, c2, n, G, (double*)workspace, (ws_bytes - 256) / sizeof(double), ctx->sm_count,
                 ctx->s));
-    return leave(ctx);
+    return se.close();
 }
 
 int cmsvd_workspace_size(const cmsvd_matrix* A, const cmsvd_params* p, size_t* bytes) {
@@ -381,7 +413,8 @@ int cmsvd_moments(cmsvd_matrix* A, double a, double b, const cmsvd_params* p, co
     CM_TRY(cmsvd_workspace_size(A, p, &need));
     if (ws_bytes < need) { set_error("workspace %zu < %zu bytes", ws_bytes, need); return CMSVD_WORKSPACE_TOO_SMALL; }
     cmsvd_context* ctx = A->ctx;
-    CM_TRY(enter(ctx));
+    Session se;
+    CM_TRY(se.open(ctx));
     prof_reset(p->profile != 0);
     Arena ws;
     ws.base = (char*)workspace;
@@ -396,7 +429,7 @@ int cmsvd_moments(cmsvd_matrix* A, double a, double b, const cmsvd_params* p, co
     CM_CUDA(cudaStreamSynchronize(ctx->s));
     prof_collect(&st);
     if (stats) *stats = st;
-    CM_TRY(leave(ctx));
+    CM_TRY(se.close());
     return status;
 }
 
@@ -410,7 +443,8 @@ int cmsvd_solve_interval(cmsvd_matrix* A, double a, double b, const cmsvd_params
     CM_TRY(cmsvd_workspace_size(A, p, &need));
     if (ws_bytes < need) { set_error("workspace %zu < %zu bytes", ws_bytes, need); return CMSVD_WORKSPACE_TOO_SMALL; }
     cmsvd_context* ctx = A->ctx;
-    CM_TRY(enter(ctx));
+    Session se;
+    CM_TRY(se.open(ctx));
     Events ev;
     CM_TRY(ev.make());
     prof_reset(p->profile != 0);
@@ -464,7 +498,7 @@ int cmsvd_solve_interval(cmsvd_matrix* A, double a, double b, const cmsvd_params
     }
     r->stats = st;
     *out = r;
-    CM_TRY(leave(ctx));
+    CM_TRY(se.close());
     if (status == CMSVD_OK && st.rank >= c) status = CMSVD_SUBSPACE_SATURATED;
     return status;
 }
