@@ -246,8 +246,10 @@ int cmsvd_workspace_size(const cmsvd_matrix* A, const cmsvd_params* p, size_t* b
  *   S_k = 2 Re sum_{j<=N/2} w_j ((node_j - gamma)/rho)^k (s_j I - A^T A)^{-1} S_0^(ell-1),
  * k = 0..M (M+1 blocks: the last one is the S_M block of S_+, Sec. 3.4.1).
  * V_in: device, n x L. S_out: device, n x L(M+1) row-major, column m*L + l.
- * The moment weights use the scaled node (a reading of Eq. for S^_k that spans
- * the same column space; see the design notes). Returns CMSVD_NOT_CONVERGED
+ * The moment weights use the scaled node (node_j - gamma)/rho in place of the
+ * literal node^k of Sec. 3.1: the two moment blocks differ by a block-triangular
+ * change of basis, so they span the same column space, and the scaled form keeps
+ * the blocks well conditioned when rho << gamma. Returns CMSVD_NOT_CONVERGED
  * (with S_out filled) when a Krylov solve hit max_iter.
  */
 int cmsvd_moments(cmsvd_matrix* A, double a, double b, const cmsvd_params* p,
