@@ -93,3 +93,54 @@ def test_batch_and_server_argument_checks(lib):
     assert lib.cmsvd_server_submit(None, 0, 0.1, 0.2, None, None, None) == B.INVALID_ARG
     assert lib.cmsvd_status_string(B.PENDING) == b"pending"
     assert lib.cmsvd_result_copy_estimate(None, None) == B.INVALID_ARG
+
+
+def test_header_is_c99_and_matches_binding_layout(lib, tmp_path):
+    """include/cmsvd.h compiles as strict C99 and links against the library, and the
+    struct layouts the ctypes binding declares match the header field by field (sizes
+    and offsets taken from the C compiler), as do the status and enum values."""
+    import ctypes as C
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"cmsvd_params": B.cmsvd_params, "cmsvd_stats": B.cmsvd_stats}
+    consts = {"CMSVD_OK": B.OK, "CMSVD_INVALID_ARG": B.INVALID_ARG, "CMSVD_INVALID_MATRIX": B.INVALID_MATRIX,
+              "CMSVD_OUT_OF_MEMORY": B.OUT_OF_MEMORY, "CMSVD_WORKSPACE_TOO_SMALL": B.WORKSPACE_TOO_SMALL,
+              "CMSVD_NOT_CONVERGED": B.NOT_CONVERGED, "CMSVD_BREAKDOWN": B.BREAKDOWN,
+              "CMSVD_SUBSPACE_SATURATED": B.SUBSPACE_SATURATED, "CMSVD_CUDA_ERROR": B.CUDA_ERROR,
+              "CMSVD_NOT_SUPPORTED": B.NOT_SUPPORTED, "CMSVD_PENDING": B.PENDING,
+              "CMSVD_LINEAR": B.LINEAR, "CMSVD_NT": B.NT, "CMSVD_SOLVER_AUTO": B.SOLVER_AUTO,
+              "CMSVD_SOLVER_KRYLOV": B.SOLVER_KRYLOV, "CMSVD_SOLVER_DIRECT": B.SOLVER_DIRECT,
+              "CMSVD_SOLVER_DENSE": B.SOLVER_DENSE, "CMSVD_FP64": B.FP64, "CMSVD_MIXED": B.MIXED,
+              "CMSVD_PROF_CLASSES": len(B.PROFILE_CLASSES)}
+    body = ["#include <stdio.h>", "#include <stddef.h>", '#include "cmsvd.h"', "int main(void) {",
+            "    cmsvd_params p;", "    if (cmsvd_params_default(&p) != CMSVD_OK) return 1;",
+            '    printf("default %d %d %d %d\\n", (int)p.N, (int)p.L, (int)p.M, (int)p.ell);']
+    for sname, st in structs.items():
+        body.append(f'    printf("size {sname} %zu\\n", sizeof({sname}));')
+        for f, _ in st._fields_:
+            body.append(f'    printf("off {sname}.{f} %zu\\n", offsetof({sname}, {f}));')
+    for k in consts:
+        body.append(f'    printf("const {k} %d\\n", (int){k});')
+    body += ["    return 0;", "}"]
+    src = tmp_path / "abi_check.c"
+    src.write_text("\n".join(body) + "\n")
+    exe = tmp_path / "abi_check"
+    libdir = os.path.dirname(B.LIB_PATH)
+    subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-L", libdir, "-lcmsvd", f"-Wl,-rpath,{libdir}", "-o", str(exe)],
+                   check=True, capture_output=True, text=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {}
+    for line in filter(None, out):
+        kind, key, val = line.split(" ", 2)
+        got[(kind, key)] = val
+    assert got[("default", "32")] == "16 4 1"
+    for sname, st in structs.items():
+        assert int(got[("size", sname)]) == C.sizeof(st), sname
+        for f, _ in st._fields_:
+            assert int(got[("off", f"{sname}.{f}")]) == getattr(st, f).offset, f"{sname}.{f}"
+    for k, v in consts.items():
+        assert int(got[("const", k)]) == v, k
