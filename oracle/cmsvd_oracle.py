@@ -233,27 +233,51 @@ def shifted_moment_operator(q: Quadrature, Splus: np.ndarray, Z: np.ndarray, V: 
     return q.rho * (Splus @ Z) + q.gamma * V
 
 
+def truncate(S: np.ndarray, delta: float):
+    """Alg. 1 step 3 (Eq. low-rank): S = U_S Sigma_S W_S^T, keep sigma_S > delta * sigma_S,1
+    (the relative reading of delta). Returns U_S, sigma_S, W_S^T and the kept rank r."""
+    US, sS, WSt = np.linalg.svd(S, full_matrices=False)
+    r = int(np.count_nonzero(sS > delta * sS[0]))
+    return US, sS, WSt, r
+
+
+def project(A, Vt: np.ndarray):
+    """Alg. 1 step 4 (Eq. avub): [U~, B] = qr(A V~)."""
+    return np.linalg.qr(A @ Vt)
+
+
+def ritz_triplets(Ut: np.ndarray, B: np.ndarray, Vt: np.ndarray):
+    """Alg. 1 step 5 (Eq. bsvd): B = P Phi Q^T and (sigma^, u^, v^) = (phi, U~ p, V~ q).
+    Returns phi, u^, v^ and Q."""
+    P, phi, Qt = np.linalg.svd(B)
+    Q = Qt.T
+    return phi, Ut @ P, Vt @ Q, Q
+
+
+def spurious_index(Q: np.ndarray, sS: np.ndarray, r: int) -> np.ndarray:
+    """Sec. 3.4.2: tau_i = q_i^T q_i / (q_i^T Sigma_S1^{-1} q_i), relative to sigma_S,1."""
+    tau = np.sum(Q * Q, axis=0) / np.sum(Q * Q / sS[:r, None], axis=0)
+    return tau / sS[0]
+
+
+def exact_residuals(A, uh: np.ndarray, vh: np.ndarray, phi: np.ndarray, norm_A: float):
+    """Sec. 3.4.1, first line: ||A^T u - sigma v|| / ||A||_2 and ||A v - sigma u|| / ||A||_2."""
+    res_u = np.linalg.norm(A.T @ uh - vh * phi, axis=0) / norm_A
+    res_v = np.linalg.norm(A @ vh - uh * phi, axis=0) / norm_A
+    return res_u, res_v
+
+
 def rayleigh_ritz(A, S: np.ndarray, a: float, b: float, L: int, M: int, delta: float,
                   eps_tau: float, tol_triplet: float, norm_A: float,
                   q: Quadrature | None = None, S_plus_last: np.ndarray | None = None) -> Result:
+    """Alg. 1 steps 3-5 on the moment block S, the tau test and the exact residuals."""
     A = as_scipy(A)
-    # Step 3: low-rank approximation, keep sigma_S > delta * sigma_S,1 (relative reading of delta)
-    US, sS, WSt = np.linalg.svd(S, full_matrices=False)
-    r = int(np.count_nonzero(sS > delta * sS[0]))
+    US, sS, WSt, r = truncate(S, delta)
     Vt = US[:, :r]
-    # Step 4: [U~, B] = qr(A V~)
-    Ut, B = np.linalg.qr(A @ Vt)
-    # Step 5: B = P Phi Q^T; (sigma, u, v) = (phi, U~ p, V~ q)
-    P, phi, Qt = np.linalg.svd(B)
-    Q = Qt.T
-    uh = Ut @ P
-    vh = Vt @ Q
-    # spurious index tau_i = q^T q / (q^T Sigma_S1^{-1} q)   (Sec. 3.4.2)
-    tau = np.sum(Q * Q, axis=0) / np.sum(Q * Q / sS[:r, None], axis=0)
-    tau_rel = tau / sS[0]
-    # exact residuals (Sec. 3.4.1, first line)
-    res_u = np.linalg.norm(A.T @ uh - vh * phi, axis=0) / norm_A
-    res_v = np.linalg.norm(A @ vh - uh * phi, axis=0) / norm_A
+    Ut, B = project(A, Vt)
+    phi, uh, vh, Q = ritz_triplets(Ut, B, Vt)
+    tau_rel = spurious_index(Q, sS, r)
+    res_u, res_v = exact_residuals(A, uh, vh, phi, norm_A)
     # Residual estimate through S_+ (Sec. 3.4.1). With scaled moment nodes the shifted
     # moments satisfy  f(A^T A) S'_k = rho S'_{k+1} + gamma S'_k,  with f(x) = x for the
     # linear variant (Prop. 1, exact) and f(x) = g^{-1}(x) = ln x for NT (approximate,

@@ -7,7 +7,8 @@
 * the contour-integral limit of Thm. 1 (spectral projector) for both variants,
 * the Exp I filter statements (tests/golden/exp1_filter.txt),
 * triplets against numpy's dense SVD, and the Exp II model problems (Sec. 4.2),
-* the spurious index tau on the 2000 x 1000 workload (Sec. 3.4.2),
+* the spurious index tau on inputs solvable by hand and on the 2000 x 1000
+  workload (Sec. 3.4.2),
 * the residual estimate through S_+ (Sec. 3.4.1): equal to the exact residual for the
   linear variant, equal to the ln(A^T A) form for NT, and mu fixed by one exact residual.
 
@@ -267,14 +268,19 @@ def test_model_problems_exp2():
     assert rl.sigma.size < 40
 
 
-def test_c1_tau_detects_spurious():
-    """2000 x 1000, 8 nnz/row, sigma ranked 400-419: 20 found; one Ritz value in
-    [a, b] is spurious (tiny tau, large residual) and tau removes it (Sec. 3.4.2)."""
+def c1_result():
+    """The 2000 x 1000 workload (8 nnz/row, sigma ranked 400-419) through the oracle."""
     A = synth.random_sparse(2000, 1000, 8, seed=0)
     s = np.linalg.svd(A.to_dense(), compute_uv=False)
     a, b, _ = synth.window_interval(s, 400, 20)
     Vin = synth.gaussian_block(1000, 16, 1)
-    r = O.solve_interval(A, a, b, 16, 16, 4, Vin, norm_A=s[0])
+    return O.solve_interval(A, a, b, 16, 16, 4, Vin, norm_A=s[0]), s, a, b
+
+
+def test_c1_tau_detects_spurious():
+    """2000 x 1000, 8 nnz/row, sigma ranked 400-419: 20 found; one Ritz value in
+    [a, b] is spurious (tiny tau, large residual) and tau removes it (Sec. 3.4.2)."""
+    r, s, a, b = c1_result()
     truth = s[400:420][::-1]
     assert r.sigma.size == 20
     assert np.max(np.abs(r.sigma - truth) / truth) < 1e-13
@@ -283,6 +289,25 @@ def test_c1_tau_detects_spurious():
     assert spurious.sum() >= 1
     assert np.all(r.all_res[spurious] > 1e-6)
     assert np.all(r.all_tau[inside & ~spurious] > 1e-3)
+
+
+def tau_special_case_error():
+    """tau of Sec. 3.4.2 on inputs solvable by hand. For q = e_k it is sigma_S,k (relative:
+    sigma_S,k / sigma_S,1). For q with equal weight on directions k and l it is the harmonic
+    mean 2 s_k s_l / (s_k + s_l), whatever the scale of q, so a Ritz vector with half its
+    weight on a rounding-level direction of S is spurious."""
+    sS = np.array([4.0, 2.0, 1.0, 1e-12])
+    Q = np.zeros((4, 3))
+    Q[1, 0] = 1.0                                    # e_2
+    Q[0, 1] = Q[3, 1] = np.sqrt(0.5)                 # half on the noise direction
+    Q[0, 2] = Q[2, 2] = 3.0                          # equal weight, scaled by 3
+    expect = np.array([2.0, 2 * 4.0 * 1e-12 / (4.0 + 1e-12), 2 * 4.0 * 1.0 / 5.0]) / 4.0
+    tau = O.spurious_index(Q, sS, 4)
+    return float(np.max(np.abs(tau - expect) / expect))
+
+
+def test_tau_special_cases():
+    assert tau_special_case_error() < 1e-14
 
 
 def estimate_errors(variant):
@@ -407,3 +432,53 @@ def test_mutation_estimate_log_of_sigma_caught(monkeypatch):
     orig = O.spectral_map
     monkeypatch.setattr(O, "spectral_map", lambda v, x: orig(v, x) if v == "linear" else np.log(np.sqrt(x)))
     assert estimate_errors("nt")[0] > 1e-3
+
+
+# Steps 3-5 (truncation, qr(A V~), SVD of B, tau, residuals): each planted mistake must
+# make a pin above fail.
+def _svd_B(B):
+    return np.linalg.svd(B)
+
+
+@pytest.mark.parametrize("kind", ["Q_not_transposed", "P_transposed"])
+def test_mutation_ritz_factors_caught(monkeypatch, kind):
+    """B = P Phi Q (G9) read the wrong way: v^ = V~ Q^T, or u^ = U~ P^T."""
+    def ritz(Ut, B, Vt):
+        P, phi, Qt = _svd_B(B)
+        if kind == "Q_not_transposed":
+            return phi, Ut @ P, Vt @ Qt, Qt
+        return phi, Ut @ P.T, Vt @ Qt.T, Qt.T
+    monkeypatch.setattr(O, "ritz_triplets", ritz)
+    assert dense_triplet_errors("linear", 1)[0] != 6
+
+
+def test_mutation_residual_without_sigma_caught(monkeypatch):
+    monkeypatch.setattr(O, "exact_residuals", lambda A, uh, vh, phi, nA: (
+        np.linalg.norm(A.T @ uh - vh, axis=0) / nA, np.linalg.norm(A @ vh - uh, axis=0) / nA))
+    assert dense_triplet_errors("linear", 1)[0] != 6
+
+
+@pytest.mark.parametrize("kind", ["arithmetic_mean", "not_relative"])
+def test_mutation_tau_caught(monkeypatch, kind):
+    def tau(Q, sS, r):
+        if kind == "arithmetic_mean":
+            return np.sum(Q * Q * sS[:r, None], axis=0) / np.sum(Q * Q, axis=0) / sS[0]
+        return np.sum(Q * Q, axis=0) / np.sum(Q * Q / sS[:r, None], axis=0)
+    monkeypatch.setattr(O, "spurious_index", tau)
+    assert tau_special_case_error() > 1e-3
+
+
+@pytest.mark.parametrize("kind", ["delta_absolute", "keep_every_column", "residual_not_normalised"])
+def test_mutation_truncation_and_normalisation_caught(monkeypatch, kind):
+    """delta read as absolute, no truncation at all (the paper's 1e-20 in effect), or the
+    residual test without the division by ||A||_2: the 2000 x 1000 count changes."""
+    if kind == "residual_not_normalised":
+        monkeypatch.setattr(O, "exact_residuals", lambda A, uh, vh, phi, nA: (
+            np.linalg.norm(A.T @ uh - vh * phi, axis=0), np.linalg.norm(A @ vh - uh * phi, axis=0)))
+    else:
+        def trunc(S, delta):
+            US, sS, WSt = np.linalg.svd(S, full_matrices=False)
+            r = int(np.count_nonzero(sS > delta)) if kind == "delta_absolute" else sS.size
+            return US, sS, WSt, r
+        monkeypatch.setattr(O, "truncate", trunc)
+    assert c1_result()[0].sigma.size != 20
