@@ -144,3 +144,30 @@ def test_header_is_c99_and_matches_binding_layout(lib, tmp_path):
             assert int(got[("off", f"{sname}.{f}")]) == getattr(st, f).offset, f"{sname}.{f}"
     for k, v in consts.items():
         assert int(got[("const", k)]) == v, k
+
+
+def test_readme_c_example_builds(lib, tmp_path):
+    """The C usage example in README.md compiles as strict C99 against the header and links
+    against the library and the CUDA runtime (built, not run: it needs a GPU)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    cuda = os.path.dirname(os.path.dirname(os.path.realpath(nvcc)))
+    if cc is None or not os.path.exists(os.path.join(cuda, "include", "cuda_runtime.h")):
+        pytest.skip("no C compiler or CUDA headers")
+    text = open(os.path.join(ROOT, "README.md")).read()
+    blocks = re.findall(r"```c\n(.*?)```", text, flags=re.S)
+    assert len(blocks) == 1
+    src = tmp_path / "example.c"
+    src.write_text(blocks[0])
+    libdir = os.path.dirname(B.LIB_PATH)
+    cudalib = next((d for d in (os.path.join(cuda, "lib64"), os.path.join(cuda, "lib"))
+                    if os.path.isdir(d)), None)
+    if cudalib is None:
+        pytest.skip("no CUDA runtime library directory")
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-pedantic", "-fPIC", "-shared",
+                        "-I", os.path.join(ROOT, "include"), "-isystem", os.path.join(cuda, "include"), str(src),
+                        "-L", libdir, "-lcmsvd", "-L", cudalib, "-lcudart", "-Wl,--no-undefined",
+                        "-o", str(tmp_path / "libexample.so")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
