@@ -345,6 +345,9 @@ class Server:
     def submit(self, mid: int, a: float, b: float, p: cmsvd_params, V_in: np.ndarray) -> int:
         t = C.c_int64()
         V = np.ascontiguousarray(V_in, dtype=np.float64)
+        n = self.shapes[mid][1] if 0 <= mid < len(self.shapes) else None
+        if n is not None and V.shape != (n, p.L):
+            raise ValueError(f"V_in must be {n} x {p.L}, got {V.shape}")   # the library copies n * L doubles
         _check(lib().cmsvd_server_submit(_P(self.handle), mid, a, b, C.byref(p), _P(V.ctypes.data), C.byref(t)),
                "cmsvd_server_submit")
         return t.value
