@@ -389,10 +389,6 @@ __global__ void __launch_bounds__(1024) k_jacobi(double* __restrict__ Xc, int ro
     }
 }
 
-// Multi-CTA form for larger blocks: one CTA per pair of a round (the pairs of a
-// round are disjoint), one launch per round; a sweep is np-1 launches and the
-// host checks the "rotated" flag after every sweep. Columns whose squared norm is
-// below negl (1e-36 ||Bm||_F^2) are treated as zero.
 // Sums three values over a 128-thread block (fixed order: deterministic).
 __device__ __forceinline__ void block_sum3_128(double& a, double& b, double& c, double (*sh)[4]) {
     for (int o = 16; o > 0; o >>= 1) {
@@ -441,9 +437,10 @@ __device__ __forceinline__ bool grid_barrier(unsigned* ctl, unsigned nblocks) {
 
 constexpr int JC_MAXDIM = 1024;             // L M <= 512; the dense direct solver factors n <= 1024
 
-// Cooperative form for 97..512 columns: one CTA per pair of a round (round-robin ordering,
+// Cooperative form for 97..1024 columns: one CTA per pair of a round (round-robin ordering,
 // the pairs of a round are disjoint), all sweeps in one launch, a bounded grid barrier
-// between rounds. Each thread holds its rows of both columns and both V columns in
+// between rounds. Columns whose squared norm is below negl (1e-36 ||Bm||_F^2) are treated
+// as zero. Each thread holds its rows of both columns and both V columns in
 // registers, so a round costs one L2 round trip. GB300 runs an FP64 warp instruction in
 // 16 clocks whatever its active lanes, so only warp 0 computes the rotation angle and
 // shares it through shared memory. (Measured alternatives, slower on this part: an 8-CTA
