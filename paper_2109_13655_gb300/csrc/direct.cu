@@ -13,7 +13,8 @@
 //   c_k(lambda) = 2 Re sum_j w_j m_j^k / (s_j - lambda),  f = c_0.
 // The analysis (finding the components) runs once per matrix on the host,
 // like the symbolic phase of a sparse direct solver; the numeric work runs on
-// the device.
+// the device. The dense direct solver (n <= 1024, one large component) is at the
+// end of this file.
 #include "internal.cuh"
 #include <vector>
 #include <numeric>

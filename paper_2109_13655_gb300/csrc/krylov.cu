@@ -16,6 +16,9 @@
 //           explicitly rounded operations) and accumulate S_k += c_{k,i} q_i.
 // The SpMM is real (L columns), not complex (2L). Iterations run as CUDA
 // graphs; convergence is polled every check_every iterations.
+// With precision MIXED the Lanczos vectors, the SpMM values and its accumulation are
+// FP32 (alpha, beta, the LDL^T recurrences and S stay FP64), and every shifted solve is
+// refined in FP64 (refined_filter, at the end of this file).
 #include "internal.cuh"
 
 namespace cmsvd {
