@@ -16,7 +16,8 @@ steps outside the timed window. e2e: the same through the C ABI with V_in in
 pinned host memory and all triplets copied back to pinned host memory inside
 the timed window. Multi-GPU: independent replicas (the method needs no
 exchange between GPUs), max time over ranks. --impl reference times the CPU
-oracle (NumPy FP64 direct solves) on the same workload on rank 0.
+oracle (NumPy FP64 direct solves) on the same workload on rank 0: W untimed and K
+timed full solves, about 6 s each on 16 host cores.
 """
 from __future__ import annotations
 
@@ -123,18 +124,18 @@ def run_reference(args, w, rank):
     Vin = synth.gaussian_block(A.n, cfg["L"], w["seed"])
     solver = O.ShiftedSolver(A)
     times, ok = [], True
-    for i in range(min(args.warmup, 1) + args.steps):
+    for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
         r = O.solve_interval(A, w["a"], w["b"], cfg["N"], cfg["L"], cfg["M"], Vin, ell=cfg["ell"],
                              norm_A=w["norm_A"], solver=solver)
         dt = time.perf_counter() - t0
-        if i >= min(args.warmup, 1):
+        if i >= args.warmup:
             times.append(dt)
             ok &= r.sigma.size == w["t"] and float(np.max(r.res_u)) <= 1e-10
     v = len(times) / sum(times)
     cores = os.cpu_count()
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": min(args.warmup, 1), "ms_per_step": 1e3 * sum(times) / len(times),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "description": w["desc"], **cfg},
             "all_steps_valid": bool(ok),
