@@ -141,8 +141,9 @@ def run_reference(args, w, rank):
             "all_steps_valid": bool(ok),
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"{len(times)} full oracle solves of the workload (NumPy/OpenBLAS FP64, "
-                                       f"{cores} host cores)"}}
+                             "sample": f"{len(times)} full oracle solves of the workload (NumPy/OpenBLAS FP64; "
+                                       f"dense steps on OpenBLAS's default {cores} threads, the stacked "
+                                       f"per-component solves on one thread)"}}
     print(json.dumps(line), flush=True)
 
 
@@ -161,8 +162,9 @@ def cpu_baseline(w, budget_s=30.0):
         times.append(time.perf_counter() - t0)
     cores = os.cpu_count()
     return {"value": len(times) / sum(times), "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{len(times)} full oracle solve(s) of the same workload, {sum(times):.1f} s total, "
-                      f"OpenBLAS default threads on {cores} cores"}
+            "sample": f"{len(times)} full oracle solve(s) of the same workload, {sum(times):.1f} s total; "
+                      f"dense steps on OpenBLAS's default {cores} threads, the stacked per-component "
+                      f"solves on one thread"}
 
 
 # ----------------------------------------------------------------------------- our arm
