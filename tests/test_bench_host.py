@@ -40,3 +40,28 @@ def test_clock_summary_flags_throttle_reasons():
 
 def test_job_throughput_is_whole_job():
     assert bench.job_throughput(10, 4, 2.0) == 20.0
+
+
+def test_reference_arm_json_line():
+    """`bench.py --impl reference` (the CPU oracle arm) on the small 2000 x 1000 workload
+    prints one JSON line with the contract's keys, the requested warm-up and step counts,
+    and every solve valid."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--workload",
+                        "random_sparse_2000x1000", "--steps", "2", "--warmup", "3"],
+                       capture_output=True, text=True, timeout=600, cwd=root)
+    assert r.returncode == 0, r.stderr
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "e2e", "cpu_baseline"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["steps"] == 2 and d["warmup"] == 3
+    assert d["config"]["workload"] == "random_sparse_2000x1000" and d["all_steps_valid"] is True
+    assert d["value"] > 0 and d["e2e"]["value"] == d["value"] and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["cores"] >= 1
