@@ -10,7 +10,8 @@
 * the spurious index tau on inputs solvable by hand and on the 2000 x 1000
   workload (Sec. 3.4.2),
 * the residual estimate through S_+ (Sec. 3.4.1): equal to the exact residual for the
-  linear variant, equal to the ln(A^T A) form for NT, and mu fixed by one exact residual.
+  linear variant, equal to the ln(A^T A) form for NT, and mu fixed by one exact residual;
+  on the Exp II model problems it follows the exact residuals (Sec. 4.2).
 
 The mutation tests at the end plant plausible mistakes in the oracle and
 check that at least one of these pins fails.
@@ -348,6 +349,24 @@ def test_residual_estimate_nt_log_form_and_mu():
     # i' is the candidate with the largest r~: every other estimate scales r~ by the same mu
     mu = r.res_est / r.res_tilde
     assert np.max(np.abs(mu - mu[0])) <= 1e-12 * mu[0]
+
+
+@pytest.mark.parametrize("which", [1, 2])
+@pytest.mark.parametrize("variant", ["linear", "nt"])
+def test_residual_estimate_tracks_exact_on_exp2(which, variant):
+    """Sec. 4.2 (the figure of residuals and their estimates): on both model problems, with
+    the paper's (L, M, N, ell) = (20, 4, 32, 1), the estimates of Sec. 3.4.1 follow the exact
+    residual norms. Here the residuals span two orders of magnitude (model 2). Every estimate
+    lies within a factor of 20 of its exact residual, and the median ratio within 2."""
+    Vin = synth.gaussian_block(200, 20, 3)
+    a, b = (0.8, 1.2) if which == 1 else (10 ** -3.025, 10 ** -1.025)
+    A, sig = synth.model_problem(which)
+    r = O.solve_interval(A, a, b, 32, 20, 4, Vin, variant=variant, norm_A=sig.max(), with_estimate=True,
+                         tol_triplet=1.0)
+    assert r.sigma.size >= 30
+    ratio = r.res_est / r.res_u
+    assert np.all(ratio > 1 / 20) and np.all(ratio < 20)
+    assert 0.5 < np.median(ratio) < 2.0
 
 
 def test_exp3_digits_standin():
