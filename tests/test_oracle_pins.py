@@ -5,6 +5,7 @@
 * Prop. 1 (S_k = (A^T A)^k S_0, linear variant),
 * closed-form moments from a dense SVD (first equality of Prop. 1; Sec. 3.3 for NT),
 * the contour-integral limit of Thm. 1 (spectral projector) for both variants,
+* the error bound of Thm. 2 (subspace distances of the exact singular vectors),
 * the Exp I filter statements (tests/golden/exp1_filter.txt),
 * triplets against numpy's dense SVD, and the Exp II model problems (Sec. 4.2),
 * the spurious index tau on inputs solvable by hand and on the 2000 x 1000
@@ -120,6 +121,48 @@ def contour_limit_error(variant="linear"):
     x = (s ** 2 - q.gamma) / q.rho if variant == "linear" else (np.log(s ** 2) - q.gamma) / q.rho
     ref = np.concatenate([Vt[inside].T @ ((x[inside] ** k)[:, None] * (Vt[inside] @ Vin)) for k in range(M)], axis=1)
     return np.max(np.abs(S - ref)) / np.max(np.abs(ref))
+
+
+def theorem2_excess(variant="linear", ell=1):
+    """Thm. 2 on a 60 x 30 matrix with known singular vectors (L = 2, M = 3, N = 16, three
+    values inside [a, b]). With f ordered by decreasing |f(sigma_i)|, K the block Krylov
+    matrix (of A^T A, or of g^{-1}(A^T A) = ln(A^T A) for NT, where the theorem holds
+    approximately), s_i in R(K) with P_LM s_i = v_i and beta_i = ||v_i - s_i||, the distances
+    of v_i from R(S) and of u_i from R(A S) must stay below beta_i |f(sigma_LM+1)/f(sigma_i)|^ell
+    and alpha_i times that. Returns the largest ratio of distance to bound over i <= LM
+    (<= 1 when the theorem holds)."""
+    sig = np.linspace(0.1, 3.0, 30)[::-1]
+    Ad = _svd_matrix(sig, 60, 5)
+    U, s, Vt = np.linalg.svd(Ad, full_matrices=False)
+    L, M, N = 2, 3, 16
+    q = O.quadrature(1.42, 1.78, N, variant)
+    Vin = synth.gaussian_block(30, L, 6)
+    S = O.moments(O.ShiftedSolver(Ad), q, Vin, M, ell=ell)
+    f = O.filter_value(s, q)
+    order = np.argsort(-np.abs(f), kind="stable")
+    V, U, so, fo = Vt.T[:, order], U[:, order], s[order], f[order]
+    H = Ad.T @ Ad
+    if variant == "nt":
+        lam, W = np.linalg.eigh(H)
+        H = (W * np.log(lam)) @ W.T
+    K = np.concatenate([np.linalg.matrix_power(H, k) @ Vin for k in range(M)], axis=1)
+    LM = L * M
+    QV, _ = np.linalg.qr(S)
+    QU, _ = np.linalg.qr(Ad @ S)
+    worst = 0.0
+    for i in range(LM):
+        si = K @ np.linalg.solve(V[:, :LM].T @ K, np.eye(LM)[:, i])
+        bound_v = np.linalg.norm(V[:, i] - si) * abs(fo[LM] / fo[i]) ** ell
+        bound_u = bound_v * so[LM:].max() / so[i]
+        dv = np.linalg.norm(V[:, i] - QV @ (QV.T @ V[:, i]))
+        du = np.linalg.norm(U[:, i] - QU @ (QU.T @ U[:, i]))
+        worst = max(worst, (dv - 1e-13) / bound_v, (du - 1e-13) / bound_u)
+    return worst
+
+
+@pytest.mark.parametrize("variant,ell", [("linear", 1), ("linear", 2), ("nt", 1), ("nt", 2)])
+def test_theorem2_error_bound(variant, ell):
+    assert theorem2_excess(variant, ell) <= 1.0
 
 
 def dense_triplet_errors(variant="linear", ell=1, m=120, n=60, first=20, count=6, seed=51):
@@ -501,3 +544,12 @@ def test_mutation_truncation_and_normalisation_caught(monkeypatch, kind):
             return US, sS, WSt, r
         monkeypatch.setattr(O, "truncate", trunc)
     assert c1_result()[0].sigma.size != 20
+
+
+def test_mutation_iteration_skipped_caught(monkeypatch):
+    """The iteration technique (Eqs. iter1-iter2) dropped: ell = 2 then gives only the ell = 1
+    subspace, which misses the bound of Thm. 2 for ell = 2."""
+    orig = O.moments
+    monkeypatch.setattr(O, "moments", lambda solver, q, V, M, ell=1, scaled=True, extra=0:
+                        orig(solver, q, V, M, 1, scaled, extra))
+    assert theorem2_excess("linear", 2) > 1.0
