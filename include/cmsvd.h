@@ -67,6 +67,16 @@ typedef enum cmsvd_precision {
                              Rank truncation and Rayleigh-Ritz stay FP64. The direct solver ignores it. */
 } cmsvd_precision;
 
+/* Precision in which the library keeps A's values (cmsvd_csr_create). The values are rounded
+   to it (round to nearest) when the matrix is created, so the stored matrix is the problem
+   that every solve on it computes. FP64 steps read the stored values widened to FP64; the
+   mixed-precision Krylov path streams them in their stored width (8, 4 or 2 bytes). */
+typedef enum cmsvd_storage {
+    CMSVD_STORE_FP64 = 0,
+    CMSVD_STORE_FP32 = 1,
+    CMSVD_STORE_BF16 = 2
+} cmsvd_storage;
+
 /* Method parameters. Names follow Alg. 1 / Alg. 2 and Sec. 4. */
 typedef struct cmsvd_params {
     int32_t N;            /* quadrature points, even, 2..128 (N/2 systems are solved, Sec. 3.1) */
@@ -161,18 +171,18 @@ int cmsvd_context_create(void* stream, cmsvd_context** out);
 int cmsvd_context_destroy(cmsvd_context* ctx);   /* NULL is accepted */
 
 /*
- * Sparse matrix A (m x n, m >= 1, n >= 1) in CSR form. rowptr: int64[m+1],
- * colidx: int32[nnz], vals: float64[nnz]; where = 0 for host arrays, 1 for
- * device arrays. The library copies them into its own device memory (the
- * caller keeps ownership of its arrays), validates them on the device
- * (rowptr monotone from 0 to nnz, columns strictly increasing within a row
- * and in [0, n), values finite: otherwise CMSVD_INVALID_MATRIX and *out is
- * NULL), and builds the CSR of A^T. The paper assumes m >= n (Sec. 1); m < n
- * is accepted and simply means A^T A is rank deficient.
+ * Sparse matrix A (m x n, m >= 1, n >= 1) in CSR form (the problem's A, Sec. 1, Eq. psvd).
+ * rowptr: int64[m+1], colidx: int32[nnz], vals: float64[nnz]; where = 0 for host arrays, 1 for
+ * device arrays. The library copies them into its own device memory (the caller keeps
+ * ownership of its arrays), validates them on the device (rowptr monotone from 0 to nnz,
+ * columns strictly increasing within a row and in [0, n), values finite: otherwise
+ * CMSVD_INVALID_MATRIX and *out is NULL), rounds the values to `storage` (cmsvd_storage;
+ * CMSVD_INVALID_MATRIX if one overflows it) and builds the CSR of A^T. The paper assumes
+ * m >= n (Sec. 1); m < n is accepted and simply means A^T A is rank deficient.
  */
 int cmsvd_csr_create(cmsvd_context* ctx, int64_t m, int64_t n, int64_t nnz,
                      const int64_t* rowptr, const int32_t* colidx, const double* vals,
-                     int where, cmsvd_matrix** out);
+                     int where, int32_t storage, cmsvd_matrix** out);
 int cmsvd_csr_destroy(cmsvd_matrix* A);          /* NULL is accepted */
 /* Dimensions of A. */
 int cmsvd_csr_shape(const cmsvd_matrix* A, int64_t* m, int64_t* n, int64_t* nnz);
@@ -193,6 +203,18 @@ int cmsvd_spmm(cmsvd_matrix* A, int transpose, int64_t L, const double* X, int64
  */
 int cmsvd_spmm_f32(cmsvd_matrix* A, int transpose, int64_t L, const float* X, int64_t ldx,
                    float* Y, int64_t ldy);
+
+/*
+ * The same product in double-float arithmetic, the SpMM of the mixed-precision Krylov path
+ * (Alg. 1 steps 1-2). X and Y are device blocks of FP32 pairs: row i holds the L high parts
+ * x_hi[i, 0..L-1] followed by the L low parts x_lo[i, 0..L-1], the value being x_hi + x_lo;
+ * ldx, ldy >= 2L are in floats. Products a * x_hi are formed exactly and the sums are
+ * compensated, all on the FP32 pipe, so Y = A X to a few units of 2^-48 of sum |a||x| (FP32
+ * or bf16 values are exact; FP64 values that are not FP32-exact are used as hi + lo FP32
+ * pairs). Y is normalized (|y_lo| <= ulp(y_hi) / 2). Errors as cmsvd_spmm.
+ */
+int cmsvd_spmm_df(cmsvd_matrix* A, int transpose, int64_t L, const float* X, int64_t ldx,
+                  float* Y, int64_t ldy);
 
 /*
  * Quadrature of Sec. 4 for j = 1..N/2 (the points with Im > 0, Sec. 3.1),
@@ -318,11 +340,13 @@ int cmsvd_server_create(int slots, size_t hbm_budget, cmsvd_server** out);
 /* Stops the workers (a running solve finishes first); requests not started are dropped.
  * Call it only after every cmsvd_server_wait on this server has returned. */
 int cmsvd_server_destroy(cmsvd_server* s);
-/* Uploads, validates and registers a matrix (as cmsvd_csr_create); *id names it in requests.
+/* Uploads, validates and registers a matrix (as cmsvd_csr_create, with the same storage
+ * argument); *id names it in requests.
  * Safe to call while requests run. CMSVD_OUT_OF_MEMORY (nothing registered) when the matrix
  * does not fit in the budget beside the resident matrices and the largest queued request. */
 int cmsvd_server_add_matrix(cmsvd_server* s, int64_t m, int64_t n, int64_t nnz, const int64_t* rowptr,
-                            const int32_t* colidx, const double* vals, int vals_on_device, int* id);
+                            const int32_t* colidx, const double* vals, int vals_on_device, int32_t storage,
+                            int* id);
 /* Queues a request; V_in (n x L, row-major, host memory) is copied. Returns at once with a
  * ticket. CMSVD_OUT_OF_MEMORY when its workspace can never fit in the budget. */
 int cmsvd_server_submit(cmsvd_server* s, int id, double a, double b, const cmsvd_params* p,

@@ -17,6 +17,13 @@ blocking, fusion or reordering beyond what the method states:
 * SVD of B and the Ritz triplets (Eq. bsvd, Alg. 1 step 5),
 * the spurious-value index tau (Sec. 3.4.2) and exact residuals (Sec. 3.4.1).
 
+For a matrix too large for direct solves (the 2e6 x 1e6 banded-plus-random case)
+and an exterior interval [a, b] with b above sigma_max, the triplets the method
+must return are the t largest singular triplets of A (Thm. 1 with Omega holding
+the top of the spectrum). ``largest_singular_values`` computes those values
+with a library Lanczos routine (ARPACK through scipy's eigsh on A^T A); it is
+pinned against numpy's dense SVD on small instances of the same construction.
+
 Readings of points the paper leaves open (each is stated where it is used):
 the moment weights use the scaled nodes ((zeta_j - gamma)/rho)^k; delta and
 the tau threshold are relative to the largest singular value of S^; a triplet
@@ -341,3 +348,26 @@ def solve_interval(A, a: float, b: float, N: int, L: int, M: int, V_in: np.ndarr
     S = S_all[:, :L * M]
     S_last = S_all[:, L * M:] if with_estimate else None
     return rayleigh_ritz(A, S, a, b, L, M, delta, eps_tau, tol_triplet, norm_A, q, S_last)
+
+
+# ---------------------------------------------------------------------------
+# Largest singular values (the expected values for an exterior interval at the top)
+# ---------------------------------------------------------------------------
+def largest_singular_values(A, k: int, tol: float = 1e-14) -> np.ndarray:
+    """The k largest singular values of A, descending.
+
+    For [a, b] with b > sigma_max, the singular values in [a, b] are the largest ones
+    (problem statement, Sec. 1), so this is the oracle of the method's values there when
+    the direct solves of ``ShiftedSolver`` are out of reach. ARPACK's implicitly restarted
+    Lanczos (scipy.sparse.linalg.eigsh) on A^T A, applied as A^T (A x) and never formed;
+    sigma = sqrt(lambda).
+    """
+    from scipy.sparse.linalg import LinearOperator, eigsh
+    A = as_scipy(A)
+    At = A.T.tocsr()
+    n = A.shape[1]
+    H = LinearOperator((n, n), matvec=lambda x: At @ (A @ x), dtype=np.float64)
+    v0 = np.ones(n) / np.sqrt(n)
+    lam = eigsh(H, k=k, which="LA", tol=tol, v0=v0, ncv=min(n, max(2 * k + 1, k + 64)),
+                return_eigenvectors=False)
+    return np.sqrt(np.sort(np.maximum(lam, 0.0))[::-1])

@@ -21,6 +21,8 @@ OK, INVALID_ARG, INVALID_MATRIX, OUT_OF_MEMORY, WORKSPACE_TOO_SMALL, NOT_CONVERG
 LINEAR, NT = 0, 1
 SOLVER_AUTO, SOLVER_KRYLOV, SOLVER_DIRECT, SOLVER_DENSE = 0, 1, 2, 3
 FP64, MIXED = 0, 1
+STORE_FP64, STORE_FP32, STORE_BF16 = 0, 1, 2
+STORAGES = {"fp64": STORE_FP64, "fp32": STORE_FP32, "bf16": STORE_BF16}
 VARIANTS = {"linear": LINEAR, "nt": NT}
 SOLVERS = {"auto": SOLVER_AUTO, "krylov": SOLVER_KRYLOV, "direct": SOLVER_DIRECT, "dense": SOLVER_DENSE}
 
@@ -63,11 +65,12 @@ _SIGS = {
     "cmsvd_params_default": (C.c_int, [C.POINTER(cmsvd_params)]),
     "cmsvd_context_create": (C.c_int, [_P, C.POINTER(_P)]),
     "cmsvd_context_destroy": (C.c_int, [_P]),
-    "cmsvd_csr_create": (C.c_int, [_P, _I64, _I64, _I64, _P, _P, _P, C.c_int, C.POINTER(_P)]),
+    "cmsvd_csr_create": (C.c_int, [_P, _I64, _I64, _I64, _P, _P, _P, C.c_int, C.c_int32, C.POINTER(_P)]),
     "cmsvd_csr_destroy": (C.c_int, [_P]),
     "cmsvd_csr_shape": (C.c_int, [_P, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I64)]),
     "cmsvd_spmm": (C.c_int, [_P, C.c_int, _I64, _P, _I64, _P, _I64]),
     "cmsvd_spmm_f32": (C.c_int, [_P, C.c_int, _I64, _P, _I64, _P, _I64]),
+    "cmsvd_spmm_df": (C.c_int, [_P, C.c_int, _I64, _P, _I64, _P, _I64]),
     "cmsvd_quadrature": (C.c_int, [_P, C.c_double, C.c_double, C.c_int32, C.c_int32, C.c_double, _P, _P, _P]),
     "cmsvd_workspace_size": (C.c_int, [_P, C.POINTER(cmsvd_params), C.POINTER(C.c_size_t)]),
     "cmsvd_gram_workspace_size": (C.c_int, [_P, _I64, C.c_int32, C.c_int32, C.POINTER(C.c_size_t)]),
@@ -82,7 +85,7 @@ _SIGS = {
     "cmsvd_result_copy_estimate": (C.c_int, [_P, _P]),
     "cmsvd_server_create": (C.c_int, [C.c_int, C.c_size_t, C.POINTER(_P)]),
     "cmsvd_server_destroy": (C.c_int, [_P]),
-    "cmsvd_server_add_matrix": (C.c_int, [_P, C.c_int64, C.c_int64, C.c_int64, _P, _P, _P, C.c_int,
+    "cmsvd_server_add_matrix": (C.c_int, [_P, C.c_int64, C.c_int64, C.c_int64, _P, _P, _P, C.c_int, C.c_int32,
                                           C.POINTER(C.c_int)]),
     "cmsvd_server_submit": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, C.POINTER(cmsvd_params), _P,
                                       C.POINTER(C.c_int64)]),
@@ -166,8 +169,10 @@ def cmsvd_context_destroy(ctx: int) -> None:
     _check(lib().cmsvd_context_destroy(_P(ctx)), "cmsvd_context_destroy")
 
 
-def cmsvd_csr_create(ctx: int, m: int, n: int, rowptr, colidx, vals) -> int:
-    """rowptr int64[m+1], colidx int32[nnz], vals float64[nnz]: numpy (host) or torch CUDA tensors."""
+def cmsvd_csr_create(ctx: int, m: int, n: int, rowptr, colidx, vals, storage=STORE_FP64) -> int:
+    """rowptr int64[m+1], colidx int32[nnz], vals float64[nnz]: numpy (host) or torch CUDA tensors.
+    storage: STORE_FP64 / STORE_FP32 / STORE_BF16 (or "fp64", "fp32", "bf16")."""
+    storage = STORAGES[storage] if isinstance(storage, str) else int(storage)
     on_dev = 0 if isinstance(rowptr, np.ndarray) else 1
     if on_dev == 0:
         rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
@@ -176,7 +181,7 @@ def cmsvd_csr_create(ctx: int, m: int, n: int, rowptr, colidx, vals) -> int:
     nnz = int(rowptr[-1])
     h = _P()
     _check(lib().cmsvd_csr_create(_P(ctx), m, n, nnz, _ptr(rowptr), _ptr(colidx) if nnz else None,
-                                  _ptr(vals) if nnz else None, on_dev, C.byref(h)), "cmsvd_csr_create")
+                                  _ptr(vals) if nnz else None, on_dev, storage, C.byref(h)), "cmsvd_csr_create")
     return h.value
 
 
@@ -200,6 +205,13 @@ def cmsvd_spmm_f32(A: int, transpose: bool, X, Y) -> None:
     """Y = A X (or A^T X) in FP32; X, Y float32 CUDA tensors, row-major blocks."""
     L = X.shape[1]
     _check(lib().cmsvd_spmm_f32(_P(A), int(transpose), L, _ptr(X), X.stride(0), _ptr(Y), Y.stride(0)), "cmsvd_spmm_f32")
+
+
+def cmsvd_spmm_df(A: int, transpose: bool, X, Y) -> None:
+    """Y = A X (or A^T X) in double-float arithmetic; X, Y float32 CUDA tensors of shape
+    (rows, 2 L): each row holds the L high parts, then the L low parts."""
+    L = X.shape[1] // 2
+    _check(lib().cmsvd_spmm_df(_P(A), int(transpose), L, _ptr(X), X.stride(0), _ptr(Y), Y.stride(0)), "cmsvd_spmm_df")
 
 
 def cmsvd_quadrature(ctx: int, a: float, b: float, N: int, variant="linear", alpha: float = 0.1):
@@ -332,13 +344,14 @@ class Server:
         self.handle = h.value
         self.shapes = []
 
-    def add_matrix(self, A) -> int:
+    def add_matrix(self, A, storage=STORE_FP64) -> int:
+        storage = STORAGES[storage] if isinstance(storage, str) else int(storage)
         i = C.c_int()
         rp = np.ascontiguousarray(A.rowptr, dtype=np.int64)
         ci = np.ascontiguousarray(A.colidx, dtype=np.int32)
         va = np.ascontiguousarray(A.vals, dtype=np.float64)
         _check(lib().cmsvd_server_add_matrix(_P(self.handle), A.m, A.n, A.nnz, _P(rp.ctypes.data), _P(ci.ctypes.data),
-                                             _P(va.ctypes.data), 0, C.byref(i)), "cmsvd_server_add_matrix")
+                                             _P(va.ctypes.data), 0, storage, C.byref(i)), "cmsvd_server_add_matrix")
         self.shapes.append((A.m, A.n))
         return i.value
 
@@ -434,17 +447,17 @@ class Context:
 class Matrix:
     """A CSR matrix resident on the device (library-owned copy)."""
 
-    def __init__(self, ctx: Context, m: int, n: int, rowptr, colidx, vals):
+    def __init__(self, ctx: Context, m: int, n: int, rowptr, colidx, vals, storage=STORE_FP64):
         if not ctx.handle:
             raise RuntimeError("context is closed")
         self.ctx = ctx
         self.m, self.n = m, n
-        self.handle = cmsvd_csr_create(ctx.handle, m, n, rowptr, colidx, vals)
+        self.handle = cmsvd_csr_create(ctx.handle, m, n, rowptr, colidx, vals, storage)
         ctx._matrices.add(self)
 
     @classmethod
-    def from_csr(cls, ctx: Context, A) -> "Matrix":
-        return cls(ctx, A.m, A.n, A.rowptr, A.colidx, A.vals)
+    def from_csr(cls, ctx: Context, A, storage=STORE_FP64) -> "Matrix":
+        return cls(ctx, A.m, A.n, A.rowptr, A.colidx, A.vals, storage)
 
     def close(self):
         if self.handle and self.ctx.handle:
@@ -473,6 +486,14 @@ class Matrix:
         rows = self.n if transpose else self.m
         Y = torch.empty((rows, X.shape[1]), dtype=torch.float32, device=X.device)
         cmsvd_spmm_f32(self.handle, transpose, X, Y)
+        return Y
+
+    def spmm_df(self, X, transpose: bool = False):
+        """X: float32 (cols, 2 L) double-float block; returns the (rows, 2 L) double-float product."""
+        import torch
+        rows = self.n if transpose else self.m
+        Y = torch.empty((rows, X.shape[1]), dtype=torch.float32, device=X.device)
+        cmsvd_spmm_df(self.handle, transpose, X, Y)
         return Y
 
     def moments(self, a, b, p: cmsvd_params, V_in, workspace=None):

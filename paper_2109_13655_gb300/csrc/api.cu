@@ -275,7 +275,7 @@ int cmsvd_context_destroy(cmsvd_context* c) {
 }
 
 int cmsvd_csr_create(cmsvd_context* ctx, int64_t m, int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colidx,
-                     const double* vals, int where, cmsvd_matrix** out) {
+                     const double* vals, int where, int32_t storage, cmsvd_matrix** out) {
     if (!out) { set_error("NULL out"); return CMSVD_INVALID_ARG; }
     *out = nullptr;
     if (!ctx) { set_error("NULL context"); return CMSVD_INVALID_ARG; }
@@ -284,15 +284,22 @@ int cmsvd_csr_create(cmsvd_context* ctx, int64_t m, int64_t n, int64_t nnz, cons
         return CMSVD_INVALID_ARG;
     }
     if (!rowptr || (nnz > 0 && (!colidx || !vals))) { set_error("NULL CSR array"); return CMSVD_INVALID_ARG; }
+    if (storage != CMSVD_STORE_FP64 && storage != CMSVD_STORE_FP32 && storage != CMSVD_STORE_BF16) {
+        set_error("unknown storage %d", storage);
+        return CMSVD_INVALID_ARG;
+    }
     Session se;
     CM_TRY(se.open(ctx));
     cmsvd_matrix* M = new (std::nothrow) cmsvd_matrix();
     if (!M) { set_error("host allocation failed"); return CMSVD_OUT_OF_MEMORY; }
     M->ctx = ctx;
     int st = csr_upload_validate(ctx, m, n, nnz, rowptr, colidx, vals, where, &M->A);
+    if (st == CMSVD_OK) st = csr_round_storage(ctx, &M->A, storage);
     if (st == CMSVD_OK) st = csr_transpose(ctx, M->A, &M->At);
+    if (st == CMSVD_OK) st = csr_round_storage(ctx, &M->At, storage);   // values already rounded: keeps the bf16 copy
     if (st != CMSVD_OK) {
         csr_free(&M->A);
+        csr_free(&M->At);
         delete M;
         return st;
     }
@@ -335,6 +342,16 @@ int cmsvd_spmm_f32(cmsvd_matrix* A, int transpose, int64_t L, const float* X, in
     CM_TRY(se.open(A->ctx));
     CM_TRY(csr_make_fp32(A));
     CM_TRY(spmm(transpose ? A->At : A->A, (int)L, X, ldx, Y, ldy, A->ctx->s));
+    return se.close();
+}
+
+int cmsvd_spmm_df(cmsvd_matrix* A, int transpose, int64_t L, const float* X, int64_t ldx, float* Y, int64_t ldy) {
+    if (!A || !X || !Y) { set_error("NULL argument"); return CMSVD_INVALID_ARG; }
+    if (L < 1 || L > 4096 || ldx < 2 * L || ldy < 2 * L) { set_error("need 1 <= L <= 4096, ldx >= 2L, ldy >= 2L"); return CMSVD_INVALID_ARG; }
+    Session se;
+    CM_TRY(se.open(A->ctx));
+    CM_TRY(csr_make_fp32(A));
+    CM_TRY(spmm_df(transpose ? A->At : A->A, (int)L, X, ldx, Y, ldy, A->ctx->s));
     return se.close();
 }
 

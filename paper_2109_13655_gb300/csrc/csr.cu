@@ -1,5 +1,6 @@
-// CSR storage of A and A^T, validation, and the SpMM Y = A X that every
-// shifted solve (Alg. 1 steps 1-2, as H X = A^T (A X)) and step 4 (A V~) use.
+// CSR storage of A and A^T: upload, validation, rounding of the values to the storage
+// precision, the transpose, and the FP32 / bf16 copies the mixed-precision SpMM streams.
+// The SpMM kernels themselves are in spmm.cu.
 #include "internal.cuh"
 #include <cub/device/device_radix_sort.cuh>
 #include <cstdarg>
@@ -169,6 +170,7 @@ static int csr_row_order(cmsvd_context* ctx, Csr* A) {
 
 // Longest row of a CSR already on the device (sets A->max_row), and the SpMM row order.
 static int csr_row_stats(cmsvd_context* ctx, Csr* A) {
+    A->sm_count = ctx->sm_count;
     unsigned long long* d = nullptr;
     CM_CUDA(cudaMalloc(&d, sizeof(unsigned long long)));
     int st = CMSVD_OK;
@@ -235,26 +237,104 @@ void csr_free(Csr* A) {
     if (A->colidx) cudaFree(A->colidx);
     if (A->vals) cudaFree(A->vals);
     if (A->vals_f) cudaFree(A->vals_f);
+    if (A->vals_lo) cudaFree(A->vals_lo);
+    if (A->vals_h) cudaFree(A->vals_h);
     if (A->row_order) cudaFree(A->row_order);
-    A->rowptr = nullptr; A->colidx = nullptr; A->vals = nullptr; A->vals_f = nullptr; A->row_order = nullptr;
+    A->rowptr = nullptr; A->colidx = nullptr; A->vals = nullptr; A->vals_f = nullptr; A->vals_lo = nullptr;
+    A->vals_h = nullptr; A->row_order = nullptr;
 }
 
-__global__ void k_to_fp32(const double* __restrict__ x, int64_t n, float* __restrict__ y) {
+// FP32 copy of the values (round to nearest); flags a value that is not FP32-exact.
+__global__ void k_to_fp32(const double* __restrict__ x, int64_t n, float* __restrict__ y, int* __restrict__ inexact) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) y[i] = (float)x[i];
+    int bad = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float f = __double2float_rn(x[i]);
+        y[i] = f;
+        bad |= (double)f != x[i];
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(inexact, 1);
 }
 
-// FP32 copies of the values of A and A^T (round to nearest), made once per matrix.
+// lo = x - hi, rounded to FP32: x = hi + lo to within 2^-48 |x|
+__global__ void k_fp32_lo(const double* __restrict__ x, const float* __restrict__ hi, int64_t n, float* __restrict__ lo) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        lo[i] = __double2float_rn(x[i] - (double)hi[i]);
+}
+
+// FP32 copies of the values of A and A^T, made once per matrix. When some value is not
+// FP32-exact (FP64 storage of general values), the remainders lo = a - fl32(a) are kept too:
+// the double-float SpMM then multiplies by hi + lo.
 int csr_make_fp32(cmsvd_matrix* M) {
     cmsvd_context* ctx = M->ctx;
     Csr* mats[2] = {&M->A, &M->At};
     for (Csr* c : mats) {
         if (c->vals_f) continue;
         CM_CUDA(cudaMalloc(&c->vals_f, sizeof(float) * (c->nnz > 0 ? c->nnz : 1)));
+        int* flag = nullptr;
+        CM_CUDA(cudaMalloc(&flag, sizeof(int)));
+        int st = CMSVD_OK;
+        auto chk = [&](cudaError_t e, const char* w) { if (e != cudaSuccess && st == CMSVD_OK) st = cuda_fail(e, w, __FILE__, __LINE__); };
+        chk(cudaMemsetAsync(flag, 0, sizeof(int), ctx->s), "memset");
         if (c->nnz > 0) {
-            k_to_fp32<<<ctx->sm_count * 4, 256, 0, ctx->s>>>(c->vals, c->nnz, c->vals_f);
+            k_to_fp32<<<ctx->sm_count * 4, 256, 0, ctx->s>>>(c->vals, c->nnz, c->vals_f, flag);
+            note_launch();
+            chk(cudaGetLastError(), "k_to_fp32");
+        }
+        chk(cudaMemcpyAsync(ctx->pinned, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->s), "copy flag");
+        chk(cudaStreamSynchronize(ctx->s), "sync");
+        cudaFree(flag);
+        if (st != CMSVD_OK) return st;
+        c->f32_exact = ctx->pinned[0] ? 0 : 1;
+        if (!c->f32_exact) {
+            CM_CUDA(cudaMalloc(&c->vals_lo, sizeof(float) * c->nnz));
+            k_fp32_lo<<<ctx->sm_count * 4, 256, 0, ctx->s>>>(c->vals, c->vals_f, c->nnz, c->vals_lo);
             CM_LAUNCH();
         }
+    }
+    return CMSVD_OK;
+}
+
+// Rounds the FP64 values to the storage precision in place (FP32 or bf16, round to nearest
+// even) and, for bf16, keeps the 16-bit patterns the mixed-precision SpMM streams.
+__global__ void k_round_storage(double* __restrict__ v, int64_t n, int storage, uint16_t* __restrict__ h,
+                                int* __restrict__ overflow) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float f = __double2float_rn(v[i]);
+        if (!isfinite(f)) atomicOr(overflow, 1);
+        if (storage == CMSVD_STORE_FP32) {
+            v[i] = (double)f;
+        } else {
+            uint32_t u = __float_as_uint(f);
+            if ((u & 0x7f800000u) != 0x7f800000u) u += 0x7fffu + ((u >> 16) & 1u);   // round to nearest even
+            const uint16_t b = (uint16_t)(u >> 16);
+            h[i] = b;
+            v[i] = (double)__uint_as_float((uint32_t)b << 16);
+        }
+    }
+}
+
+int csr_round_storage(cmsvd_context* ctx, Csr* A, int storage) {
+    A->storage = storage;
+    if (storage == CMSVD_STORE_FP64 || A->nnz == 0) return CMSVD_OK;
+    if (storage == CMSVD_STORE_BF16) CM_CUDA(cudaMalloc(&A->vals_h, sizeof(uint16_t) * A->nnz));
+    int* flag = nullptr;
+    CM_CUDA(cudaMalloc(&flag, sizeof(int)));
+    int st = CMSVD_OK;
+    auto chk = [&](cudaError_t e, const char* w) { if (e != cudaSuccess && st == CMSVD_OK) st = cuda_fail(e, w, __FILE__, __LINE__); };
+    chk(cudaMemsetAsync(flag, 0, sizeof(int), ctx->s), "memset");
+    k_round_storage<<<ctx->sm_count * 4, 256, 0, ctx->s>>>(A->vals, A->nnz, storage, A->vals_h, flag);
+    note_launch();
+    chk(cudaGetLastError(), "k_round_storage");
+    chk(cudaMemcpyAsync(ctx->pinned, flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->s), "copy flag");
+    chk(cudaStreamSynchronize(ctx->s), "sync");
+    cudaFree(flag);
+    if (st != CMSVD_OK) return st;
+    if (ctx->pinned[0]) {
+        set_error("a value is outside the range of the storage precision");
+        return CMSVD_INVALID_MATRIX;
     }
     return CMSVD_OK;
 }
@@ -377,165 +457,6 @@ int csr_transpose(cmsvd_context* ctx, const Csr& A, Csr* At) {
     if (st != CMSVD_OK) { csr_free(&T); return st; }
     *At = T;
     return CMSVD_OK;
-}
-
-// ----------------------------------------------------------------------------- SpMM
-// One group of LPR lanes per row; lane l owns columns l, l+LPR, ... of the
-// row-major L-column block. The row's (col, val) pairs are loaded cooperatively
-// and broadcast with shuffles, so every nonzero reads one contiguous L-vector of
-// X. Each output element is summed in the row's storage order (deterministic).
-__device__ __forceinline__ double fma_rn_t(double a, double b, double c) { return __fma_rn(a, b, c); }
-__device__ __forceinline__ float fma_rn_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-
-// One chunk of up to LPR nonzeros of a row, broadcast from the lanes that loaded them:
-// the X rows of SPMM_ILP nonzeros are gathered before their multiply-adds, so that many
-// gathers are in flight (a gather whose address comes from a shuffle otherwise waits for
-// the previous multiply-add). The multiply-adds stay in the row's storage order.
-constexpr int SPMM_ILP = 8;
-template <typename T, int LPR, int CPL>
-__device__ __forceinline__ void spmm_chunk(unsigned mask, int32_t mc, T mv, int cnt, const T* __restrict__ X,
-                                           int64_t ldx, int c0, int lane, int L, T (&acc)[CPL]) {
-    int k0 = 0;
-    for (; k0 + SPMM_ILP <= cnt; k0 += SPMM_ILP) {   // full groups: gathers first, then the multiply-adds
-        T xv[SPMM_ILP][CPL];
-        T vv[SPMM_ILP];
-#pragma unroll
-        for (int u = 0; u < SPMM_ILP; ++u) {
-            const int32_t col = __shfl_sync(mask, mc, k0 + u, LPR);
-            vv[u] = __shfl_sync(mask, mv, k0 + u, LPR);
-            const T* xr = X + (int64_t)col * ldx + c0 + lane;
-#pragma unroll
-            for (int q = 0; q < CPL; ++q) xv[u][q] = c0 + lane + q * LPR < L ? __ldg(xr + q * LPR) : (T)0;
-        }
-#pragma unroll
-        for (int u = 0; u < SPMM_ILP; ++u)
-#pragma unroll
-            for (int q = 0; q < CPL; ++q)
-                if (c0 + lane + q * LPR < L) acc[q] = fma_rn_t(vv[u], xv[u][q], acc[q]);
-    }
-    for (; k0 < cnt; ++k0) {                          // the rest (short rows take only this path)
-        const int32_t col = __shfl_sync(mask, mc, k0, LPR);
-        const T v = __shfl_sync(mask, mv, k0, LPR);
-        const T* xr = X + (int64_t)col * ldx + c0 + lane;
-#pragma unroll
-        for (int q = 0; q < CPL; ++q)
-            if (c0 + lane + q * LPR < L) acc[q] = fma_rn_t(v, __ldg(xr + q * LPR), acc[q]);
-    }
-}
-
-template <typename T, int LPR, int CPL>
-__global__ void __launch_bounds__(256) k_spmm(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
-                                              const T* __restrict__ vals, int64_t rows, int L,
-                                              const T* __restrict__ X, int64_t ldx, T* __restrict__ Y,
-                                              int64_t ldy, const int32_t* __restrict__ order) {
-    const int lane = threadIdx.x % LPR;
-    const int64_t group = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / LPR;
-    const int64_t ngroups = ((int64_t)gridDim.x * blockDim.x) / LPR;
-    const unsigned mask = LPR == 32 ? 0xffffffffu : (((1u << LPR) - 1u) << ((threadIdx.x & 31) / LPR * LPR));
-    for (int64_t rr = group; rr < rows; rr += ngroups) {
-        const int64_t r = order ? (int64_t)order[rr] : rr;
-        const int64_t s = rowptr[r], e = rowptr[r + 1];
-        for (int c0 = 0; c0 < L; c0 += LPR * CPL) {
-            T acc[CPL];
-#pragma unroll
-            for (int q = 0; q < CPL; ++q) acc[q] = (T)0;
-            for (int64_t p0 = s; p0 < e; p0 += LPR) {
-                const int64_t p = p0 + lane;
-                int32_t mc = 0;
-                T mv = (T)0;
-                if (p < e) { mc = colidx[p]; mv = vals[p]; }
-                const int cnt = (int)((e - p0) < LPR ? (e - p0) : LPR);
-                spmm_chunk<T, LPR, CPL>(mask, mc, mv, cnt, X, ldx, c0, lane, L, acc);
-            }
-#pragma unroll
-            for (int q = 0; q < CPL; ++q)
-                if (c0 + lane + q * LPR < L) Y[r * ldy + c0 + lane + q * LPR] = acc[q];
-        }
-    }
-}
-
-// Long rows (a few rows holding most nonzeros, e.g. the transpose of a matrix whose
-// columns are image pixels): one CTA per row. Its 256 / LPR groups take contiguous,
-// equal slices of the row, and their partial sums are added in slice order, so the
-// result is deterministic (the summation order differs from k_spmm's).
-template <typename T, int LPR, int CPL>
-__global__ void __launch_bounds__(256) k_spmm_rowcta(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colidx,
-                                                     const T* __restrict__ vals, int64_t rows, int L,
-                                                     const T* __restrict__ X, int64_t ldx, T* __restrict__ Y,
-                                                     int64_t ldy, const int32_t* __restrict__ order) {
-    constexpr int G = 256 / LPR;
-    __shared__ T part[G][LPR * CPL];
-    const int lane = threadIdx.x % LPR, g = threadIdx.x / LPR;
-    const unsigned mask = LPR == 32 ? 0xffffffffu : (((1u << LPR) - 1u) << ((threadIdx.x & 31) / LPR * LPR));
-    for (int64_t rr = blockIdx.x; rr < rows; rr += gridDim.x) {
-        const int64_t r = order ? (int64_t)order[rr] : rr;
-        const int64_t rs = rowptr[r], re = rowptr[r + 1];
-        const int64_t slice = (re - rs + G - 1) / G;
-        const int64_t s = rs + g * slice < re ? rs + g * slice : re;
-        const int64_t e = s + slice < re ? s + slice : re;
-        for (int c0 = 0; c0 < L; c0 += LPR * CPL) {
-            T acc[CPL];
-#pragma unroll
-            for (int q = 0; q < CPL; ++q) acc[q] = (T)0;
-            for (int64_t p0 = s; p0 < e; p0 += LPR) {
-                const int64_t p = p0 + lane;
-                int32_t mc = 0;
-                T mv = (T)0;
-                if (p < e) { mc = colidx[p]; mv = vals[p]; }
-                const int cnt = (int)((e - p0) < LPR ? (e - p0) : LPR);
-                spmm_chunk<T, LPR, CPL>(mask, mc, mv, cnt, X, ldx, c0, lane, L, acc);
-            }
-#pragma unroll
-            for (int q = 0; q < CPL; ++q) part[g][lane + q * LPR] = acc[q];
-            __syncthreads();
-            for (int c = threadIdx.x; c < LPR * CPL; c += blockDim.x) {
-                if (c0 + c < L) {
-                    T sum = part[0][c];
-                    for (int h = 1; h < G; ++h) sum += part[h][c];
-                    Y[r * ldy + c0 + c] = sum;
-                }
-            }
-            __syncthreads();
-        }
-    }
-}
-
-template <typename T>
-static int spmm_t(const Csr& A, const T* vals, int L, const T* X, int64_t ldx, T* Y, int64_t ldy, cudaStream_t s) {
-    if (A.m == 0 || L <= 0) return CMSVD_OK;
-    // compulsory traffic: A (values, indices, row pointers), X once, Y once
-    const double e = (double)sizeof(T);
-    ProfScope ps(CMSVD_PROF_SPMM, s, (e + 4.0) * A.nnz + 8.0 * (A.m + 1) + e * L * (A.n + A.m), 2.0 * A.nnz * L);
-    const int dev_sms = 152;
-    if (A.max_row > 2048) {
-        const unsigned grid = (unsigned)(A.m < dev_sms * 8 ? A.m : dev_sms * 8);
-        if (L <= 8) k_spmm_rowcta<T, 8, 1><<<grid, 256, 0, s>>>(A.rowptr, A.colidx, vals, A.m, L, X, ldx, Y, ldy, A.row_order);
-        else if (L <= 16) k_spmm_rowcta<T, 16, 1><<<grid, 256, 0, s>>>(A.rowptr, A.colidx, vals, A.m, L, X, ldx, Y, ldy, A.row_order);
-        else if (L <= 32) k_spmm_rowcta<T, 32, 1><<<grid, 256, 0, s>>>(A.rowptr, A.colidx, vals, A.m, L, X, ldx, Y, ldy, A.row_order);
-        else k_spmm_rowcta<T, 32, 4><<<grid, 256, 0, s>>>(A.rowptr, A.colidx, vals, A.m, L, X, ldx, Y, ldy, A.row_order);
-        CM_LAUNCH();
-        return CMSVD_OK;
-    }
-    if (L <= 8) {
-        k_spmm<T, 8, 1><<<grid_for(A.m, 256 / 8, dev_sms * 32), 256, 0, s>>>(A.rowptr, A.colidx, vals, A.m, L, X, ldx, Y, ldy, A.row_order);
-    } else if (L <= 16) {
-        k_spmm<T, 16, 1><<<grid_for(A.m, 256 / 16, dev_sms * 32), 256, 0, s>>>(A.rowptr, A.colidx, vals, A.m, L, X, ldx, Y, ldy, A.row_order);
-    } else if (L <= 32) {
-        k_spmm<T, 32, 1><<<grid_for(A.m, 8, dev_sms * 32), 256, 0, s>>>(A.rowptr, A.colidx, vals, A.m, L, X, ldx, Y, ldy, A.row_order);
-    } else {
-        k_spmm<T, 32, 4><<<grid_for(A.m, 8, dev_sms * 32), 256, 0, s>>>(A.rowptr, A.colidx, vals, A.m, L, X, ldx, Y, ldy, A.row_order);
-    }
-    CM_LAUNCH();
-    return CMSVD_OK;
-}
-
-int spmm(const Csr& A, int L, const double* X, int64_t ldx, double* Y, int64_t ldy, cudaStream_t s) {
-    return spmm_t<double>(A, A.vals, L, X, ldx, Y, ldy, s);
-}
-
-int spmm(const Csr& A, int L, const float* X, int64_t ldx, float* Y, int64_t ldy, cudaStream_t s) {
-    if (!A.vals_f) { set_error("FP32 values of A were not made"); return CMSVD_INVALID_ARG; }
-    return spmm_t<float>(A, A.vals_f, L, X, ldx, Y, ldy, s);
 }
 
 }  // namespace cmsvd

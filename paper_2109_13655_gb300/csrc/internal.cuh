@@ -56,14 +56,25 @@ void prof_reset(bool timing);
 void prof_collect(cmsvd_stats* st);   // synchronizes the recorded events
 
 // ----------------------------------------------------------------------------- objects
+// SpMM configuration picked by the autotuner (spmm.cu) for one (operand kind, L) pair.
+// natural = 1 takes the rows in storage order instead of the locality order (row_order).
+struct SpmmCfg { int lpr = 0, unroll = 0, slices = 1, blocks_per_sm = 0, natural = 0; float ms = 0.f; };
+struct SpmmTuneEntry { int kind = -1, L = 0; SpmmCfg cfg; };
+
 struct Csr {
     int64_t m = 0, n = 0, nnz = 0;
     int64_t* rowptr = nullptr;   // device, m+1
     int32_t* colidx = nullptr;   // device, nnz
-    double* vals = nullptr;      // device, nnz
-    float* vals_f = nullptr;     // device, nnz: FP32 copy for the mixed-precision Krylov path (made on demand)
+    double* vals = nullptr;      // device, nnz: the values as FP64 (after rounding to the storage precision)
+    float* vals_f = nullptr;     // device, nnz: FP32 values (made on demand for FP32 / double-float products)
+    float* vals_lo = nullptr;    // device, nnz: a - fl32(a), made with vals_f when some value is not FP32-exact
+    uint16_t* vals_h = nullptr;  // device, nnz: bf16 bit patterns (storage BF16)
+    int storage = CMSVD_STORE_FP64;
+    int f32_exact = -1;          // 1: every value is FP32-representable (known once vals_f exists)
+    int sm_count = 0;
     int64_t max_row = 0;         // longest row (nonzeros); long rows switch the SpMM to one CTA per row
     int32_t* row_order = nullptr; // device, m: rows sorted by their first column (SpMM processing order)
+    SpmmTuneEntry tune[64];      // autotuner cache (host)
 };
 
 struct Components {             // connected components of the column graph (A^T A)
@@ -82,6 +93,27 @@ struct Components {             // connected components of the column graph (A^T
     int64_t* comp_first_dev = nullptr;  // device copy
     int32_t* col_local = nullptr;       // device [n], local index of a column inside its component
 };
+
+// ----------------------------------------------------------------------------- double-float arithmetic
+// A value x is carried as an unevaluated sum hi + lo of two FP32 numbers (|lo| <= ulp(hi)/2
+// after normalization). Building blocks, all with explicit round-to-nearest intrinsics so that
+// the compiler neither contracts nor reorders them:
+//   two_sum       Knuth's TwoSum: s + e == a + b exactly, for any a, b;
+//   fast_two_sum  Dekker's Fast2Sum: the same when |a| >= |b| (or a == 0);
+//   two_prod      the FMA-based exact product: p + e == a * b exactly.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
 
 }  // namespace cmsvd
 
@@ -136,12 +168,22 @@ struct Arena {
 int csr_upload_validate(cmsvd_context* ctx, int64_t m, int64_t n, int64_t nnz, const int64_t* rowptr,
                         const int32_t* colidx, const double* vals, int where, Csr* out);
 int csr_transpose(cmsvd_context* ctx, const Csr& A, Csr* At);
+// Rounds A's values to the storage precision (cmsvd_storage) in place; bf16 also keeps the
+// 16-bit patterns. CMSVD_INVALID_MATRIX when a value overflows the storage precision.
+int csr_round_storage(cmsvd_context* ctx, Csr* A, int storage);
 void csr_free(Csr* A);
-// Y (rows x L, ldy) = A X (X: ncols x L, ldx); optional per-column scale of the result.
+// Y (rows x L, ldy) = A X (X: ncols x L, ldx); every kernel variant sums each output
+// element in the row's storage order, so the result does not depend on the variant.
 int spmm(const Csr& A, int L, const double* X, int64_t ldx, double* Y, int64_t ldy, cudaStream_t s);
-// FP32 SpMM (mixed path): values from A.vals_f, FP32 accumulation.
+// FP32 SpMM: FP32 values of A (A.vals_f, or the bf16 values for bf16 storage), FP32 accumulation.
 int spmm(const Csr& A, int L, const float* X, int64_t ldx, float* Y, int64_t ldy, cudaStream_t s);
-int csr_make_fp32(cmsvd_matrix* M);
+// Double-float SpMM (FP32 arithmetic, error-free products and compensated sums): X and Y
+// hold each row as L high parts followed by L low parts (ld in floats, >= 2 L).
+int spmm_df(const Csr& A, int L, const float* X, int64_t ldx, float* Y, int64_t ldy, cudaStream_t s);
+// Runs the autotuner for (A, kind, L) now, on the given buffers, outside any stream capture.
+enum { SPMM_KIND_F64 = 0, SPMM_KIND_F32 = 1, SPMM_KIND_DF = 2 };
+int spmm_tune(Csr& A, int kind, int L, const void* X, int64_t ldx, void* Y, int64_t ldy, cudaStream_t s);
+int csr_make_fp32(cmsvd_matrix* M);   // vals_f (and vals_lo when needed) of A and A^T
 int components_build(cmsvd_matrix* M);
 void components_free(Components* c);
 

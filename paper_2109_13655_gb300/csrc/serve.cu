@@ -47,7 +47,8 @@ struct SrvReq {
 bool acceptable(int st) { return st == CMSVD_OK || st == CMSVD_NOT_CONVERGED || st == CMSVD_SUBSPACE_SATURATED; }
 
 size_t csr_bytes(const cmsvd::Csr& A) {
-    return sizeof(int64_t) * (A.m + 1) + (sizeof(int32_t) + sizeof(double)) * A.nnz + (A.vals_f ? sizeof(float) * A.nnz : 0);
+    return sizeof(int64_t) * (A.m + 1) + (sizeof(int32_t) + sizeof(double)) * A.nnz + (A.vals_f ? sizeof(float) * A.nnz : 0) +
+           (A.vals_lo ? sizeof(float) * A.nnz : 0) + (A.vals_h ? sizeof(uint16_t) * A.nnz : 0) + sizeof(int32_t) * A.m;
 }
 
 }  // namespace
@@ -235,12 +236,12 @@ int cmsvd_server_destroy(cmsvd_server* S) {
 }
 
 int cmsvd_server_add_matrix(cmsvd_server* S, int64_t m, int64_t n, int64_t nnz, const int64_t* rowptr,
-                            const int32_t* colidx, const double* vals, int vals_on_device, int* id) {
+                            const int32_t* colidx, const double* vals, int vals_on_device, int32_t storage, int* id) {
     using namespace cmsvd;
     if (!S || !id) { set_error("NULL argument"); return CMSVD_INVALID_ARG; }
     cmsvd_matrix* base = nullptr;
     std::lock_guard<std::mutex> ulk(S->umu);   // one upload at a time on the upload context
-    CM_TRY(cmsvd_csr_create(S->uctx, m, n, nnz, rowptr, colidx, vals, vals_on_device, &base));
+    CM_TRY(cmsvd_csr_create(S->uctx, m, n, nnz, rowptr, colidx, vals, vals_on_device, storage, &base));
     // build what solves would otherwise create lazily, so that the per-slot views only read it
     int st = components_build(base);
     if (st == CMSVD_OK) st = csr_make_fp32(base);

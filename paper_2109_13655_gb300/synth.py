@@ -13,6 +13,10 @@ synthetic stand-ins:
 * ``block_permuted``    -- dense blocks on a block diagonal with random row and
                            column permutations; its spectrum is the union of
                            the blocks' spectra, so it is known exactly.
+* ``banded_random``     -- m x n CSR with k_band columns near the row's diagonal
+                           position and k_rand uniform-random columns per row,
+                           U(-1,1) values rounded to bf16 (the 2e6 x 1e6
+                           mixed-precision case).
 * ``model_problem``     -- the Experiment II model problems
                            A = U diag(sigma) V^T, m = 1000, n = 200 (Sec. 4.2).
 * ``gaussian_block``    -- the real Gaussian input block V_in (n x L).
@@ -152,6 +156,39 @@ def block_permuted(nb: int, bm: int, bn: int, seed: int, dist: str = "normal") -
     cols = col_perm[bi * bn + jj].ravel()
     A = csr_from_coo(nb * bm, nb * bn, rows, cols, blocks.ravel())
     return BlockPermuted(A, blocks, row_perm, col_perm)
+
+
+def banded_random(m: int = 2_000_000, n: int = 1_000_000, k_band: int = 8, k_rand: int = 8,
+                  half_width: int = 5000, seed: int = 10) -> CSR:
+    """m x n CSR with k_band + k_rand distinct columns per row (the 2e6 x 1e6 case).
+
+    Row i's "band" columns are uniform in [c_i - half_width, c_i + half_width] clipped to
+    [0, n), with c_i = floor(i n / m); its other k_rand columns are uniform over [0, n).
+    A row whose draws collide is drawn again as a whole. Values are U(-1, 1) rounded to
+    bf16-representable numbers, so FP64, FP32 and bf16 storage hold the same matrix.
+    """
+    rng = np.random.default_rng(seed)
+    k = k_band + k_rand
+    c = (np.arange(m, dtype=np.int64) * n) // m
+    lo = np.maximum(c - half_width, 0)
+    width = np.minimum(c + half_width, n - 1) - lo + 1
+
+    def draw(rows):
+        cols = np.empty((rows.size, k), dtype=np.int64)
+        cols[:, :k_band] = lo[rows, None] + (rng.random((rows.size, k_band)) * width[rows, None]).astype(np.int64)
+        cols[:, k_band:] = rng.integers(0, n, size=(rows.size, k_rand))
+        cols.sort(axis=1)
+        return cols
+
+    cols = draw(np.arange(m))
+    while True:
+        bad = np.nonzero((np.diff(cols, axis=1) == 0).any(axis=1))[0]
+        if bad.size == 0:
+            break
+        cols[bad] = draw(bad)
+    vals = bf16_round(rng.uniform(-1.0, 1.0, size=m * k))
+    rowptr = np.arange(0, m * k + 1, k, dtype=np.int64)
+    return CSR(m, n, rowptr, cols.ravel().astype(np.int32), vals)
 
 
 def _haar_orthonormal(rng: np.random.Generator, rows: int, cols: int) -> np.ndarray:

@@ -57,7 +57,7 @@ def test_null_arguments_rejected(lib):
     import ctypes as C
     assert lib.cmsvd_params_default(None) == B.INVALID_ARG
     assert lib.cmsvd_context_create(None, None) == B.INVALID_ARG
-    assert lib.cmsvd_csr_create(None, 2, 2, 0, None, None, None, 0, C.byref(C.c_void_p())) == B.INVALID_ARG
+    assert lib.cmsvd_csr_create(None, 2, 2, 0, None, None, None, 0, 0, C.byref(C.c_void_p())) == B.INVALID_ARG
     assert lib.cmsvd_result_count(None, None) == B.INVALID_ARG
     assert lib.cmsvd_context_destroy(None) == B.OK
     assert lib.cmsvd_csr_destroy(None) == B.OK

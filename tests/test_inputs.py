@@ -54,3 +54,20 @@ def test_batched_problems_counts():
         assert p["N"] == 32 and p["M"] == 4 and p["L"] in (16, 32)
         assert p["kind"] == ("exterior" if i % 2 == 0 else "interior")
         assert abs(p["t"] - p["L"] * p["M"] // 3) <= 10
+
+
+def test_banded_random_structure():
+    """The 2e6 x 1e6 banded-plus-random construction (here at a small size): k_band columns
+    within half_width of floor(i n / m), k_rand further distinct columns, sorted, bf16 values."""
+    m, n, hw = 4000, 2000, 50
+    A = synth.banded_random(m, n, half_width=hw, seed=3)
+    assert (A.m, A.n, A.nnz) == (m, n, 16 * m)
+    cols = A.colidx.reshape(m, 16).astype(np.int64)
+    assert np.all(np.diff(cols, axis=1) > 0)
+    c = (np.arange(m) * n) // m
+    near = np.abs(cols - c[:, None]) <= hw
+    assert np.all(near.sum(axis=1) >= 8)            # the 8 band columns (random ones may fall in too)
+    assert np.all(synth.bf16_round(A.vals) == A.vals)
+    assert np.all(np.abs(A.vals) <= 1.0)
+    B = synth.banded_random(m, n, half_width=hw, seed=3)
+    assert np.array_equal(A.colidx, B.colidx) and np.array_equal(A.vals, B.vals)

@@ -553,3 +553,30 @@ def test_mutation_iteration_skipped_caught(monkeypatch):
     monkeypatch.setattr(O, "moments", lambda solver, q, V, M, ell=1, scaled=True, extra=0:
                         orig(solver, q, V, M, 1, scaled, extra))
     assert theorem2_excess("linear", 2) > 1.0
+
+
+# ---------------------------------------------------------------------------
+# Largest singular values (expected values of an exterior interval at the top)
+# ---------------------------------------------------------------------------
+def test_largest_singular_values_against_dense_svd():
+    """oracle.largest_singular_values (ARPACK on A^T A) against numpy's dense SVD on small
+    instances of the banded-plus-random construction: the k largest values, descending."""
+    for seed, (m, n, hw) in enumerate([(1200, 600, 40), (3000, 1000, 100)]):
+        A = synth.banded_random(m, n, half_width=hw, seed=seed)
+        d = np.linalg.svd(A.to_dense(), compute_uv=False)
+        for k in (1, 12, 40):
+            s = O.largest_singular_values(A, k)
+            assert s.shape == (k,)
+            assert np.all(np.diff(s) <= 0)
+            assert np.max(np.abs(s - d[:k]) / d[:k]) < 1e-12
+
+
+def test_exterior_interval_top_values_match_method():
+    """For [a, b] with b above sigma_max the method (direct solves) returns exactly the values
+    above a, which are the largest ones: the two oracles agree."""
+    A = synth.banded_random(1500, 500, half_width=30, seed=5)
+    top = O.largest_singular_values(A, 12)
+    a, b = 0.5 * (top[9] + top[10]), 1.01 * top[0]
+    r = O.solve_interval(A, a, b, 32, 16, 4, synth.gaussian_block(500, 16, 1), norm_A=top[0])
+    assert r.sigma.size == 10
+    assert np.max(np.abs(np.sort(r.sigma)[::-1] - top[:10]) / top[:10]) < 1e-12
