@@ -10,6 +10,12 @@ if it returns all 200 triplets with residual <= 1e-10.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
 
+Secondary keys of the same line: the 2e6 x 1e6 mixed-precision workload (banded plus
+random columns, 32M nonzeros, Krylov solver) in mixed precision and in FP64
+(c3_mixed_vs_fp64: one timed solve each, about 70 s), the full-scale SpMM roofline
+(spmm_roofline), the 2000 x 1000 Krylov workload in both precisions (krylov_workload),
+64 batched problems (batched_workload) and the serving loop (serving_workload).
+
 value: device-resident inputs (the matrix and V_in stay in HBM), CUDA events
 around each call on the caller's stream, L2 flushed (256 MiB write) between
 steps outside the timed window. e2e: the same through the C ABI with V_in in
@@ -36,7 +42,7 @@ sys.path.insert(0, ROOT)
 
 from paper_2109_13655_gb300 import synth  # noqa: E402
 
-METRIC = "interval-SVD solves/s at residual<=1e-10 (FP64)"
+METRIC = "interval-SVD solves/s at residual<=1e-10, mixed vs FP64 on 1 GB300; p50/p99 latency"
 UNIT = "solves/s"
 
 
@@ -57,6 +63,16 @@ def workload(name: str):
         cfg = dict(N=16, L=16, M=4, ell=1)
         return dict(name=name, A=A, a=a, b=b, t=20, norm_A=float(s[0]), cfg=cfg, seed=1,
                     desc="2000x1000 CSR, 8 nnz/row N(0,1), sigma ranked 400-419, N=16 L=16 M=4")
+    if name == "banded_random_2000000x1000000":
+        g = np.loadtxt(os.path.join(ROOT, "tests", "golden", "banded_random_2000000x1000000_top.txt"))
+        t = 85
+        cfg = dict(N=32, L=32, M=8, ell=2, alpha=0.2)
+        return dict(name=name, A=synth.banded_random(), a=0.5 * (g[t - 1] + g[t]), b=1.01 * g[0], t=t,
+                    norm_A=float(g[0]), cfg=cfg, seed=11, golden=g[:t],
+                    desc="2000000x1000000 CSR, 16 nnz/row (8 within +-5000 of the diagonal position, 8 uniform), "
+                         "U(-1,1) bf16-exact values (nnz 32M); exterior window of the 85 largest sigma (a at the "
+                         "widest relative gap near the 100th value, b = 1.01 sigma_1); N=32 L=32 M=8 ell=2 "
+                         "alpha=0.2; Krylov solver")
     raise ValueError(name)
 
 
@@ -199,8 +215,11 @@ def run_ours(args, w, rank, world, local_rank):
         t = B.cmsvd_result_count(r)
         return st, t == w["t"] and st["max_res_u"] <= 1e-10 and st["max_res_v"] <= 1e-10
 
-    for _ in range(args.warmup):
+    setup_ms = None
+    for k in range(args.warmup):
         _, r = one(Vin)
+        if k == 0:   # the first solve on a matrix builds the components of A^T A (solver AUTO), on the host
+            setup_ms = B.cmsvd_result_stats(r)["ms_components"]
         B.cmsvd_result_destroy(r)
     torch.cuda.synchronize()
     if dist:
@@ -248,6 +267,7 @@ def run_ours(args, w, rank, world, local_rank):
     batched = measure_batched(B, dev) if (rank == 0 and args.batched) else None
     serving = measure_serving(B) if (rank == 0 and args.serving) else None
     spmm_big = measure_spmm(B, dev) if (rank == 0 and args.spmm) else None
+    c3 = measure_c3(B, dev) if (rank == 0 and args.c3) else None
     if rank == 0:
         value = job_throughput(args.steps, world, tmax)
         prof = aggregate_profile(stats)
@@ -263,6 +283,7 @@ def run_ours(args, w, rank, world, local_rank):
             "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99)),
                            "min": float(np.min(ms))},
             "all_steps_valid": bool(valid),
+            "setup_ms_outside_timing": {"components_of_AtA": setup_ms},
             "phase_ms": {k: float(np.median([s[k] for s in stats])) for k in
                          ("ms_solve", "ms_truncate", "ms_qr", "ms_ritz")},
             "clocks": clk.summary(),
@@ -283,6 +304,8 @@ def run_ours(args, w, rank, world, local_rank):
             line["serving_workload"] = serving
         if spmm_big is not None:
             line["spmm_roofline"] = spmm_big
+        if c3 is not None:
+            line["c3_mixed_vs_fp64"] = c3
         if args.cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w)
         print(json.dumps(line), flush=True)
@@ -339,6 +362,77 @@ def measure_krylov(B, ctx, dev, steps=3):
                      "ms_rayleigh_ritz": st["ms_truncate"] + st["ms_qr"] + st["ms_ritz"]}
         del ws
     M.close()
+    return out
+
+
+def measure_c3(B, dev):
+    """The 2e6 x 1e6 mixed-precision workload (banded plus random columns, 32M nonzeros) through
+    the Krylov solver: mixed precision (double-float Lanczos on the FP32 pipe, bf16 storage of A)
+    against plain FP64 (FP64 storage), each as one warm-up solve cut short at 96 Lanczos steps
+    per pass (it runs the SpMM autotuner and the graph captures) and one timed full solve (CUDA
+    events on the caller's stream; the 129 MB L2 is far smaller than the inputs: A and A^T take
+    0.4-0.8 GB, every Lanczos block 256 MB). Each solve must return all 85 values with
+    residuals <= 1e-10 and sigma within 1e-10 of the expected values (ARPACK, tests/golden).
+    Reports per precision: solves/s, Lanczos steps, phase times, kernel classes, the SpMM
+    autotuner's picks; and per triplet the mixed-vs-FP64 differences of sigma and residuals."""
+    import torch
+    w = workload("banded_random_2000000x1000000")
+    A, cfg = w["A"], w["cfg"]
+    ctx = B.Context()
+    Vin = torch.from_numpy(synth.gaussian_block(A.n, cfg["L"], w["seed"])).to(dev)
+    out = {"description": w["desc"], "interval": [w["a"], w["b"]], "t": w["t"]}
+    res = {}
+    for name, prec, storage in (("mixed", B.MIXED, "bf16"), ("fp64", B.FP64, "fp64")):
+        M = B.Matrix.from_csr(ctx, A, storage=storage)
+        p = B.params(N=cfg["N"], L=cfg["L"], M=cfg["M"], ell=cfg["ell"], alpha=cfg["alpha"], solver="krylov",
+                     precision=prec, norm_A=w["norm_A"], profile=1)
+        ws = M.workspace(p)
+        pw = B.params(N=cfg["N"], L=cfg["L"], M=cfg["M"], ell=1, alpha=cfg["alpha"], solver="krylov",
+                      precision=prec, norm_A=w["norm_A"], max_iter=96)
+        _, r = B.cmsvd_solve_interval(M.handle, w["a"], w["b"], pw, Vin, ws)          # warm-up
+        B.cmsvd_result_destroy(r)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream = torch.cuda.current_stream()
+        e0.record(stream)
+        status, r = B.cmsvd_solve_interval(M.handle, w["a"], w["b"], p, Vin, ws)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        t = B.cmsvd_result_count(r)
+        st = B.cmsvd_result_stats(r)
+        sig, ru, rv = np.zeros(t), np.zeros(t), np.zeros(t)
+        B.cmsvd_result_copy(r, sig, None, None, ru, rv)
+        B.cmsvd_result_destroy(r)
+        truth = np.sort(w["golden"])
+        ok = t == w["t"] and float(max(ru.max(), rv.max())) <= 1e-10 and \
+            float(np.max(np.abs(sig - truth) / truth)) <= 1e-10
+        res[name] = (sig, ru, rv)
+        tun = {"A": B.cmsvd_spmm_tuning(M.handle, False, 2 if name == "mixed" else 0, cfg["L"]),
+               "At": B.cmsvd_spmm_tuning(M.handle, True, 2 if name == "mixed" else 0, cfg["L"])}
+        prof = {B.PROFILE_CLASSES[i]: {"ms": st["prof_ms"][i], "launches": st["prof_launches"][i],
+                                       "bytes": st["prof_bytes"][i], "flops": st["prof_flops"][i]}
+                for i in range(len(B.PROFILE_CLASSES)) if st["prof_launches"][i]}
+        out[name] = {"solves_per_s": 1e3 / ms, "ms_per_solve": ms, "status": int(status), "found": int(t),
+                     "all_valid": bool(ok), "lanczos_steps_last_filter": int(st["krylov_iters"]),
+                     "max_sigma_rel_err_vs_expected": float(np.max(np.abs(sig - truth) / truth)) if t == w["t"] else None,
+                     "max_res_u": float(ru.max()) if t else None, "max_res_v": float(rv.max()) if t else None,
+                     "rank": int(st["rank"]), "kernel_launches": int(st["kernel_launches"]),
+                     "phase_ms": {k: st[k] for k in ("ms_solve", "ms_truncate", "ms_qr", "ms_ritz")},
+                     "kernel_profile": prof, "spmm_autotune": tun,
+                     "storage": storage}
+        M.close()
+        del ws
+        torch.cuda.empty_cache()
+    ctx.close()
+    if res["mixed"][0].size == res["fp64"][0].size and res["fp64"][0].size:
+        sm, rm, _ = res["mixed"]
+        sf, rf, _ = res["fp64"]
+        out["mixed_vs_fp64"] = {"speedup": out["mixed"]["solves_per_s"] / out["fp64"]["solves_per_s"],
+                                "max_sigma_rel_diff": float(np.max(np.abs(sm - sf) / sf)),
+                                "max_res_u_mixed": float(rm.max()), "max_res_u_fp64": float(rf.max()),
+                                "per_triplet_sigma_rel_diff": [float(x) for x in np.abs(sm - sf) / sf],
+                                "per_triplet_res_u": {"mixed": [float(x) for x in rm], "fp64": [float(x) for x in rf]}}
     return out
 
 
@@ -477,47 +571,63 @@ def measure_serving(B, slots=8, rate=200.0, count=300, seed=5):
             "queue_ms": {"p50": pct(que, 50), "p99": pct(que, 99)}, "all_valid": valid}
 
 
-def measure_spmm(B, dev, reps=10):
-    """The CSR SpMM at full scale: the 2,000,000 x 1,000,000 block-permuted matrix (62500
-    dense 32 x 16 blocks, 32M nonzeros, rows and columns permuted) against an L = 32 block,
-    A X and A^T Y, in FP64 and in FP32 (the mixed path's SpMM). Algorithmic bytes per call:
-    (e + 4) nnz + 8 (rows + 1) + e L (m + n) with e the element size (A once, X once, Y once);
-    achieved = bytes / CUDA-event time, against the measured HBM copy bandwidth. In FP64 the
-    2 L flops per nonzero (1.75 flop/B) exceed GB300's FP64 balance (~0.18 flop/B), so the
-    FP64 SpMM is bound by the FP64 pipe, not by HBM; TFLOP/s is reported beside GB/s."""
+def measure_spmm(B, dev, reps=12):
+    """The CSR SpMM at full scale, L = 32, on the 2e6 x 1e6 banded-plus-random matrix (32M
+    nonzeros, bf16-exact values) and on its known-spectrum twin (62500 permuted 32 x 16 blocks):
+    A X and A^T Y in FP64 (FP64 storage), FP32 and double-float (bf16 storage). Three input blocks
+    rotate, so no call finds its X in L2 from the call before (as in the Krylov loop, where X is a
+    new Lanczos vector every step). Algorithmic bytes per call: (e_a + 4) nnz + 8 (rows + 1) +
+    e_x L (m + n), with e_a the stored value size and e_x the block element size (A, X and Y
+    once); achieved = bytes / CUDA-event time, against the measured HBM copy bandwidth. The FP64
+    product does 2 L flops per nonzero, 1.75 flop/B, against GB300's FP64 balance of ~0.18 flop/B:
+    it is bound by the FP64 pipe, and TFLOP/s is reported beside GB/s. The autotuner's pick is
+    reported per product."""
     import torch
-    bp = synth.block_permuted(62500, 32, 16, seed=6, dist="uniform_bf16")
-    A = bp.A
-    ctx = B.Context()
-    M = B.Matrix.from_csr(ctx, A)
-    L = 32
-    X = torch.randn(A.n, L, dtype=torch.float64, device=dev)
-    Y = torch.randn(A.m, L, dtype=torch.float64, device=dev)
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     hbm = json.load(open(peaks_path)).get("hbm_gbs", 6780.4) if os.path.exists(peaks_path) else 6780.4
-    X32, Y32 = X.float(), Y.float()
-    out = {}
-    for name, fn, rows, e in (("A_X", lambda: M.spmm(X), A.m, 8), ("At_Y", lambda: M.spmm(Y, transpose=True), A.n, 8),
-                              ("A_X_fp32", lambda: M.spmm_f32(X32), A.m, 4),
-                              ("At_Y_fp32", lambda: M.spmm_f32(Y32, transpose=True), A.n, 4)):
-        for _ in range(3):
-            fn()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            fn()
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps
-        byts = (e + 4.0) * A.nnz + 8.0 * (rows + 1) + e * L * (A.m + A.n)
-        flops = 2.0 * A.nnz * L
-        out[name] = {"ms": ms, "algorithmic_bytes": byts, "GB_per_s": byts / ms / 1e6, "frac_of_hbm": byts / ms / 1e6 / hbm,
-                     "TFLOP_per_s": flops / ms / 1e9}
-    M.close()
+    L = 32
+    ctx = B.Context()
+    out = {"description": f"L = 32, three rotating inputs; HBM peak {hbm} GB/s (measured copy)"}
+    mats = (("banded_random_2000000x1000000", synth.banded_random()),
+            ("block_permuted_2000000x1000000", synth.block_permuted(62500, 32, 16, seed=6, dist="uniform_bf16").A))
+    for mname, A in mats:
+        res = {}
+        for storage in ("fp64", "bf16"):
+            M = B.Matrix.from_csr(ctx, A, storage=storage)
+            Xs = [torch.randn(A.n, L, dtype=torch.float64, device=dev) for _ in range(3)]
+            Ys = [torch.randn(A.m, L, dtype=torch.float64, device=dev) for _ in range(3)]
+            split = lambda Z: torch.cat([Z.float(), (Z - Z.float().double()).float()], 1).contiguous()
+            if storage == "fp64":
+                cases = [("A_X_fp64", [lambda X=X: M.spmm(X) for X in Xs], A.m, 8, 8, 0, False),
+                         ("At_Y_fp64", [lambda Y=Y: M.spmm(Y, transpose=True) for Y in Ys], A.n, 8, 8, 0, True)]
+            else:
+                Xf, Yf = [X.float() for X in Xs], [Y.float() for Y in Ys]
+                Xd, Yd = [split(X) for X in Xs], [split(Y) for Y in Ys]
+                cases = [("A_X_fp32", [lambda X=X: M.spmm_f32(X) for X in Xf], A.m, 2, 4, 1, False),
+                         ("At_Y_fp32", [lambda Y=Y: M.spmm_f32(Y, transpose=True) for Y in Yf], A.n, 2, 4, 1, True),
+                         ("A_X_df", [lambda X=X: M.spmm_df(X) for X in Xd], A.m, 2, 8, 2, False),
+                         ("At_Y_df", [lambda Y=Y: M.spmm_df(Y, transpose=True) for Y in Yd], A.n, 2, 8, 2, True)]
+            for cname, fns, rows, e_a, e_x, kind, tr in cases:
+                for f in fns:
+                    f()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for k in range(reps):
+                    fns[k % 3]()
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / reps
+                byts = (e_a + 4.0) * A.nnz + 8.0 * (rows + 1) + e_x * L * (A.m + A.n)
+                res[cname] = {"ms": ms, "algorithmic_bytes": byts, "GB_per_s": byts / ms / 1e6,
+                              "frac_of_hbm": byts / ms / 1e6 / hbm, "TFLOP_per_s": 2.0 * A.nnz * L / ms / 1e9,
+                              "autotune": B.cmsvd_spmm_tuning(M.handle, tr, kind, L)}
+            del Xs, Ys
+            M.close()
+            torch.cuda.empty_cache()
+        res["nnz"] = A.nnz
+        out[mname] = res
     ctx.close()
-    out["description"] = (f"2000000x1000000 CSR (nnz {A.nnz}, 62500 permuted 32x16 blocks), L = 32, FP64; "
-                          f"HBM peak {hbm} GB/s (measured copy)")
     return out
 
 
@@ -630,6 +740,8 @@ def main():
                     help="skip the secondary Poisson-arrival serving measurement")
     ap.add_argument("--no-spmm", dest="spmm", action="store_false",
                     help="skip the secondary full-scale SpMM bandwidth measurement")
+    ap.add_argument("--no-c3", dest="c3", action="store_false",
+                    help="skip the secondary 2e6 x 1e6 mixed-vs-FP64 Krylov measurement (about 3 minutes)")
     ap.add_argument("--table2", action="store_true",
                     help="also run the eight Exp III intervals on the digit-image stand-in (minutes)")
     args = ap.parse_args()

@@ -17,6 +17,8 @@
  *     column-major (one contiguous vector per triplet).
  *   - All work of one context is ordered on that context's stream. Calls that
  *     return host-visible values synchronize that stream before returning.
+ *   - A call on a context makes the context's device current while it runs and
+ *     makes the caller's current device current again before it returns.
  *   - The library owns the objects it creates (context, matrix, result) until
  *     the matching destroy call. It never frees caller memory.
  */
@@ -61,10 +63,15 @@ typedef enum cmsvd_solver {
 
 typedef enum cmsvd_precision {
     CMSVD_FP64 = 0,       /* every step in FP64 */
-    CMSVD_MIXED = 1       /* Krylov solver: Lanczos vectors, SpMM and A's values in FP32 (FP32 accumulation;
-                             alpha, beta, the shifted recurrences and all accumulations in FP64), then FP64
-                             iterative refinement of every shifted solve (residual in FP64 with FP64 A).
-                             Rank truncation and Rayleigh-Ritz stay FP64. The direct solver ignores it. */
+    CMSVD_MIXED = 1       /* Krylov solver on the FP32 pipe: A's values as stored (bf16, FP32, or FP64 split into
+                             two FP32 parts), every Lanczos vector as a double-float pair hi + lo of FP32
+                             numbers, SpMM, vector updates, dot products and the moment accumulation in
+                             double-float arithmetic (error-free FP32 products and sums, unit roundoff ~2^-48).
+                             The recurrence scalars (alpha, beta, LDL^T pivots, tridiagonal solves) and the
+                             moments stay FP64, as do rank truncation and Rayleigh-Ritz. With refine > 0 every
+                             shifted solve is then checked in FP64, R_j = X - (s_j I - A^T A) Y_j with FP64 A,
+                             and refined by correction solves while ||R_j|| / ||X|| > tol_solve. The direct and
+                             dense solvers ignore it. */
 } cmsvd_precision;
 
 /* Precision in which the library keeps A's values (cmsvd_csr_create). The values are rounded
@@ -96,13 +103,15 @@ typedef struct cmsvd_params {
     int32_t check_every;  /* Krylov iterations between host convergence checks (default 48) */
     int32_t direct_max_block; /* AUTO picks DIRECT when the largest component has at most this many columns (default 32) */
     int32_t profile;      /* 1: time every kernel class with CUDA events and fill the prof_* statistics (default 0) */
-    int32_t refine;       /* Krylov solver: up to this many rounds of FP64 iterative refinement of every shifted
-                             solve, R_j = X - (s_j I - A^T A) Y_j, (s_j I - A^T A) E_j = R_j, Y_j += E_j, until
-                             max ||R_j|| / ||X|| <= tol_solve (default 0: none) */
+    int32_t refine;       /* Krylov solver: FP64 check of every shifted solve, R_j = X - (s_j I - A^T A) Y_j with
+                             FP64 A, and up to this many rounds of correction solves (s_j I - A^T A) E_j = R_j,
+                             Y_j += E_j, until max ||R_j|| / ||X|| <= tol_solve (default 0: no check) */
     int32_t estimate;     /* 1: also compute the residual estimate of Sec. 3.4.1 through S_+ = [S_1, ..., S_M]
                              (Eq. residual; NT: Eq. res_nonlinear with mu from one exact residual), returned by
                              cmsvd_result_copy_estimate. The exact residuals are always computed (default 0) */
-    int32_t pad_;         /* reserved, 0 */
+    int32_t fault_breakdown_at; /* test hook, 0 = off: > 0 makes the Krylov solver treat column 0 as broken down
+                             at that Lanczos step, as a non-finite coefficient would, so that the solve returns
+                             CMSVD_BREAKDOWN (failure handling is tested without a real fault) */
 } cmsvd_params;
 
 /* Kernel classes of the prof_* statistics (index into the arrays). */
@@ -145,6 +154,9 @@ typedef struct cmsvd_stats {
     int64_t prof_launches[CMSVD_PROF_CLASSES];
     double prof_bytes[CMSVD_PROF_CLASSES];
     double prof_flops[CMSVD_PROF_CLASSES];
+    double ms_components;     /* host ms spent by this solve building the connected components of A^T A
+                                 (solver AUTO, first solve on a matrix only; 0 otherwise). This symbolic
+                                 set-up copies the CSR to the host and runs a union-find */
 } cmsvd_stats;
 
 typedef struct cmsvd_context cmsvd_context;
@@ -217,6 +229,18 @@ int cmsvd_spmm_df(cmsvd_matrix* A, int transpose, int64_t L, const float* X, int
                   float* Y, int64_t ldy);
 
 /*
+ * The SpMM autotuner's pick for A (transpose = 0) or A^T (transpose = 1), operand kind 0
+ * (FP64, cmsvd_spmm), 1 (FP32, cmsvd_spmm_f32) or 2 (double-float, cmsvd_spmm_df) and width L.
+ * The first product of a kind and width on a matrix (outside a stream capture) times every
+ * kernel variant on its own operands and keeps the fastest; all variants give bitwise equal
+ * results. cfg[4] (host) receives lanes per row, gathers in flight per lane, column slices
+ * per product, and 1 when rows run in storage order (0: rows sorted by first column); *ms
+ * (may be NULL) the time of one product in the tuning run. CMSVD_NOT_SUPPORTED when that
+ * product has not run yet. This is a property of the implementation; the paper has none.
+ */
+int cmsvd_spmm_tuning(const cmsvd_matrix* A, int transpose, int32_t kind, int64_t L, int32_t* cfg, float* ms);
+
+/*
  * Quadrature of Sec. 4 for j = 1..N/2 (the points with Im > 0, Sec. 3.1),
  * computed on the device. Outputs are host arrays of N/2 complex values,
  * interleaved (re, im): shift[j] = z_j (linear) or exp(t_j) (NT);
@@ -247,15 +271,17 @@ int cmsvd_gram(cmsvd_context* ctx, int64_t n, int32_t c1, int32_t c2, const doub
  * device, and host programs that hand a library only the buffers of the call.
  * The paper has no counterpart; this is a property of the library interface.
  *
- * Same arguments and result as cmsvd_gram (within rounding: the chunking may
- * differ). The chunk partials live in one fixed 8 MiB array of device memory
- * inside the library (1,048,576 doubles), held by every GPU that loads the
- * library until the process exits. Limit: c1 * c2 <= 1,048,576; larger
- * requests return CMSVD_INVALID_ARG. The call allocates nothing.
- * The first call on a device looks up the array's device address (one-time
- * set-up); make that first call before any stream capture on that device.
- * Every call shares the array: calls that overlap on the GPU (other streams,
- * other contexts, other threads) race and must be serialized by the caller.
+ * Same arguments, limits (1 <= c1, c2 <= 4096) and result as cmsvd_gram (within rounding:
+ * the chunking may differ), plus c1 * c2 <= 1,048,576: the chunk partials live in one fixed
+ * 8 MiB array of device memory inside the library (1,048,576 doubles), held by every GPU that
+ * loads the library until the process exits. Larger requests return CMSVD_INVALID_ARG. The
+ * call allocates nothing. The first call on a device looks up the array's device address
+ * (one-time set-up) and keeps it for the life of the process; make that first call before
+ * any stream capture on that device, and do not call it after cudaDeviceReset or a release of
+ * the device's primary context (the array then moves and the kept address is stale).
+ * Every call shares the array: calls that overlap on the GPU (other streams, other contexts,
+ * other threads) race and must be serialized by the caller. Like every entry point, it makes
+ * the context's device current while it runs and restores the caller's current device.
  */
 int cmsvd_gram_noalloc(cmsvd_context* ctx, int64_t n, int32_t c1, int32_t c2, const double* X, int64_t ldx,
                        const double* Y, int64_t ldy, double* G);

@@ -33,7 +33,8 @@ class cmsvd_params(C.Structure):
                 ("variant", C.c_int32), ("solver", C.c_int32), ("precision", C.c_int32),
                 ("max_iter", C.c_int32), ("tol_solve", C.c_double), ("tol_triplet", C.c_double),
                 ("norm_A", C.c_double), ("check_every", C.c_int32), ("direct_max_block", C.c_int32),
-                ("profile", C.c_int32), ("refine", C.c_int32), ("estimate", C.c_int32), ("pad_", C.c_int32)]
+                ("profile", C.c_int32), ("refine", C.c_int32), ("estimate", C.c_int32),
+                ("fault_breakdown_at", C.c_int32)]
 
 PROFILE_CLASSES = ("spmm", "krylov", "direct", "gram", "gemm", "small_dense", "other", "jacobi")
 
@@ -47,7 +48,7 @@ class cmsvd_stats(C.Structure):
                 ("ms_qr", C.c_double), ("ms_ritz", C.c_double), ("kernel_launches", C.c_int64),
                 ("refine_rounds", C.c_int32), ("pad_", C.c_int32), ("refine_residual", C.c_double),
                 ("prof_ms", C.c_double * 8), ("prof_launches", C.c_int64 * 8), ("prof_bytes", C.c_double * 8),
-                ("prof_flops", C.c_double * 8)]
+                ("prof_flops", C.c_double * 8), ("ms_components", C.c_double)]
 
     def as_dict(self) -> dict:
         d = {}
@@ -71,6 +72,7 @@ _SIGS = {
     "cmsvd_spmm": (C.c_int, [_P, C.c_int, _I64, _P, _I64, _P, _I64]),
     "cmsvd_spmm_f32": (C.c_int, [_P, C.c_int, _I64, _P, _I64, _P, _I64]),
     "cmsvd_spmm_df": (C.c_int, [_P, C.c_int, _I64, _P, _I64, _P, _I64]),
+    "cmsvd_spmm_tuning": (C.c_int, [_P, C.c_int, C.c_int32, _I64, _P, C.POINTER(C.c_float)]),
     "cmsvd_quadrature": (C.c_int, [_P, C.c_double, C.c_double, C.c_int32, C.c_int32, C.c_double, _P, _P, _P]),
     "cmsvd_workspace_size": (C.c_int, [_P, C.POINTER(cmsvd_params), C.POINTER(C.c_size_t)]),
     "cmsvd_gram_workspace_size": (C.c_int, [_P, _I64, C.c_int32, C.c_int32, C.POINTER(C.c_size_t)]),
@@ -214,6 +216,19 @@ def cmsvd_spmm_df(A: int, transpose: bool, X, Y) -> None:
     _check(lib().cmsvd_spmm_df(_P(A), int(transpose), L, _ptr(X), X.stride(0), _ptr(Y), Y.stride(0)), "cmsvd_spmm_df")
 
 
+def cmsvd_spmm_tuning(A: int, transpose: bool, kind: int, L: int):
+    """The autotuner's pick: dict(lanes_per_row, gathers, slices, natural_order, ms), or None
+    when that product has not run yet. kind: 0 FP64, 1 FP32, 2 double-float."""
+    cfg = np.zeros(4, dtype=np.int32)
+    ms = C.c_float()
+    s = lib().cmsvd_spmm_tuning(_P(A), int(transpose), kind, L, _P(cfg.ctypes.data), C.byref(ms))
+    if s == NOT_SUPPORTED:
+        return None
+    _check(s, "cmsvd_spmm_tuning")
+    return {"lanes_per_row": int(cfg[0]), "gathers_in_flight": int(cfg[1]), "column_slices": int(cfg[2]),
+            "row_order": "storage" if cfg[3] else "first-column", "ms_in_tuning": float(ms.value)}
+
+
 def cmsvd_quadrature(ctx: int, a: float, b: float, N: int, variant="linear", alpha: float = 0.1):
     """(shift, weight, scaled) for j = 1..N/2 as complex128 numpy arrays."""
     J = N // 2
@@ -229,18 +244,40 @@ def cmsvd_gram_workspace_size(ctx: int, n: int, c1: int, c2: int) -> int:
     return b.value
 
 
-def cmsvd_gram(ctx: int, X, Y, G, workspace) -> None:
-    """G (c1 x c2) = X^T Y for float64 CUDA tensors X (n x c1), Y (n x c2) (row strides as leading dims)."""
+def _gram_operands(X, Y, G):
+    """Shape, dtype and device checks of a Gram call, before anything reaches the library:
+    a wrong shape would make the kernels read or write outside the tensors."""
+    import torch
+    if X.dim() != 2 or Y.dim() != 2 or G.dim() != 2:
+        raise ValueError("X, Y and G must be 2-D")
     n, c1 = X.shape
     c2 = Y.shape[1]
+    if Y.shape[0] != n:
+        raise ValueError(f"Y has {Y.shape[0]} rows, X has {n}")
+    if tuple(G.shape) != (c1, c2):
+        raise ValueError(f"G must be {c1} x {c2}, got {tuple(G.shape)}")
+    for name, t in (("X", X), ("Y", Y), ("G", G)):
+        if t.dtype != torch.float64:
+            raise ValueError(f"{name} must be float64")
+        if t.stride(1) != 1:
+            raise ValueError(f"{name} rows must be contiguous")
+    if not G.is_contiguous():
+        raise ValueError("G must be contiguous")
+    if not (X.is_cuda and Y.is_cuda and G.is_cuda):
+        raise ValueError("X, Y and G must be CUDA tensors")
+    return n, c1, c2
+
+
+def cmsvd_gram(ctx: int, X, Y, G, workspace) -> None:
+    """G (c1 x c2) = X^T Y for float64 CUDA tensors X (n x c1), Y (n x c2) (row strides as leading dims)."""
+    n, c1, c2 = _gram_operands(X, Y, G)
     _check(lib().cmsvd_gram(_P(ctx), n, c1, c2, _ptr_any(X), X.stride(0), _ptr_any(Y), Y.stride(0), _ptr(G),
                             _ptr(workspace), workspace.numel() * workspace.element_size()), "cmsvd_gram")
 
 
 def cmsvd_gram_noalloc(ctx: int, X, Y, G) -> None:
     """G = X^T Y like cmsvd_gram, using the library's fixed device scratch (no workspace)."""
-    n, c1 = X.shape
-    c2 = Y.shape[1]
+    n, c1, c2 = _gram_operands(X, Y, G)
     _check(lib().cmsvd_gram_noalloc(_P(ctx), n, c1, c2, _ptr_any(X), X.stride(0), _ptr_any(Y), Y.stride(0), _ptr(G)),
            "cmsvd_gram_noalloc")
 

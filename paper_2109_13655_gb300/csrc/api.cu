@@ -1,5 +1,6 @@
 // C-ABI entry points (include/cmsvd.h) and the orchestration of one solve.
 #include "internal.cuh"
+#include <chrono>
 #include <cmath>
 #include <cstdlib>
 #include <new>
@@ -41,6 +42,7 @@ int check_params(const cmsvd_matrix* A, double a, double b, const cmsvd_params* 
     if (p->max_iter < 1) { set_error("max_iter must be >= 1"); return CMSVD_INVALID_ARG; }
     if (p->refine < 0 || p->refine > 100) { set_error("refine must be in [0, 100]"); return CMSVD_INVALID_ARG; }
     if (p->estimate != 0 && p->estimate != 1) { set_error("estimate must be 0 or 1"); return CMSVD_INVALID_ARG; }
+    if (p->fault_breakdown_at < 0) { set_error("fault_breakdown_at must be >= 0"); return CMSVD_INVALID_ARG; }
     if (!(p->delta >= 0.0) || !(p->eps_tau >= 0.0) || !(p->tol_triplet > 0.0) || !(p->tol_solve > 0.0)) {
         set_error("delta, eps_tau >= 0 and tol_solve, tol_triplet > 0 required");
         return CMSVD_INVALID_ARG;
@@ -55,15 +57,19 @@ int check_params(const cmsvd_matrix* A, double a, double b, const cmsvd_params* 
     return CMSVD_OK;
 }
 
-int pick_solver(cmsvd_matrix* A, const cmsvd_params* p) {
-    if (p->solver == CMSVD_SOLVER_KRYLOV) return CMSVD_SOLVER_KRYLOV;
-    if (p->solver == CMSVD_SOLVER_DIRECT) return CMSVD_SOLVER_DIRECT;
-    if (p->solver == CMSVD_SOLVER_DENSE) return CMSVD_SOLVER_DENSE;
+// AUTO: the connected components of A^T A decide (built once per matrix, on the host: the
+// symbolic phase of the direct solve, timed into stats->ms_components). Errors propagate.
+int pick_solver(cmsvd_matrix* A, const cmsvd_params* p, int* solver, cmsvd_stats* st) {
+    if (p->solver != CMSVD_SOLVER_AUTO) { *solver = p->solver; return CMSVD_OK; }
     if (!A->comp.ready) {
-        if (components_build(A) != CMSVD_OK) return A->A.n <= 1024 ? CMSVD_SOLVER_DENSE : CMSVD_SOLVER_KRYLOV;
+        const auto t0 = std::chrono::steady_clock::now();
+        CM_TRY(components_build(A));
+        A->ms_components = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        st->ms_components = A->ms_components;
     }
-    if (A->comp.max_size <= p->direct_max_block) return CMSVD_SOLVER_DIRECT;
-    return A->A.n <= 1024 ? CMSVD_SOLVER_DENSE : CMSVD_SOLVER_KRYLOV;
+    if (A->comp.max_size <= p->direct_max_block) *solver = CMSVD_SOLVER_DIRECT;
+    else *solver = A->A.n <= 1024 ? CMSVD_SOLVER_DENSE : CMSVD_SOLVER_KRYLOV;
+    return CMSVD_OK;
 }
 
 // Workspace plan shared by the size query and the solve.
@@ -108,46 +114,6 @@ size_t scratch_size(const cmsvd_matrix* A, const cmsvd_params* p, bool with_ritz
     return mx;
 }
 
-int enter(cmsvd_context* ctx) {
-    CM_CUDA(cudaSetDevice(ctx->device));
-    CM_CUDA(cudaEventRecord(ctx->ev_in, ctx->user));
-    CM_CUDA(cudaStreamWaitEvent(ctx->s, ctx->ev_in, 0));
-    return CMSVD_OK;
-}
-
-int leave(cmsvd_context* ctx) {
-    CM_CUDA(cudaEventRecord(ctx->ev_out, ctx->s));
-    CM_CUDA(cudaStreamWaitEvent(ctx->user, ctx->ev_out, 0));
-    return CMSVD_OK;
-}
-
-// An entry point's work runs on the context's internal stream between enter() and leave().
-// A Session joins the caller's stream back even when the call returns early with an error,
-// so that what the caller queues next (freeing its buffers, say) waits for the kernels
-// already queued on the internal stream.
-struct Session {
-    cmsvd_context* c = nullptr;
-    Session() = default;
-    Session(const Session&) = delete;
-    Session& operator=(const Session&) = delete;
-    ~Session() {
-        if (c) {
-            cudaEventRecord(c->ev_out, c->s);
-            cudaStreamWaitEvent(c->user, c->ev_out, 0);
-        }
-    }
-    int open(cmsvd_context* ctx) {
-        CM_TRY(enter(ctx));
-        c = ctx;
-        return CMSVD_OK;
-    }
-    int close() {
-        cmsvd_context* x = c;
-        c = nullptr;
-        return leave(x);
-    }
-};
-
 int ensure_norm(cmsvd_matrix* A, const cmsvd_params* p, Arena& ws, double* normA) {
     if (p->norm_A > 0.0) { *normA = p->norm_A; return CMSVD_OK; }
     if (A->norm_est <= 0.0) {
@@ -165,7 +131,8 @@ int run_moments(cmsvd_matrix* A, double a, double b, const cmsvd_params* p, cons
     cmsvd_context* ctx = A->ctx;
     QuadParams qp{a, b, p->alpha, p->N, p->variant};
     CM_TRY(quadrature_device(qp, pl.quad, ctx->s));
-    const int solver = pick_solver(A, p);
+    int solver = CMSVD_SOLVER_AUTO;
+    CM_TRY(pick_solver(A, p, &solver, st));
     st->solver_used = solver;
     const int64_t lds = (int64_t)p->L * (p->M + 1);
     size_t mark = ws.off;
@@ -238,7 +205,7 @@ int cmsvd_params_default(cmsvd_params* p) {
     p->profile = 0;
     p->refine = 0;
     p->estimate = 0;
-    p->pad_ = 0;
+    p->fault_breakdown_at = 0;
     return CMSVD_OK;
 }
 
@@ -353,6 +320,22 @@ int cmsvd_spmm_df(cmsvd_matrix* A, int transpose, int64_t L, const float* X, int
     CM_TRY(csr_make_fp32(A));
     CM_TRY(spmm_df(transpose ? A->At : A->A, (int)L, X, ldx, Y, ldy, A->ctx->s));
     return se.close();
+}
+
+int cmsvd_spmm_tuning(const cmsvd_matrix* A, int transpose, int32_t kind, int64_t L, int32_t* cfg, float* ms) {
+    if (!A || !cfg) { set_error("NULL argument"); return CMSVD_INVALID_ARG; }
+    if (kind < 0 || kind > 2) { set_error("kind must be 0 (FP64), 1 (FP32) or 2 (double-float)"); return CMSVD_INVALID_ARG; }
+    SpmmCfg c;
+    if (!spmm_tuned(transpose ? A->At : A->A, kind, (int)L, &c)) {
+        set_error("no autotuned configuration for this matrix, kind and L yet");
+        return CMSVD_NOT_SUPPORTED;
+    }
+    cfg[0] = c.lpr;
+    cfg[1] = c.unroll;
+    cfg[2] = c.slices;
+    cfg[3] = c.natural;
+    if (ms) *ms = c.ms;
+    return CMSVD_OK;
 }
 
 int cmsvd_quadrature(cmsvd_context* ctx, double a, double b, int32_t N, int32_t variant, double alpha, double* shift,

@@ -1065,8 +1065,8 @@ extern "C" int cmsvd_gram_noalloc(cmsvd_context* ctx, int64_t n, int32_t c1, int
                                   const double* Y, int64_t ldy, double* G) {
     using namespace cmsvd;
     if (!ctx || !X || !Y || !G) { set_error("NULL argument"); return CMSVD_INVALID_ARG; }
-    if (n < 1 || c1 < 1 || c2 < 1 || ldx < c1 || ldy < c2) {
-        set_error("need n >= 1, c1 >= 1, c2 >= 1, ldx >= c1, ldy >= c2");
+    if (n < 1 || c1 < 1 || c2 < 1 || c1 > 4096 || c2 > 4096 || ldx < c1 || ldy < c2) {
+        set_error("need n >= 1, 1 <= c1, c2 <= 4096, ldx >= c1, ldy >= c2");
         return CMSVD_INVALID_ARG;
     }
     if ((int64_t)c1 * c2 > kNoAllocDoubles) {
@@ -1074,12 +1074,10 @@ extern "C" int cmsvd_gram_noalloc(cmsvd_context* ctx, int64_t n, int32_t c1, int
                   (long long)c1 * c2, (long long)kNoAllocDoubles);
         return CMSVD_INVALID_ARG;
     }
-    CM_CUDA(cudaSetDevice(ctx->device));
+    Session se;
+    CM_TRY(se.open(ctx));   // the context's device is current from here to the return
     double* scratch = nullptr;
     CM_TRY(noalloc_scratch(ctx->device, &scratch));
-    // order after the caller's stream, as every other entry point does
-    CM_CUDA(cudaEventRecord(ctx->ev_in, ctx->user));
-    CM_CUDA(cudaStreamWaitEvent(ctx->s, ctx->ev_in, 0));
     const int sym = (X == Y && c1 == c2 && ldx == ldy) ? 1 : 0;
     int nc;
     int64_t rpc;
@@ -1097,7 +1095,5 @@ extern "C" int cmsvd_gram_noalloc(cmsvd_context* ctx, int64_t n, int32_t c1, int
     CM_LAUNCH();
     k_sum_partials<<<(int)((cnt + 255) / 256), 256, 0, ctx->s>>>(scratch, nc, c1, c2, sym, G);
     CM_LAUNCH();
-    CM_CUDA(cudaEventRecord(ctx->ev_out, ctx->s));
-    CM_CUDA(cudaStreamWaitEvent(ctx->user, ctx->ev_out, 0));
-    return CMSVD_OK;
+    return se.close();
 }

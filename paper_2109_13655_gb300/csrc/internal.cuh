@@ -4,6 +4,8 @@
 #include <cstdint>
 #include <cstddef>
 #include <cstring>
+#include <memory>
+#include <mutex>
 #include "cmsvd.h"
 
 namespace cmsvd {
@@ -60,6 +62,12 @@ void prof_collect(cmsvd_stats* st);   // synchronizes the recorded events
 // natural = 1 takes the rows in storage order instead of the locality order (row_order).
 struct SpmmCfg { int lpr = 0, unroll = 0, slices = 1, blocks_per_sm = 0, natural = 0; float ms = 0.f; };
 struct SpmmTuneEntry { int kind = -1, L = 0; SpmmCfg cfg; };
+// Autotuner cache of one stored matrix, shared by its shallow per-stream views (serving):
+// one thread tunes at a time; the others use the default configuration meanwhile.
+struct SpmmTuneCache {
+    std::mutex mu;
+    SpmmTuneEntry e[64];
+};
 
 struct Csr {
     int64_t m = 0, n = 0, nnz = 0;
@@ -74,7 +82,7 @@ struct Csr {
     int sm_count = 0;
     int64_t max_row = 0;         // longest row (nonzeros); long rows switch the SpMM to one CTA per row
     int32_t* row_order = nullptr; // device, m: rows sorted by their first column (SpMM processing order)
-    SpmmTuneEntry tune[64];      // autotuner cache (host)
+    std::shared_ptr<SpmmTuneCache> tune = std::make_shared<SpmmTuneCache>();   // autotuner cache (host)
 };
 
 struct Components {             // connected components of the column graph (A^T A)
@@ -130,6 +138,7 @@ struct cmsvd_matrix {
     cmsvd_context* ctx = nullptr;
     cmsvd::Csr A, At;
     double norm_est = 0.0;             // cached ||A||_2 estimate (0 = not yet)
+    double ms_components = 0.0;        // host time of the components build (0 = not built)
     cmsvd::Components comp;
 };
 
@@ -147,6 +156,51 @@ struct cmsvd_result {
 };
 
 namespace cmsvd {
+
+// ----------------------------------------------------------------------------- entry-point session
+// An entry point's work runs on the context's internal stream: open() makes the context's
+// device current (remembering the caller's), orders the internal stream after the caller's
+// stream, and close() orders the caller's stream after the internal one and makes the caller's
+// device current again. The destructor does the same on an early error return, so that what
+// the caller queues next (freeing its buffers, say) waits for the kernels already queued, and
+// the caller's current device is never left changed.
+struct Session {
+    cmsvd_context* c = nullptr;
+    int prev = -1;
+    Session() = default;
+    Session(const Session&) = delete;
+    Session& operator=(const Session&) = delete;
+    ~Session() {
+        if (c) {
+            cudaEventRecord(c->ev_out, c->s);
+            cudaStreamWaitEvent(c->user, c->ev_out, 0);
+        }
+        restore();
+    }
+    void restore() {
+        if (prev >= 0) cudaSetDevice(prev);
+        prev = -1;
+    }
+    int open(cmsvd_context* ctx) {
+        int d = -1;
+        CM_CUDA(cudaGetDevice(&d));
+        prev = d;
+        CM_CUDA(cudaSetDevice(ctx->device));
+        CM_CUDA(cudaEventRecord(ctx->ev_in, ctx->user));
+        CM_CUDA(cudaStreamWaitEvent(ctx->s, ctx->ev_in, 0));
+        c = ctx;
+        return CMSVD_OK;
+    }
+    int close() {
+        cmsvd_context* x = c;
+        c = nullptr;
+        cudaError_t e = cudaEventRecord(x->ev_out, x->s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(x->user, x->ev_out, 0);
+        restore();
+        if (e != cudaSuccess) return cuda_fail(e, "rejoin the caller's stream", __FILE__, __LINE__);
+        return CMSVD_OK;
+    }
+};
 
 // ----------------------------------------------------------------------------- workspace arena
 // Bump allocator over the caller's workspace. With base == nullptr it only
@@ -183,6 +237,7 @@ int spmm_df(const Csr& A, int L, const float* X, int64_t ldx, float* Y, int64_t 
 // Runs the autotuner for (A, kind, L) now, on the given buffers, outside any stream capture.
 enum { SPMM_KIND_F64 = 0, SPMM_KIND_F32 = 1, SPMM_KIND_DF = 2 };
 int spmm_tune(Csr& A, int kind, int L, const void* X, int64_t ldx, void* Y, int64_t ldy, cudaStream_t s);
+bool spmm_tuned(const Csr& A, int kind, int L, SpmmCfg* cfg);
 int csr_make_fp32(cmsvd_matrix* M);   // vals_f (and vals_lo when needed) of A and A^T
 int components_build(cmsvd_matrix* M);
 void components_free(Components* c);

@@ -161,9 +161,9 @@ struct OpDF {
     __device__ __forceinline__ void store(const Acc& a, int64_t r, int col) const {
         float* y = Y + r * ldy + col;
 #pragma unroll
-        for (int q = 0; q < VEC; ++q) {
+        for (int q = 0; q < VEC; ++q) {   // two_sum: the low part may exceed the high part after cancellation
             float h, l;
-            fast_two_sum(a.h[q], a.l[q], h, l);
+            two_sum(a.h[q], a.l[q], h, l);
             y[q] = h;
             y[L + q] = l;
         }
@@ -317,12 +317,14 @@ __global__ void __launch_bounds__(256) k_spmm_rowcta(const int64_t* __restrict__
 // Candidate (lanes per row, gathers in flight) pairs; the kernel template is instantiated for
 // each. The column slicing and the grid are run-time choices.
 struct Variant { int lpr, unroll; };
-static const Variant kVariants[] = {{4, 4}, {4, 8}, {8, 4}, {8, 8}, {16, 4}, {16, 8}, {32, 4}, {32, 8}};
+static const Variant kVariants[] = {{1, 4}, {1, 8}, {2, 4}, {2, 8}, {4, 4}, {4, 8}, {8, 4}, {8, 8},
+                                    {16, 4}, {16, 8}, {32, 4}, {32, 8}};
 
 template <class Op, class Val>
 static const void* kernel_ptr(int lpr, int unroll) {
 #define CM_K(LP, UU) if (lpr == LP && unroll == UU) return (const void*)k_spmm_vec<Op, Val, LP, UU>;
-    CM_K(4, 4) CM_K(4, 8) CM_K(8, 4) CM_K(8, 8) CM_K(16, 4) CM_K(16, 8) CM_K(32, 4) CM_K(32, 8)
+    CM_K(1, 4) CM_K(1, 8) CM_K(2, 4) CM_K(2, 8) CM_K(4, 4) CM_K(4, 8) CM_K(8, 4) CM_K(8, 8)
+    CM_K(16, 4) CM_K(16, 8) CM_K(32, 4) CM_K(32, 8)
 #undef CM_K
     return nullptr;
 }
@@ -369,8 +371,9 @@ static SpmmCfg default_cfg(int vec, int L) {
     return c;
 }
 
+// callers hold A.tune->mu
 static SpmmTuneEntry* tune_find(Csr& A, int kind, int L) {
-    for (auto& t : A.tune)
+    for (auto& t : A.tune->e)
         if (t.kind == kind && t.L == L) return &t;
     return nullptr;
 }
@@ -391,12 +394,17 @@ static int autotune(Csr& A, int kind, int L, const Op& op, const Val& val, cudaS
     SpmmCfg best = default_cfg(Op::VEC, L);
     float best_ms = 1e30f;
     int st = CMSVD_OK;
-    const int max_slices = L / Op::VEC >= 4 ? 4 : (L / Op::VEC >= 2 ? 2 : 1);
+    // Column slices (each launch covers L / slices columns for all rows, so that the gathered
+    // part of X can stay in L2) with lanes per row matched to the slice width: one to four
+    // passes of LPR * VEC columns per slice.
+    const int nvec = (L + Op::VEC - 1) / Op::VEC;
     for (int nat = 0; nat < (A.row_order ? 2 : 1) && st == CMSVD_OK; ++nat)
+    for (int sl = 1; sl <= 8 && sl <= nvec && st == CMSVD_OK; sl *= 2)
     for (const Variant& v : kVariants) {
-        if (v.lpr * Op::VEC > 2 * L && v.lpr > 4) continue;             // mostly idle lanes
-        for (int sl = 1; sl <= max_slices; sl *= 2) {
-            if (sl > 1 && v.lpr * Op::VEC > L / sl && v.lpr > 4) continue;
+        const int w = ((L / sl + Op::VEC - 1) / Op::VEC) * Op::VEC;      // columns per slice
+        if (v.lpr * Op::VEC > w && v.lpr > 1) continue;                 // idle lanes
+        if (v.lpr * Op::VEC * 4 < w) continue;                          // more than four passes per row
+        {
             SpmmCfg c;
             c.lpr = v.lpr;
             c.unroll = v.unroll;
@@ -419,8 +427,8 @@ static int autotune(Csr& A, int kind, int L, const Op& op, const Val& val, cudaS
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != CMSVD_OK) return st;
-    SpmmTuneEntry* slot = &A.tune[63];                                 // a full cache reuses its last entry
-    for (auto& t : A.tune)
+    SpmmTuneEntry* slot = &A.tune->e[63];                              // a full cache reuses its last entry
+    for (auto& t : A.tune->e)
         if (t.kind < 0) { slot = &t; break; }
     slot->kind = kind;
     slot->L = L;
@@ -432,10 +440,17 @@ static int autotune(Csr& A, int kind, int L, const Op& op, const Val& val, cudaS
 
 template <class Op, class Val>
 static int run_vec(Csr& A, int kind, int L, const Op& op, const Val& val, cudaStream_t s) {
+    // small products are launch-bound: not tuned
+    if (A.nnz * (int64_t)L < (int64_t)1 << 24) return launch_vec(A, op, val, L, default_cfg(Op::VEC, L), s);
+    std::unique_lock<std::mutex> lk(A.tune->mu, std::try_to_lock);
+    if (!lk.owns_lock()) return launch_vec(A, op, val, L, default_cfg(Op::VEC, L), s);   // another stream is tuning
     SpmmTuneEntry* t = tune_find(A, kind, L);
-    if (t) return launch_vec(A, op, val, L, t->cfg, s);
-    if (capturing(s) || A.nnz * (int64_t)L < (int64_t)1 << 20)   // small products: launch-bound, not tuned
-        return launch_vec(A, op, val, L, default_cfg(Op::VEC, L), s);
+    if (t) {
+        const SpmmCfg c = t->cfg;
+        lk.unlock();
+        return launch_vec(A, op, val, L, c, s);
+    }
+    if (capturing(s)) return launch_vec(A, op, val, L, default_cfg(Op::VEC, L), s);
     SpmmCfg c;
     return autotune(A, kind, L, op, val, s, &c);
 }
@@ -518,6 +533,20 @@ int spmm_df(const Csr& Ac, int L, const float* X, int64_t ldx, float* Y, int64_t
     ValF32 v{A.vals_f};
     if (vec) return run_vec(A, key(SPMM_KIND_DF, kv), L, OpDF<4>{X, ldx, Y, ldy, L}, v, s);
     return run_vec(A, key(SPMM_KIND_DF, kv), L, OpDF<1>{X, ldx, Y, ldy, L}, v, s);
+}
+
+// The autotuner's pick for (A, kind, L), if it has run: vectorized operands first.
+bool spmm_tuned(const Csr& A, int kind, int L, SpmmCfg* cfg) {
+    std::lock_guard<std::mutex> lk(A.tune->mu);
+    const SpmmTuneEntry* found = nullptr;
+    for (const auto& t : A.tune->e) {
+        if (t.kind >= kind * 8 && t.kind < kind * 8 + 8 && t.L == L) {
+            if (!found || ((t.kind & 1) && !(found->kind & 1))) found = &t;
+        }
+    }
+    if (!found) return false;
+    *cfg = found->cfg;
+    return true;
 }
 
 // Runs the autotuner (if it has not run) on the given buffers: one product is computed.

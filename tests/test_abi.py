@@ -171,3 +171,17 @@ def test_readme_c_example_builds(lib, tmp_path):
                         "-L", libdir, "-lcmsvd", "-L", cudalib, "-lcudart", "-Wl,--no-undefined",
                         "-o", str(tmp_path / "libexample.so")], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_gram_operand_checks_before_any_launch():
+    """The binding rejects mismatched Gram operands before the library (or a GPU) is touched."""
+    torch = pytest.importorskip("torch")
+    X = torch.zeros((10, 3), dtype=torch.float64)
+    with pytest.raises(ValueError, match="rows"):
+        B.cmsvd_gram_noalloc(0, X, torch.zeros((9, 4), dtype=torch.float64), torch.zeros((3, 4), dtype=torch.float64))
+    with pytest.raises(ValueError, match="G must be"):
+        B.cmsvd_gram_noalloc(0, X, torch.zeros((10, 4), dtype=torch.float64), torch.zeros((4, 3), dtype=torch.float64))
+    with pytest.raises(ValueError, match="float64"):
+        B.cmsvd_gram(0, X.float(), X.float(), torch.zeros((3, 3)), None)
+    with pytest.raises(ValueError, match="CUDA"):
+        B.cmsvd_gram_noalloc(0, X, X, torch.zeros((3, 3), dtype=torch.float64))

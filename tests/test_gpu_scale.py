@@ -54,3 +54,48 @@ def test_known_spectrum_2000000x1000000(B):
     assert np.max(np.abs(out.U.T @ out.U - np.eye(100))) <= 1e-10
     M.close()
     ctx.close()
+
+
+def banded_random_case():
+    """The 2e6 x 1e6 banded-plus-random matrix (synth.banded_random, 32M nonzeros, bf16-exact
+    values) with the exterior window of its 85 largest singular values: a at the midpoint of
+    the widest relative gap near the 100th value (between the 85th and 86th), b = 1.01 sigma_1.
+    Expected values: tests/golden/banded_random_2000000x1000000_top.txt (the oracle's ARPACK
+    Lanczos on A^T A). N = 32, L = 32, M = 8 with alpha = 0.2 and ell = 2 (the iteration
+    technique, Eqs. iter1-iter2): with ell = 1 the filter at alpha = 0.1 leaves too many
+    directions above the rank threshold for L M = 256 and most values miss 1e-10."""
+    import os
+    g = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "banded_random_2000000x1000000_top.txt"))
+    t = 85
+    a, b = 0.5 * (g[t - 1] + g[t]), 1.01 * g[0]
+    return synth.banded_random(), g, t, a, b
+
+
+@pytest.mark.parametrize("precision,storage", [("mixed", "bf16"), ("fp64", "fp64")])
+def test_banded_random_2000000x1000000_krylov(B, precision, storage):
+    """The 2e6 x 1e6 mixed-precision workload through the Krylov solver (the only solver for
+    this matrix: A^T A has one connected component of 1e6 columns), FP64 and double-float.
+    Checks: exact count (85), sigma within 1e-10 of the expected values, residuals <= 1e-10
+    (from the library and recomputed with SciPy on sampled triplets), and orthonormality."""
+    A, g, t, a, b = banded_random_case()
+    ctx = B.Context()
+    M = B.Matrix.from_csr(ctx, A, storage=storage)
+    Vin = torch.from_numpy(synth.gaussian_block(A.n, 32, 11)).cuda()
+    p = B.params(N=32, L=32, M=8, ell=2, alpha=0.2, solver="krylov", norm_A=float(g[0]),
+                 precision=B.MIXED if precision == "mixed" else B.FP64)
+    out = M.solve_interval(a, b, p, Vin)
+    assert out.stats["solver_used"] == B.SOLVER_KRYLOV and out.stats["krylov_iters"] > 0
+    assert out.stats["converged"] == 1
+    assert out.sigma.size == t
+    truth = np.sort(g[:t])
+    assert np.max(np.abs(out.sigma - truth) / truth) <= 1e-10
+    assert out.res_u.max() <= 1e-10 and out.res_v.max() <= 1e-10
+    As = sp.csr_matrix((A.vals, A.colidx, A.rowptr), shape=(A.m, A.n))
+    for i in np.linspace(0, t - 1, 6).astype(int):
+        u, v, sg = out.U[:, i], out.V[:, i], out.sigma[i]
+        assert np.linalg.norm(As.T @ u - sg * v) / g[0] <= 1e-10
+        assert np.linalg.norm(As @ v - sg * u) / g[0] <= 1e-10
+    assert np.max(np.abs(out.V.T @ out.V - np.eye(t))) <= 1e-10
+    assert np.max(np.abs(out.U.T @ out.U - np.eye(t))) <= 1e-10
+    M.close()
+    ctx.close()

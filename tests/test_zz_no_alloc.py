@@ -30,7 +30,7 @@ def ctx(B):
 
 
 @pytest.mark.parametrize("n,c1,c2,same", [(5000, 64, 64, True), (3001, 80, 7, False), (20000, 512, 512, True),
-                                          (1, 3, 5, False)])
+                                          (20000, 512, 300, False), (1, 3, 5, False), (3000, 1, 4096, False)])
 def test_noalloc_matches_workspace_gram(B, ctx, n, c1, c2, same):
     rng = np.random.default_rng(n + c1 + c2)
     X = torch.from_numpy(rng.standard_normal((n, c1))).cuda()
@@ -52,3 +52,21 @@ def test_noalloc_rejects_oversize(B, ctx):
     with pytest.raises(B.CmsvdError) as e:
         B.cmsvd_gram_noalloc(ctx.handle, X, X, G)
     assert e.value.status == B.INVALID_ARG
+    # the same column limit as cmsvd_gram (c2 <= 4096), whatever c1 * c2
+    X1 = torch.zeros((4, 1), dtype=torch.float64, device="cuda")
+    Y1 = torch.zeros((4, 4097), dtype=torch.float64, device="cuda")
+    G1 = torch.zeros((1, 4097), dtype=torch.float64, device="cuda")
+    with pytest.raises(B.CmsvdError) as e:
+        B.cmsvd_gram_noalloc(ctx.handle, X1, Y1, G1)
+    assert e.value.status == B.INVALID_ARG
+
+
+def test_noalloc_restores_current_device(B, ctx):
+    """The call makes the context's device current only while it runs."""
+    X = torch.ones((64, 8), dtype=torch.float64, device="cuda")
+    G = torch.empty((8, 8), dtype=torch.float64, device="cuda")
+    before = torch.cuda.current_device()
+    B.cmsvd_gram_noalloc(ctx.handle, X, X, G)
+    torch.cuda.synchronize()
+    assert torch.cuda.current_device() == before
+    assert torch.allclose(G, torch.full((8, 8), 64.0, dtype=torch.float64, device="cuda"))
