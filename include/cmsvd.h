@@ -231,12 +231,14 @@ int cmsvd_spmm_df(cmsvd_matrix* A, int transpose, int64_t L, const float* X, int
 /*
  * The SpMM autotuner's pick for A (transpose = 0) or A^T (transpose = 1), operand kind 0
  * (FP64, cmsvd_spmm), 1 (FP32, cmsvd_spmm_f32) or 2 (double-float, cmsvd_spmm_df) and width L.
- * The first product of a kind and width on a matrix (outside a stream capture) times every
- * kernel variant on its own operands and keeps the fastest; all variants give bitwise equal
- * results. cfg[4] (host) receives lanes per row, gathers in flight per lane, column slices
- * per product, and 1 when rows run in storage order (0: rows sorted by first column); *ms
- * (may be NULL) the time of one product in the tuning run. CMSVD_NOT_SUPPORTED when that
- * product has not run yet. This is a property of the implementation; the paper has none.
+ * The first product of a kind and width on a matrix through those entry points, and the first
+ * Lanczos product of a Krylov solve (before its graph capture), times every kernel variant on
+ * its own operands and keeps the fastest; all variants give bitwise equal results. Products
+ * inside a solve's other steps use a kept pick or the default configuration and never tune.
+ * cfg[4] (host) receives lanes per row, gathers in flight per lane, column slices per product,
+ * and 1 when rows run in storage order (0: rows sorted by first column); *ms (may be NULL) the
+ * time of one product in the tuning run. CMSVD_NOT_SUPPORTED when no pick exists yet. This is
+ * a property of the implementation; the paper has none.
  */
 int cmsvd_spmm_tuning(const cmsvd_matrix* A, int transpose, int32_t kind, int64_t L, int32_t* cfg, float* ms);
 

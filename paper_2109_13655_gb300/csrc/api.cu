@@ -298,7 +298,7 @@ int cmsvd_spmm(cmsvd_matrix* A, int transpose, int64_t L, const double* X, int64
     if (L < 1 || L > 4096 || ldx < L || ldy < L) { set_error("need 1 <= L <= 4096, ldx >= L, ldy >= L"); return CMSVD_INVALID_ARG; }
     Session se;
     CM_TRY(se.open(A->ctx));
-    CM_TRY(spmm(transpose ? A->At : A->A, (int)L, X, ldx, Y, ldy, A->ctx->s));
+    CM_TRY(spmm_tune(transpose ? A->At : A->A, SPMM_KIND_F64, (int)L, X, ldx, Y, ldy, A->ctx->s));
     return se.close();
 }
 
@@ -308,7 +308,7 @@ int cmsvd_spmm_f32(cmsvd_matrix* A, int transpose, int64_t L, const float* X, in
     Session se;
     CM_TRY(se.open(A->ctx));
     CM_TRY(csr_make_fp32(A));
-    CM_TRY(spmm(transpose ? A->At : A->A, (int)L, X, ldx, Y, ldy, A->ctx->s));
+    CM_TRY(spmm_tune(transpose ? A->At : A->A, SPMM_KIND_F32, (int)L, X, ldx, Y, ldy, A->ctx->s));
     return se.close();
 }
 
@@ -318,7 +318,7 @@ int cmsvd_spmm_df(cmsvd_matrix* A, int transpose, int64_t L, const float* X, int
     Session se;
     CM_TRY(se.open(A->ctx));
     CM_TRY(csr_make_fp32(A));
-    CM_TRY(spmm_df(transpose ? A->At : A->A, (int)L, X, ldx, Y, ldy, A->ctx->s));
+    CM_TRY(spmm_tune(transpose ? A->At : A->A, SPMM_KIND_DF, (int)L, X, ldx, Y, ldy, A->ctx->s));
     return se.close();
 }
 

@@ -438,6 +438,11 @@ static int autotune(Csr& A, int kind, int L, const Op& op, const Val& val, cudaS
     return launch_vec(A, op, val, L, best, s);
 }
 
+// Tuning runs only inside spmm_tune (the Krylov solver before its graph capture, and the
+// public SpMM entry points); other products (the Rayleigh-Ritz steps, whose widths change
+// from solve to solve) take a cached pick or the default configuration.
+static thread_local bool t_allow_tune = false;
+
 template <class Op, class Val>
 static int run_vec(Csr& A, int kind, int L, const Op& op, const Val& val, cudaStream_t s) {
     // small products are launch-bound: not tuned
@@ -450,7 +455,7 @@ static int run_vec(Csr& A, int kind, int L, const Op& op, const Val& val, cudaSt
         lk.unlock();
         return launch_vec(A, op, val, L, c, s);
     }
-    if (capturing(s)) return launch_vec(A, op, val, L, default_cfg(Op::VEC, L), s);
+    if (!t_allow_tune || capturing(s)) return launch_vec(A, op, val, L, default_cfg(Op::VEC, L), s);
     SpmmCfg c;
     return autotune(A, kind, L, op, val, s, &c);
 }
@@ -551,9 +556,13 @@ bool spmm_tuned(const Csr& A, int kind, int L, SpmmCfg* cfg) {
 
 // Runs the autotuner (if it has not run) on the given buffers: one product is computed.
 int spmm_tune(Csr& A, int kind, int L, const void* X, int64_t ldx, void* Y, int64_t ldy, cudaStream_t s) {
-    if (kind == SPMM_KIND_F64) return spmm(A, L, (const double*)X, ldx, (double*)Y, ldy, s);
-    if (kind == SPMM_KIND_F32) return spmm(A, L, (const float*)X, ldx, (float*)Y, ldy, s);
-    return spmm_df(A, L, (const float*)X, ldx, (float*)Y, ldy, s);
+    t_allow_tune = true;
+    int st;
+    if (kind == SPMM_KIND_F64) st = spmm(A, L, (const double*)X, ldx, (double*)Y, ldy, s);
+    else if (kind == SPMM_KIND_F32) st = spmm(A, L, (const float*)X, ldx, (float*)Y, ldy, s);
+    else st = spmm_df(A, L, (const float*)X, ldx, (float*)Y, ldy, s);
+    t_allow_tune = false;
+    return st;
 }
 
 }  // namespace cmsvd

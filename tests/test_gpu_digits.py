@@ -73,3 +73,29 @@ def test_digits_like_table1(B, digits, kind, t, L, solver):
         assert np.max(np.abs(out.V[:, i] - ref.V[:, i])) <= tol
     M.close()
     ctx.close()
+
+
+@pytest.mark.parametrize("kind,t,L", [("exterior", 40, 30), ("exterior", 79, 60), ("exterior", 153, 120),
+                                      ("interior", 39, 30), ("interior", 85, 60), ("interior", 158, 120)])
+def test_digits_like_table1_remaining(B, digits, kind, t, L):
+    """The other six intervals of Table 1 (Sec. 4.3) with AUTO (the dense direct solver for
+    n = 784), against the oracle and the dense spectrum: exact count, sigma within 1e-10,
+    residuals <= 1e-10, orthonormal vectors."""
+    A, s = digits
+    a, b = interval(s, kind, t)
+    truth = np.sort(s[(s >= a) & (s <= b)])
+    assert truth.size == t
+    Vin = synth.gaussian_block(A.n, L, 5)
+    ref = O.solve_interval(A, a, b, 32, L, 4, Vin, variant="nt", norm_A=s[0])
+    assert ref.sigma.size == t
+    ctx = B.Context()
+    M = B.Matrix.from_csr(ctx, A)
+    out = M.solve_interval(a, b, B.params(N=32, L=L, M=4, variant="nt", norm_A=s[0]), torch.from_numpy(Vin).cuda())
+    assert out.stats["solver_used"] == B.SOLVER_DENSE
+    assert out.sigma.size == t
+    assert np.max(np.abs(out.sigma - truth) / truth) <= 1e-10
+    assert np.max(np.abs(out.sigma - ref.sigma) / ref.sigma) <= 1e-10
+    assert out.res_u.max() <= 1e-10 and out.res_v.max() <= 1e-10
+    assert np.max(np.abs(out.V.T @ out.V - np.eye(t))) <= 1e-10
+    M.close()
+    ctx.close()
