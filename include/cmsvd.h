@@ -183,6 +183,19 @@ int cmsvd_context_create(void* stream, cmsvd_context** out);
 int cmsvd_context_destroy(cmsvd_context* ctx);   /* NULL is accepted */
 
 /*
+ * Arithmetic of the tall dense products of the rank truncation and of qr(A V~) (Alg. 1 steps
+ * 3-4: Grams X^T Y and products X W with n >= 16384 rows and 32..1024 columns) on this context.
+ * mode 0 (default): FP64-accurate emulation on the BF16 tensor cores. Every FP64 operand is cut
+ * into 8 slices of 7 bits (integers below 128, exact in bf16) under a power-of-two scale per
+ * row or column; the slice products are BF16 GEMMs with FP32 accumulation, exact because every
+ * sum of at most 1024 such products stays below 2^24, and they are added in FP64 per level of
+ * equal scale. Each result is within a few 2^-53 of the products of the largest entries that
+ * share its scales. mode 1: the FP64 pipe only. The paper computes these steps in FP64
+ * (MATLAB svd and qr); this is a property of the implementation. CMSVD_INVALID_ARG otherwise.
+ */
+int cmsvd_context_set_dense_arith(cmsvd_context* ctx, int32_t mode);
+
+/*
  * Sparse matrix A (m x n, m >= 1, n >= 1) in CSR form (the problem's A, Sec. 1, Eq. psvd).
  * rowptr: int64[m+1], colidx: int32[nnz], vals: float64[nnz]; where = 0 for host arrays, 1 for
  * device arrays. The library copies them into its own device memory (the caller keeps
@@ -258,7 +271,9 @@ int cmsvd_quadrature(cmsvd_context* ctx, double a, double b, int32_t N, int32_t 
  * orthogonalizations in the rank truncation (Alg. 1 step 3) and in qr(A V~)
  * (step 4). X: n x c1 (leading dimension ldx >= c1), Y: n x c2 (ldy >= c2),
  * G: c1 x c2 row-major; all device, all FP64. Deterministic: the rows are split
- * into fixed chunks whose partial products are added in chunk order.
+ * into fixed chunks whose partial products are added in chunk order. For n >= 16384 and
+ * 32 <= c1 <= 1024, c2 >= 32 it follows the context's dense arithmetic
+ * (cmsvd_context_set_dense_arith).
  * workspace: device scratch of at least cmsvd_gram_workspace_size bytes, owned by
  * the caller. 1 <= c1, c2 <= 4096, n >= 1.
  */
@@ -287,6 +302,16 @@ int cmsvd_gram(cmsvd_context* ctx, int64_t n, int32_t c1, int32_t c2, const doub
  */
 int cmsvd_gram_noalloc(cmsvd_context* ctx, int64_t n, int32_t c1, int32_t c2, const double* X, int64_t ldx,
                        const double* Y, int64_t ldy, double* G);
+
+/*
+ * Z = X W for a tall device block X (n x c1, ldx >= c1) and a small one W (c1 x c2, ldw >= c2),
+ * Z n x c2 (ldz >= c2), all row-major FP64: the product that forms the orthonormal bases of the
+ * rank truncation (Alg. 1 step 3) and the Ritz vectors (step 5). For n >= 16384 and
+ * 32 <= c1 <= 1024, c2 >= 32 it follows the context's dense arithmetic
+ * (cmsvd_context_set_dense_arith). 1 <= c1, c2 <= 4096.
+ */
+int cmsvd_gemm(cmsvd_context* ctx, int64_t n, int32_t c1, int32_t c2, const double* X, int64_t ldx,
+               const double* W, int64_t ldw, double* Z, int64_t ldz);
 
 /* Device workspace (bytes) that cmsvd_moments / cmsvd_solve_interval need for A and *p. */
 int cmsvd_workspace_size(const cmsvd_matrix* A, const cmsvd_params* p, size_t* bytes);

@@ -66,6 +66,7 @@ _SIGS = {
     "cmsvd_params_default": (C.c_int, [C.POINTER(cmsvd_params)]),
     "cmsvd_context_create": (C.c_int, [_P, C.POINTER(_P)]),
     "cmsvd_context_destroy": (C.c_int, [_P]),
+    "cmsvd_context_set_dense_arith": (C.c_int, [_P, C.c_int32]),
     "cmsvd_csr_create": (C.c_int, [_P, _I64, _I64, _I64, _P, _P, _P, C.c_int, C.c_int32, C.POINTER(_P)]),
     "cmsvd_csr_destroy": (C.c_int, [_P]),
     "cmsvd_csr_shape": (C.c_int, [_P, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I64)]),
@@ -78,6 +79,7 @@ _SIGS = {
     "cmsvd_gram_workspace_size": (C.c_int, [_P, _I64, C.c_int32, C.c_int32, C.POINTER(C.c_size_t)]),
     "cmsvd_gram": (C.c_int, [_P, _I64, C.c_int32, C.c_int32, _P, _I64, _P, _I64, _P, _P, C.c_size_t]),
     "cmsvd_gram_noalloc": (C.c_int, [_P, _I64, C.c_int32, C.c_int32, _P, _I64, _P, _I64, _P]),
+    "cmsvd_gemm": (C.c_int, [_P, _I64, C.c_int32, C.c_int32, _P, _I64, _P, _I64, _P, _I64]),
     "cmsvd_moments": (C.c_int, [_P, C.c_double, C.c_double, C.POINTER(cmsvd_params), _P, _P, _P, C.c_size_t,
                                 C.POINTER(cmsvd_stats)]),
     "cmsvd_solve_interval": (C.c_int, [_P, C.c_double, C.c_double, C.POINTER(cmsvd_params), _P, _P, C.c_size_t,
@@ -275,6 +277,19 @@ def cmsvd_gram(ctx: int, X, Y, G, workspace) -> None:
                             _ptr(workspace), workspace.numel() * workspace.element_size()), "cmsvd_gram")
 
 
+def cmsvd_gemm(ctx: int, X, W, Z) -> None:
+    """Z (n x c2) = X (n x c1) W (c1 x c2), float64 CUDA tensors with contiguous rows."""
+    import torch
+    n, c1 = X.shape
+    if W.shape[0] != c1 or tuple(Z.shape) != (n, W.shape[1]):
+        raise ValueError("shapes must be X n x c1, W c1 x c2, Z n x c2")
+    for name, t in (("X", X), ("W", W), ("Z", Z)):
+        if t.dtype != torch.float64 or not t.is_cuda or t.stride(1) != 1:
+            raise ValueError(f"{name} must be a float64 CUDA tensor with contiguous rows")
+    _check(lib().cmsvd_gemm(_P(ctx), n, c1, W.shape[1], _ptr_any(X), X.stride(0), _ptr_any(W), W.stride(0),
+                            _ptr_any(Z), Z.stride(0)), "cmsvd_gemm")
+
+
 def cmsvd_gram_noalloc(ctx: int, X, Y, G) -> None:
     """G = X^T Y like cmsvd_gram, using the library's fixed device scratch (no workspace)."""
     n, c1, c2 = _gram_operands(X, Y, G)
@@ -465,6 +480,10 @@ class Context:
         self.stream = stream
         self.handle = cmsvd_context_create(stream.cuda_stream)
         self._matrices = weakref.WeakSet()
+
+    def set_dense_arith(self, mode: int) -> None:
+        """0: tall Grams and products emulated in FP64 on the BF16 tensor cores (default); 1: FP64 pipe."""
+        _check(lib().cmsvd_context_set_dense_arith(_P(self.handle), int(mode)), "cmsvd_context_set_dense_arith")
 
     def close(self):
         """Destroy the context; matrices created on it are destroyed first."""

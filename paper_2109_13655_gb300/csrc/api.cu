@@ -233,11 +233,19 @@ int cmsvd_context_create(void* stream, cmsvd_context** out) {
 int cmsvd_context_destroy(cmsvd_context* c) {
     if (!c) return CMSVD_OK;
     if (c->s) cudaStreamSynchronize(c->s);
+    ozaki_release(c);
     if (c->s) cudaStreamDestroy(c->s);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
     if (c->ev_out) cudaEventDestroy(c->ev_out);
     if (c->pinned) cudaFreeHost(c->pinned);
     delete c;
+    return CMSVD_OK;
+}
+
+int cmsvd_context_set_dense_arith(cmsvd_context* ctx, int32_t mode) {
+    if (!ctx) { set_error("NULL context"); return CMSVD_INVALID_ARG; }
+    if (mode != 0 && mode != 1) { set_error("mode must be 0 (tensor-core FP64 emulation) or 1 (FP64 pipe)"); return CMSVD_INVALID_ARG; }
+    ctx->dense_arith = mode;
     return CMSVD_OK;
 }
 
@@ -393,6 +401,19 @@ int cmsvd_gram(cmsvd_context* ctx, int64_t n, int32_t c1, int32_t c2, const doub
     CM_TRY(se.open(ctx));
     CM_TRY(gram(X, ldx, c1, Y, ldy, c2, n, G, (double*)workspace, (ws_bytes - 256) / sizeof(double), ctx->sm_count,
                 ctx->s));
+    return se.close();
+}
+
+int cmsvd_gemm(cmsvd_context* ctx, int64_t n, int32_t c1, int32_t c2, const double* X, int64_t ldx, const double* W,
+               int64_t ldw, double* Z, int64_t ldz) {
+    if (!ctx || !X || !W || !Z) { set_error("NULL argument"); return CMSVD_INVALID_ARG; }
+    if (n < 1 || c1 < 1 || c2 < 1 || c1 > 4096 || c2 > 4096 || ldx < c1 || ldw < c2 || ldz < c2) {
+        set_error("need n >= 1, 1 <= c1, c2 <= 4096, ldx >= c1, ldw >= c2, ldz >= c2");
+        return CMSVD_INVALID_ARG;
+    }
+    Session se;
+    CM_TRY(se.open(ctx));
+    CM_TRY(gemm_nn(X, ldx, W, ldw, Z, ldz, n, c1, c2, ctx->s, 0));
     return se.close();
 }
 

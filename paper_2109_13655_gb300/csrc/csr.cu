@@ -23,6 +23,11 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
     return e == cudaErrorMemoryAllocation ? CMSVD_OUT_OF_MEMORY : CMSVD_CUDA_ERROR;
 }
 
+cmsvd_context*& current_ctx() {
+    static thread_local cmsvd_context* c = nullptr;
+    return c;
+}
+
 // ----------------------------------------------------------------------------- profiler
 Profiler& prof() {
     static thread_local Profiler p;

@@ -159,6 +159,8 @@ size_t gram_partials_cap(int c, int sm_count) {
 
 int gram(const double* X, int64_t ldx, int c1, const double* Y, int64_t ldy, int c2, int64_t n, double* G,
          double* partials, size_t partials_cap, int sm_count, cudaStream_t s) {
+    cmsvd_context* ctx = current_ctx();
+    if (ctx && ctx->s == s && ozaki_applies(ctx, n, c1, c2)) return gram_ozaki(ctx, X, ldx, c1, Y, ldy, c2, n, G, c2);
     int nc;
     int64_t rpc;
     const int sym = (X == Y && c1 == c2 && ldx == ldy) ? 1 : 0;
@@ -231,6 +233,8 @@ __global__ void __launch_bounds__(256) k_gemm_nn(const double* __restrict__ X, i
 int gemm_nn(const double* X, int64_t ldx, const double* W, int64_t ldw, double* Z, int64_t ldz, int64_t n, int c1,
             int c2, cudaStream_t s, int upper) {
     if (n <= 0 || c2 <= 0) return CMSVD_OK;
+    cmsvd_context* ctx = current_ctx();
+    if (ctx && ctx->s == s && ozaki_applies(ctx, n, c1, c2)) return gemm_ozaki(ctx, X, ldx, W, ldw, Z, ldz, n, c1, c2);
     dim3 grid((c2 + GT - 1) / GT, (unsigned)((n + GT - 1) / GT));
     double work = 0.0;   // multiply-adds actually performed per row
     for (int cc0 = 0; cc0 < c2; cc0 += GT) work += (double)(upper ? min(c1, cc0 + GT) : c1) * min(GT, c2 - cc0);
@@ -438,22 +442,48 @@ __device__ __forceinline__ bool grid_barrier(unsigned* ctl, unsigned nblocks) {
 constexpr int JC_MAXDIM = 1024;             // L M <= 512; the dense direct solver factors n <= 1024
 
 // Cooperative form for 97..1024 columns: one CTA per pair of a round (round-robin ordering,
-// the pairs of a round are disjoint), all sweeps in one launch, a bounded grid barrier
-// between rounds. Columns whose squared norm is below negl (1e-36 ||Bm||_F^2) are treated
-// as zero. Each thread holds its rows of both columns and both V columns in
-// registers, so a round costs one L2 round trip. GB300 runs an FP64 warp instruction in
-// 16 clocks whatever its active lanes, so only warp 0 computes the rotation angle and
-// shares it through shared memory. (Measured alternatives, slower on this part: an 8-CTA
-// thread-block cluster keeping column blocks in shared memory, 25-36 ms per 256 x 256
-// SVD, FP64-bound on its 8 SMs; block-cyclic cooperative kernels with 2 or 4 columns per
-// block, 31 and 21 ms; this form, 16 ms.)
+// the pairs of a round are disjoint), all sweeps in one launch. Within a sweep the rounds are
+// ordered by data flow, not by a grid barrier: every column carries a version (the rounds
+// that have updated it, ver[]), and the CTA that owns a pair in round r waits only until both
+// of its columns have reached version r, rotates them, and publishes version r + 1. Each
+// column is updated once per round, by the owner of its pair, so these waits order every
+// read after the write it needs; a round then costs one L2 round trip of two flags instead
+// of a barrier over every CTA. One bounded grid barrier per sweep decides convergence (did
+// any CTA rotate). Columns whose squared norm is below negl (1e-36 ||Bm||_F^2) are treated
+// as zero. Each thread holds its rows of both columns and both V columns in registers.
+// GB300 runs an FP64 warp instruction in 16 clocks whatever its active lanes, so only warp 0
+// computes the rotation angle and shares it through shared memory. (Measured alternatives,
+// slower on this part: an 8-CTA thread-block cluster keeping column blocks in shared memory,
+// 25-36 ms per 256 x 256 SVD, FP64-bound on its 8 SMs; block-cyclic cooperative kernels with
+// 2 or 4 columns per block, 31 and 21 ms; this form with a grid barrier per round, 16 ms.)
+// Every wait is bounded: past the limit a CTA sets ctl[3] and every CTA leaves.
 // RPT: rows (and V entries) per thread, the smallest of 2, 4, 8 with 128 RPT >= rows, cols
 // (the FP64 FMAs of the dot products run on every register slot, so a larger RPT than
 // needed costs FP64 issue slots).
+__device__ __forceinline__ bool jc_wait_cols(const unsigned* ver, int p, int q, unsigned gen, unsigned* ctl) {
+    __shared__ int sh_fail;
+    if (threadIdx.x == 0) {
+        volatile const unsigned* vp = ver + p;
+        volatile const unsigned* vq = ver + q;
+        volatile unsigned* err = ctl + 3;
+        long long it = 0;
+        int fail = 0;
+        while ((*vp < gen || *vq < gen)) {
+            if (*err != 0) { fail = 1; break; }
+            if (++it > 20000000LL) { atomicExch(ctl + 3, 1u); fail = 1; break; }   // >= 0.8 s
+            if (it > 2048) __nanosleep(32);
+        }
+        __threadfence();   // the columns' data is read after their versions
+        sh_fail = fail;
+    }
+    __syncthreads();
+    return sh_fail == 0;
+}
+
 template <int RPT>
 __global__ void __launch_bounds__(128) k_jacobi_coop(double* __restrict__ Xc, double* __restrict__ V, int rows, int cols,
                                                      int np, double tol, const double* __restrict__ fro2, int max_sweeps,
-                                                     unsigned* ctl, unsigned* rot) {
+                                                     unsigned* ctl, unsigned* rot, unsigned* ver) {
     __shared__ double sh[3][4];
     __shared__ double sh_cs, sh_sn;
     __shared__ int sh_ok;
@@ -462,11 +492,15 @@ __global__ void __launch_bounds__(128) k_jacobi_coop(double* __restrict__ Xc, do
     int sweep = 0;
     for (; sweep < max_sweeps; ++sweep) {
         for (int round = 0; round < np - 1; ++round) {
+            const unsigned gen = (unsigned)(sweep * (np - 1) + round);
             int p, q;
             if (k == 0) { p = round; q = np - 1; }
             else { p = (round + k) % (np - 1); q = (round - k + (np - 1)) % (np - 1); }
+            if (p > q) { const int t = p; p = q; q = t; }
+            // a padding column (np = cols + 1) has no data: its partner only moves on
+            const int pw = p < cols ? p : q, qw = q < cols ? q : p;
+            if (!jc_wait_cols(ver, pw, qw, gen, ctl)) return;
             if (p < cols && q < cols) {
-                if (p > q) { const int t = p; p = q; q = t; }
                 double* xp = Xc + (size_t)p * rows;
                 double* xq = Xc + (size_t)q * rows;
                 double* vp = V + (size_t)p * cols;
@@ -510,20 +544,26 @@ __global__ void __launch_bounds__(128) k_jacobi_coop(double* __restrict__ Xc, do
                     for (int u = 0; u < RPT; ++u) {
                         const int i = threadIdx.x + 128 * u;
                         if (i < rows) {
-                            xp[i] = cs * xa[u] - sn * xb[u];
-                            xq[i] = sn * xa[u] + cs * xb[u];
+                            __stcg(xp + i, cs * xa[u] - sn * xb[u]);
+                            __stcg(xq + i, sn * xa[u] + cs * xb[u]);
                         }
                         if (i < cols) {
-                            vp[i] = cs * va[u] - sn * vb[u];
-                            vq[i] = sn * va[u] + cs * vb[u];
+                            __stcg(vp + i, cs * va[u] - sn * vb[u]);
+                            __stcg(vq + i, sn * va[u] + cs * vb[u]);
                         }
                     }
                     if (threadIdx.x == 0) atomicExch(rot + sweep, 1u);
                 }
-                __syncthreads();   // sh, sh_ok reused by the next round
             }
-            if (!grid_barrier(ctl, gridDim.x)) return;
+            // publish: the columns' new data before their new versions
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                if (p < cols) atomicExch(ver + p, gen + 1);
+                if (q < cols) atomicExch(ver + q, gen + 1);
+            }
         }
+        if (!grid_barrier(ctl, gridDim.x)) return;   // every rotation of the sweep is counted
         if (*(volatile unsigned*)(rot + sweep) == 0) { ++sweep; break; }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) ctl[2] = sweep;
@@ -597,11 +637,13 @@ int jacobi_svd(const double* Bm, int brows, int bcols, int trans, double* Xc, do
         CM_LAUNCH();
         return CMSVD_OK;
     }
-    // all sweeps in one launch; ctl (4 words) and rot (one word per sweep) live in jac_ctl
+    // all sweeps in one launch; ctl (4 words), rot (one word per sweep) and the column versions
+    // (JC_MAXDIM words from word 64) live in jac_ctl
     unsigned* ctl = jac_ctl;
     unsigned* rot = jac_ctl + 4;
+    unsigned* ver = jac_ctl + 64;
     const int max_sweeps = 40;
-    CM_CUDA(cudaMemsetAsync(ctl, 0, sizeof(unsigned) * (4 + max_sweeps), s));
+    CM_CUDA(cudaMemsetAsync(ctl, 0, sizeof(unsigned) * (64 + JC_MAXDIM), s));
     if (rows > JC_MAXDIM || cols > JC_MAXDIM) { set_error("Jacobi SVD supports at most %d rows and columns", JC_MAXDIM); return CMSVD_NOT_SUPPORTED; }
     const int grid = np / 2;
     {
@@ -612,7 +654,8 @@ int jacobi_svd(const double* Bm, int brows, int bcols, int trans, double* Xc, do
         CM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 128, 0));
         if (per_sm * ctx->sm_count < grid) { set_error("Jacobi grid of %d CTAs cannot be co-resident", grid); return CMSVD_NOT_SUPPORTED; }
         ProfScope ps(CMSVD_PROF_JACOBI, s, 0.0, 0.0, 1);
-        void* args[] = {&Xc, &V, (void*)&rows, (void*)&cols, (void*)&np, (void*)&tol, &fro2, (void*)&max_sweeps, &ctl, &rot};
+        void* args[] = {&Xc, &V, (void*)&rows, (void*)&cols, (void*)&np, (void*)&tol, &fro2, (void*)&max_sweeps, &ctl, &rot,
+                        &ver};
         CM_CUDA(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(128), args, 0, s));
         note_launch();
     }

@@ -132,6 +132,10 @@ struct cmsvd_context {
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     int sm_count = 0;
     int* pinned = nullptr;             // host-pinned flags for polling
+    int dense_arith = 0;               // 0: FP64-accurate tall products on BF16 tensor cores (ozaki.cu); 1: FP64 pipe
+    void* blas = nullptr;              // cuBLAS handle of the tensor-core slice products (made on first use)
+    void* oz_buf = nullptr;            // their scratch, kept between calls
+    size_t oz_bytes = 0;
 };
 
 struct cmsvd_matrix {
@@ -157,6 +161,17 @@ struct cmsvd_result {
 
 namespace cmsvd {
 
+// The context of the entry point running on this host thread (set by Session::open).
+cmsvd_context*& current_ctx();
+
+// FP64-accurate tall-skinny products from exact BF16 tensor-core slice products (ozaki.cu).
+bool ozaki_applies(const cmsvd_context* ctx, int64_t n, int c1, int c2);
+int gram_ozaki(cmsvd_context* ctx, const double* X, int64_t ldx, int c1, const double* Y, int64_t ldy, int c2,
+               int64_t n, double* G, int64_t ldg);
+int gemm_ozaki(cmsvd_context* ctx, const double* X, int64_t ldx, const double* W, int64_t ldw, double* Z, int64_t ldz,
+               int64_t n, int c1, int c2);
+void ozaki_release(cmsvd_context* ctx);
+
 // ----------------------------------------------------------------------------- entry-point session
 // An entry point's work runs on the context's internal stream: open() makes the context's
 // device current (remembering the caller's), orders the internal stream after the caller's
@@ -167,6 +182,7 @@ namespace cmsvd {
 struct Session {
     cmsvd_context* c = nullptr;
     int prev = -1;
+    cmsvd_context* outer = nullptr;
     Session() = default;
     Session(const Session&) = delete;
     Session& operator=(const Session&) = delete;
@@ -178,13 +194,18 @@ struct Session {
         restore();
     }
     void restore() {
-        if (prev >= 0) cudaSetDevice(prev);
+        if (prev >= 0) {
+            cudaSetDevice(prev);
+            current_ctx() = outer;
+        }
         prev = -1;
     }
     int open(cmsvd_context* ctx) {
         int d = -1;
         CM_CUDA(cudaGetDevice(&d));
         prev = d;
+        outer = current_ctx();
+        current_ctx() = ctx;
         CM_CUDA(cudaSetDevice(ctx->device));
         CM_CUDA(cudaEventRecord(ctx->ev_in, ctx->user));
         CM_CUDA(cudaStreamWaitEvent(ctx->s, ctx->ev_in, 0));
@@ -296,7 +317,7 @@ int orth_qr(const double* X, int64_t ldx, int64_t n, int c, double* Q, double* R
 // left singular vectors of Bm. sv_j = ||Xc_j||, perm sorts sv descending.
 // flag2: 16 bytes of device scratch (8-byte aligned + 8).
 // tol > 0 overrides the rotation threshold max(1e-15, rows u) (loose sweeps for the deflation).
-// jac_ctl: 64 device words of scratch for the cooperative sweeps.
+// jac_ctl: 64 + 1024 device words of scratch for the cooperative sweeps.
 int jacobi_svd(const double* Bm, int brows, int bcols, int trans, double* Xc, double* V, double* sv, int* perm,
                int* flag2, cmsvd_context* ctx, double tol, unsigned* jac_ctl);
 

@@ -892,7 +892,8 @@ template <class V, int MODE>
 static int launch_panel(Lz& z, double* S, int64_t lds, cudaStream_t s) {
     const int kc = MODE == 0 ? z.Mk : (MODE == 1 ? 2 * z.J : 4);
     const size_t smem = panel_smem(kc, MODE == 2 ? z.Lorig : z.L, z.P);
-    if (smem > 48 * 1024) CM_CUDA(cudaFuncSetAttribute(k_panel<V, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // above 48 KB of shared memory in all (dynamic plus the kernel's static word) a launch needs the opt-in
+    if (smem > 32 * 1024) CM_CUDA(cudaFuncSetAttribute(k_panel<V, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_panel<V, MODE><<<z.nblk, lz_block(z.L), smem, s>>>(z, S, lds);
     CM_LAUNCH();
     return CMSVD_OK;

@@ -1,0 +1,379 @@
+// FP64-accurate tall-skinny Gram (G = X^T Y) and product (Z = X W) from exact BF16 tensor-core
+// products: the rank truncation (Alg. 1 step 3) and qr(A V~) (step 4) are built on these two
+// products, and GB300's FP64 pipe issues 2 FMAs per clock per SM against its BF16 tensor cores'
+// ~900.
+//
+// Splitting (an Ozaki-type scheme): every operand value is written as
+//   x = s 2^e sum_{p=1..S} d_p 2^{-7p} + r,   d_p in [0, 127] (with the sign s of x), |r| < 2^(e-56),
+// with S = 8 slices of 7 bits and a power-of-two scale 2^e > |x| per column (Gram) or per row /
+// column (product). A slice value d is an integer below 128, so it is exact in bf16, every product
+// of two slices is an integer below 2^14, and any sum of at most 1024 such products is an integer
+// below 2^24: the FP32 accumulation of the tensor cores is then exact whatever its order. The
+// products of one level k = p + q share the scale 2^(-7k), so up to 1024 / K products of a level
+// are stacked along the contraction and formed by one GEMM. The level sums are added into the
+// FP64 result, scaled by 2^(e_i + f_j - 7k), in FP64. Pairs with p + q > S + 1 are dropped: per
+// product their sum is below 2^-53 of 2^(e_i + f_j). With the truncation of the operands to 56
+// bits below their scales, each emulated product is within a few 2^-53 of 2^(e_i + f_j), that is
+// of the products of the largest entries sharing the scales: FP64 accuracy for operands whose
+// entries are of one magnitude within a row or column (orthogonalized blocks), and the accuracy
+// class of an FP64 Gram of this length (sqrt(n) u sum |x||y|) in general.
+//
+// The slice products are plain BF16 GEMMs with FP32 outputs and run on cuBLAS; slicing and the
+// FP64 epilogue are this file's kernels.
+#include "internal.cuh"
+#include <cublas_v2.h>
+#include <climits>
+
+namespace cmsvd {
+
+constexpr int OZ_S = 8;          // slices
+constexpr int OZ_BITS = 7;       // bits per slice
+constexpr int OZ_KMAX = 1024;    // products per exact FP32 sum
+constexpr int OZ_CHUNK = 128;    // Gram: rows per chunk (8 stacked slices x 128 <= 1024)
+
+// ----------------------------------------------------------------------------- scales
+// ilogb of the largest |x| of each column (cols of an n x c row-major block) / each row.
+__global__ void k_oz_col_exp(const double* __restrict__ X, int64_t ld, int64_t n, int c, int* __restrict__ ex) {
+    for (int j = threadIdx.x; j < c; j += blockDim.x) {
+        int best = INT_MIN;
+        for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+            const double v = X[i * ld + j];
+            if (v != 0.0) best = max(best, ilogb(v));
+        }
+        if (best != INT_MIN) atomicMax(ex + j, best);
+    }
+}
+
+__global__ void k_oz_row_exp(const double* __restrict__ X, int64_t ld, int64_t n, int c, int* __restrict__ ex) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; i < n;
+         i += ((int64_t)gridDim.x * blockDim.x) / 32) {
+        int best = INT_MIN;
+        for (int j = lane; j < c; j += 32) {
+            const double v = X[i * ld + j];
+            if (v != 0.0) best = max(best, ilogb(v));
+        }
+        for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
+        if (lane == 0) ex[i] = best;
+    }
+}
+
+// The S slices of x relative to the scale 2^(e+1) (e = ilogb of the largest |x| it shares a
+// scale with): the magnitude as a fixed-point integer with 7 S = 56 fractional bits, cut into
+// 7-bit fields (exact integer arithmetic), each carrying the sign of x.
+// scale exponents are initialised to OZ_NONE (all-zero column or row)
+constexpr int OZ_NONE = (int)0x80808080;
+__device__ __forceinline__ int oz_e(int e) { return e == OZ_NONE || e == INT_MIN ? 0 : e; }
+__device__ __forceinline__ int oz_shift(int e) { return e == OZ_NONE || e == INT_MIN ? 0 : e + 1; }
+
+__device__ __forceinline__ void oz_slices(double x, int e, float (&d)[OZ_S]) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int E = (int)((b >> 52) & 0x7ff);
+    unsigned long long m = b & ((1ull << 52) - 1);
+    int Ee = E;
+    if (E == 0) Ee = 1; else m |= 1ull << 52;
+    // |x| = m 2^(Ee-1075); scale 2^(e+1): V = floor(|x| 2^(56-e-1)) = m >> (1075 - Ee + e + 1 - 56),
+    // below 2^56 since |x| < 2^(e+1); the shift is -3 for the largest value of a normal scale group
+    const int sh = 1075 - Ee + e + 1 - OZ_BITS * OZ_S;
+    const unsigned long long V = (x == 0.0 || sh >= 64) ? 0ull : (sh >= 0 ? (m >> sh) : (m << (-sh)));
+    const float sg = (b >> 63) ? -1.f : 1.f;
+#pragma unroll
+    for (int p = 0; p < OZ_S; ++p) d[p] = sg * (float)((V >> (OZ_BITS * (OZ_S - 1 - p))) & 127ull);
+}
+
+// Gram operand: X (n x c row-major) -> per chunk b of 128 rows, S slices of c x 128 column-major
+// (ld c), slice p at block position p (rev = 0) or S-1-p (rev = 1).
+__global__ void k_oz_slice_gram(const double* __restrict__ X, int64_t ld, int64_t n, int c, const int* __restrict__ ex,
+                                int rev, __nv_bfloat16* __restrict__ out) {
+    const int64_t total = n * c;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / c;
+        const int j = (int)(e % c);
+        float d[OZ_S];
+        oz_slices(X[i * ld + j], oz_e(ex[j]), d);
+        const int64_t b = i / OZ_CHUNK, il = i % OZ_CHUNK;
+        __nv_bfloat16* blk = out + b * (int64_t)OZ_S * c * OZ_CHUNK;
+#pragma unroll
+        for (int p = 0; p < OZ_S; ++p) {
+            const int pos = rev ? OZ_S - 1 - p : p;
+            blk[(int64_t)pos * c * OZ_CHUNK + il * c + j] = __float2bfloat16_rn(d[p]);
+        }
+    }
+}
+
+// Product operands. X (n x c1, row-major, row scale): column-major (S c1) x n, ld S c1, slice p of
+// row i at rows p c1 .. p c1 + c1 - 1 of column i. W (c1 x c2, row-major, column scale):
+// S column-major c2 x c1 blocks (ld c2), slice q at block S-1-q (reversed).
+__global__ void k_oz_slice_rows(const double* __restrict__ X, int64_t ld, int64_t n, int c1, const int* __restrict__ ex,
+                                __nv_bfloat16* __restrict__ out) {
+    const int64_t total = n * c1;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / c1;
+        const int j = (int)(e % c1);
+        float d[OZ_S];
+        oz_slices(X[i * ld + j], oz_e(ex[i]), d);
+        __nv_bfloat16* col = out + i * (int64_t)OZ_S * c1;
+#pragma unroll
+        for (int p = 0; p < OZ_S; ++p) col[(int64_t)p * c1 + j] = __float2bfloat16_rn(d[p]);
+    }
+}
+
+__global__ void k_oz_slice_w(const double* __restrict__ W, int64_t ldw, int c1, int c2, const int* __restrict__ ex,
+                             __nv_bfloat16* __restrict__ out) {
+    const int64_t total = (int64_t)c1 * c2;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(e / c2), l = (int)(e % c2);
+        float d[OZ_S];
+        oz_slices(W[(int64_t)k * ldw + l], oz_e(ex[l]), d);
+#pragma unroll
+        for (int q = 0; q < OZ_S; ++q)
+            out[(int64_t)(OZ_S - 1 - q) * c2 * c1 + (int64_t)k * c2 + l] = __float2bfloat16_rn(d[q]);
+    }
+}
+
+// ----------------------------------------------------------------------------- epilogues
+// Gram, pass 1: P[part][j + k c1] = sum_lvl 2^(-7 lvl) sum_{b in part} C[lvl][b][j + k c1] over a
+// part of OZ_PART chunks of the current group (blockIdx.y); the FP32 chunk sums are exact
+// integers and are added in FP64.
+constexpr int OZ_PART = 16;
+__global__ void k_oz_gram_part(const float* __restrict__ C, int nb, int64_t cnt, double* __restrict__ P) {
+    const int part = blockIdx.y;
+    const int b0 = part * OZ_PART, b1 = b0 + OZ_PART < nb ? b0 + OZ_PART : nb;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * blockDim.x) {
+        double v = 0.0;
+        for (int lvl = 2; lvl <= OZ_S + 1; ++lvl) {
+            const float* Cl = C + (int64_t)(lvl - 2) * nb * cnt;
+            double s = 0.0;
+            for (int b = b0; b < b1; ++b) s += (double)Cl[(int64_t)b * cnt + e];
+            v = __fma_rn(s, ldexp(1.0, -OZ_BITS * lvl), v);   // exact scaling by a power of two
+        }
+        P[(int64_t)part * cnt + e] = v;
+    }
+}
+
+// Gram, pass 2: G[j][k] = 2^(ex_j + 1 + ey_k + 1) sum_part P[part][j + k c1], parts in order.
+__global__ void k_oz_gram_fin(const double* __restrict__ P, int nparts, int c1, int c2, const int* __restrict__ ex,
+                              const int* __restrict__ ey, double* __restrict__ G, int64_t ldg) {
+    const int64_t cnt = (int64_t)c1 * c2;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e % c1), k = (int)(e / c1);
+        double v = 0.0;
+        for (int q = 0; q < nparts; ++q) v += P[(int64_t)q * cnt + e];
+        G[(int64_t)j * ldg + k] = ldexp(v, oz_shift(ex[j]) + oz_shift(ey[k]));
+    }
+}
+
+// Product: Z[i][l] = sum_g 2^(ex_i + 1 + fw_l + 1 - 7 lvl_g) C[g][l + i c2] over the ng GEMM
+// outputs of a row block (exact FP32 integers), summed in FP64 and written once.
+struct OzLevels { int lvl[64]; double scale[64]; };   // level of each GEMM output and 2^(-7 level)
+__global__ void k_oz_gemm_epi(const float* __restrict__ C, int ng, OzLevels lv, int64_t n, int c2,
+                              const int* __restrict__ ex, const int* __restrict__ ew, double* __restrict__ Z, int64_t ldz) {
+    const int64_t cnt = n * c2;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / c2;
+        const int l = (int)(e % c2);
+        double v = 0.0;
+        for (int g = 0; g < ng; ++g) v = __fma_rn((double)C[(int64_t)g * cnt + e], lv.scale[g], v);
+        Z[i * ldz + l] = ldexp(v, oz_shift(ex[i]) + oz_shift(ew[l]));
+    }
+}
+
+// ----------------------------------------------------------------------------- host
+static int blas_ok(cublasStatus_t s, const char* what) {
+    if (s == CUBLAS_STATUS_SUCCESS) return CMSVD_OK;
+    set_error("%s failed (cuBLAS status %d)", what, (int)s);
+    return s == CUBLAS_STATUS_ALLOC_FAILED ? CMSVD_OUT_OF_MEMORY : CMSVD_CUDA_ERROR;
+}
+
+static int oz_handle(cmsvd_context* ctx, cublasHandle_t* h) {
+    if (!ctx->blas) {
+        cublasHandle_t x = nullptr;
+        CM_TRY(blas_ok(cublasCreate(&x), "cublasCreate"));
+        ctx->blas = x;
+    }
+    *h = (cublasHandle_t)ctx->blas;
+    CM_TRY(blas_ok(cublasSetStream(*h, ctx->s), "cublasSetStream"));
+    return CMSVD_OK;
+}
+
+// Scratch kept by the context between calls (grown on demand).
+static int oz_scratch(cmsvd_context* ctx, size_t bytes, char** out) {
+    if (ctx->oz_bytes < bytes) {
+        if (ctx->oz_buf) {
+            CM_CUDA(cudaStreamSynchronize(ctx->s));
+            cudaFree(ctx->oz_buf);
+            ctx->oz_buf = nullptr;
+            ctx->oz_bytes = 0;
+        }
+        CM_CUDA(cudaMalloc(&ctx->oz_buf, bytes));
+        ctx->oz_bytes = bytes;
+    }
+    *out = (char*)ctx->oz_buf;
+    return CMSVD_OK;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+bool ozaki_applies(const cmsvd_context* ctx, int64_t n, int c1, int c2) {
+    return ctx && ctx->dense_arith == 0 && n >= 16384 && c1 >= 32 && c2 >= 32 && c1 <= OZ_KMAX;
+}
+
+// G (c1 x c2, row-major, ldg) = X^T Y.
+int gram_ozaki(cmsvd_context* ctx, const double* X, int64_t ldx, int c1, const double* Y, int64_t ldy, int c2,
+               int64_t n, double* G, int64_t ldg) {
+    cudaStream_t s = ctx->s;
+    cublasHandle_t h;
+    CM_TRY(oz_handle(ctx, &h));
+    const int64_t nb = (n + OZ_CHUNK - 1) / OZ_CHUNK;
+    const bool same = X == Y && c1 == c2 && ldx == ldy;
+    // chunk results of all levels of a group of chunks: at most 256 MB of FP32 at a time
+    int64_t nbg = (int64_t)((256ll << 20) / ((int64_t)c1 * c2 * 4 * OZ_S));
+    if (nbg < 1) nbg = 1;
+    if (nbg > nb) nbg = nb;
+    const size_t bx = align256((size_t)nb * OZ_S * c1 * OZ_CHUNK * 2);
+    const size_t by = 0;
+    const size_t byr = align256((size_t)nb * OZ_S * c2 * OZ_CHUNK * 2);
+    nbg = (nbg + OZ_PART - 1) / OZ_PART * OZ_PART;           // whole parts per group
+    const size_t bc = align256((size_t)OZ_S * nbg * c1 * c2 * 4);
+    const int64_t nparts = (nb + OZ_PART - 1) / OZ_PART;
+    const size_t bp = align256((size_t)nparts * c1 * c2 * 8);
+    const size_t be = align256(sizeof(int) * (c1 + c2));
+    char* buf = nullptr;
+    CM_TRY(oz_scratch(ctx, bx + by + byr + bc + bp + be, &buf));
+    __nv_bfloat16* xs = (__nv_bfloat16*)buf;
+    __nv_bfloat16* ys = (__nv_bfloat16*)(buf + bx + by);      // reversed slice order (the B operand)
+    float* Cb = (float*)(buf + bx + by + byr);
+    double* Pp = (double*)(buf + bx + by + byr + bc);
+    int* ex = (int*)(buf + bx + by + byr + bc + bp);
+    int* ey = ex + c1;
+    ProfScope ps(CMSVD_PROF_GRAM, s, 8.0 * n * (same ? c1 : c1 + c2) + 8.0 * c1 * c2,
+                 2.0 * n * c1 * c2);
+    // the rows past n in the last chunk must be zero slices
+    if (n % OZ_CHUNK) {
+        const int64_t b = nb - 1;
+        CM_CUDA(cudaMemsetAsync(xs + b * (int64_t)OZ_S * c1 * OZ_CHUNK, 0, (size_t)OZ_S * c1 * OZ_CHUNK * 2, s));
+        CM_CUDA(cudaMemsetAsync(ys + b * (int64_t)OZ_S * c2 * OZ_CHUNK, 0, (size_t)OZ_S * c2 * OZ_CHUNK * 2, s));
+    }
+    CM_CUDA(cudaMemsetAsync(ex, 0x80, sizeof(int) * (c1 + c2), s));   // OZ_NONE, below any ilogb
+    const int grid = ctx->sm_count * 4;
+    k_oz_col_exp<<<grid, 256, 0, s>>>(X, ldx, n, c1, ex);
+    CM_LAUNCH();
+    k_oz_slice_gram<<<grid, 256, 0, s>>>(X, ldx, n, c1, ex, 0, xs);
+    CM_LAUNCH();
+    if (!same) {
+        k_oz_col_exp<<<grid, 256, 0, s>>>(Y, ldy, n, c2, ey);
+        CM_LAUNCH();
+    } else {
+        CM_CUDA(cudaMemcpyAsync(ey, ex, sizeof(int) * c1, cudaMemcpyDeviceToDevice, s));
+    }
+    k_oz_slice_gram<<<grid, 256, 0, s>>>(Y, ldy, n, c2, ey, 1, ys);
+    CM_LAUNCH();
+    const float one = 1.f, zero = 0.f;
+    for (int64_t b0 = 0; b0 < nb; b0 += nbg) {
+        const int64_t cnt = nb - b0 < nbg ? nb - b0 : nbg;
+        for (int lvl = 2; lvl <= OZ_S + 1; ++lvl) {
+            const int pairs = lvl - 1;                       // (p, q) = (1, lvl-1) .. (lvl-1, 1)
+            // A = X slices 0..pairs-1 of each chunk (c1 x pairs*128, column-major, ld c1);
+            // B = Y slices stored in reverse, the last `pairs` of each chunk (slices pairs-1 .. 0).
+            const __nv_bfloat16* A = xs + b0 * (int64_t)OZ_S * c1 * OZ_CHUNK;
+            const __nv_bfloat16* Bm = ys + b0 * (int64_t)OZ_S * c2 * OZ_CHUNK + (int64_t)(OZ_S - pairs) * c2 * OZ_CHUNK;
+            float* Cl = Cb + (int64_t)(lvl - 2) * cnt * c1 * c2;
+            CM_TRY(blas_ok(cublasGemmStridedBatchedEx(h, CUBLAS_OP_N, CUBLAS_OP_T, c1, c2, pairs * OZ_CHUNK, &one,
+                                                      A, CUDA_R_16BF, c1, (int64_t)OZ_S * c1 * OZ_CHUNK,
+                                                      Bm, CUDA_R_16BF, c2, (int64_t)OZ_S * c2 * OZ_CHUNK, &zero,
+                                                      Cl, CUDA_R_32F, c1, (int64_t)c1 * c2, (int)cnt,
+                                                      CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT),
+                           "cublasGemmStridedBatchedEx (Gram slices)"));
+        }
+        const int64_t ce = (int64_t)c1 * c2;
+        dim3 pg((unsigned)((ce + 255) / 256 < 64 ? (ce + 255) / 256 : 64), (unsigned)((cnt + OZ_PART - 1) / OZ_PART));
+        k_oz_gram_part<<<pg, 256, 0, s>>>(Cb, (int)cnt, ce, Pp + (b0 / OZ_PART) * ce);
+        CM_LAUNCH();
+    }
+    {
+        const int64_t ce = (int64_t)c1 * c2;
+        k_oz_gram_fin<<<(int)((ce + 255) / 256 < ctx->sm_count * 4 ? (ce + 255) / 256 : ctx->sm_count * 4), 256, 0, s>>>(
+            Pp, (int)nparts, c1, c2, ex, ey, G, ldg);
+        CM_LAUNCH();
+    }
+    return CMSVD_OK;
+}
+
+// Z (n x c2, ldz) = X (n x c1, ldx) W (c1 x c2, ldw).
+int gemm_ozaki(cmsvd_context* ctx, const double* X, int64_t ldx, const double* W, int64_t ldw, double* Z, int64_t ldz,
+               int64_t n, int c1, int c2) {
+    cudaStream_t s = ctx->s;
+    cublasHandle_t h;
+    CM_TRY(oz_handle(ctx, &h));
+    const int g = OZ_KMAX / c1 < 1 ? 1 : OZ_KMAX / c1;     // slice pairs per exact FP32 sum
+    // the GEMMs of every level (pairs split into runs of at most g) and their levels
+    OzLevels lv;
+    int ng = 0;
+    int p0s[64], nps[64];
+    for (int lvl = 2; lvl <= OZ_S + 1; ++lvl)
+        for (int p0 = 0; p0 < lvl - 1; p0 += g) {
+            lv.lvl[ng] = lvl;
+            lv.scale[ng] = ldexp(1.0, -OZ_BITS * lvl);
+            p0s[ng] = p0;
+            nps[ng] = (lvl - 1) - p0 < g ? (lvl - 1) - p0 : g;
+            ++ng;
+        }
+    // row blocks: the FP32 outputs of one block take at most 512 MB
+    int64_t nblk = (int64_t)((512ll << 20) / ((int64_t)ng * c2 * 4));
+    nblk = nblk / 256 * 256;
+    if (nblk < 256) nblk = 256;
+    if (nblk > n) nblk = n;
+    const size_t bx = align256((size_t)n * OZ_S * c1 * 2);
+    const size_t bw = align256((size_t)OZ_S * c1 * c2 * 2);
+    const size_t bc = align256((size_t)ng * nblk * c2 * 4);
+    const size_t be = align256(sizeof(int) * (n + c2));
+    char* buf = nullptr;
+    CM_TRY(oz_scratch(ctx, bx + bw + bc + be, &buf));
+    __nv_bfloat16* xs = (__nv_bfloat16*)buf;
+    __nv_bfloat16* ws = (__nv_bfloat16*)(buf + bx);
+    float* Cb = (float*)(buf + bx + bw);
+    int* ex = (int*)(buf + bx + bw + bc);
+    int* ew = ex + n;
+    ProfScope ps(CMSVD_PROF_GEMM, s, 8.0 * ((double)n * c1 + (double)c1 * c2 + (double)n * c2), 2.0 * n * c1 * c2);
+    CM_CUDA(cudaMemsetAsync(ew, 0x80, sizeof(int) * c2, s));
+    const int grid = ctx->sm_count * 4;
+    k_oz_row_exp<<<grid, 256, 0, s>>>(X, ldx, n, c1, ex);
+    CM_LAUNCH();
+    k_oz_slice_rows<<<grid, 256, 0, s>>>(X, ldx, n, c1, ex, xs);
+    CM_LAUNCH();
+    k_oz_col_exp<<<grid, 256, 0, s>>>(W, ldw, c1, c2, ew);
+    CM_LAUNCH();
+    k_oz_slice_w<<<grid, 256, 0, s>>>(W, ldw, c1, c2, ew, ws);
+    CM_LAUNCH();
+    const float one = 1.f, zero = 0.f;
+    for (int64_t r0 = 0; r0 < n; r0 += nblk) {
+        const int64_t nr = n - r0 < nblk ? n - r0 : nblk;
+        for (int gi = 0; gi < ng; ++gi) {
+            const int lvl = lv.lvl[gi], p0 = p0s[gi], np = nps[gi];
+            // X slices p0 .. p0+np-1 (rows p0 c1 .. of each column, ld S c1) against W slices
+            // lvl-2-p0 .. lvl-1-p0-np (reversed storage: contiguous, block S-1-q for slice q)
+            const __nv_bfloat16* Bm = xs + r0 * (int64_t)OZ_S * c1 + (int64_t)p0 * c1;
+            const int qhi = lvl - 2 - p0;                    // W slice paired with X slice p0
+            const __nv_bfloat16* A = ws + (int64_t)(OZ_S - 1 - qhi) * c2 * c1;
+            CM_TRY(blas_ok(cublasGemmEx(h, CUBLAS_OP_N, CUBLAS_OP_N, c2, (int)nr, np * c1, &one, A, CUDA_R_16BF, c2,
+                                        Bm, CUDA_R_16BF, OZ_S * c1, &zero, Cb + (int64_t)gi * nr * c2, CUDA_R_32F, c2,
+                                        CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT),
+                           "cublasGemmEx (product slices)"));
+        }
+        const int64_t cnt = nr * c2;
+        const int eg = (int)((cnt + 255) / 256 < ctx->sm_count * 8 ? (cnt + 255) / 256 : ctx->sm_count * 8);
+        k_oz_gemm_epi<<<eg, 256, 0, s>>>(Cb, ng, lv, nr, c2, ex + r0, ew, Z + r0 * ldz, ldz);
+        CM_LAUNCH();
+    }
+    return CMSVD_OK;
+}
+
+void ozaki_release(cmsvd_context* ctx) {
+    if (ctx->blas) cublasDestroy((cublasHandle_t)ctx->blas);
+    ctx->blas = nullptr;
+    if (ctx->oz_buf) cudaFree(ctx->oz_buf);
+    ctx->oz_buf = nullptr;
+    ctx->oz_bytes = 0;
+}
+
+}  // namespace cmsvd
