@@ -393,21 +393,6 @@ __global__ void __launch_bounds__(1024) k_jacobi(double* __restrict__ Xc, int ro
     }
 }
 
-// Sums three values over a 128-thread block (fixed order: deterministic).
-__device__ __forceinline__ void block_sum3_128(double& a, double& b, double& c, double (*sh)[4]) {
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
-        c += __shfl_xor_sync(0xffffffffu, c, o);
-    }
-    const int w = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) { sh[0][w] = a; sh[1][w] = b; sh[2][w] = c; }
-    __syncthreads();
-    a = (sh[0][0] + sh[0][1]) + (sh[0][2] + sh[0][3]);
-    b = (sh[1][0] + sh[1][1]) + (sh[1][2] + sh[1][3]);
-    c = (sh[2][0] + sh[2][1]) + (sh[2][2] + sh[2][3]);
-}
-
 // Grid barrier for cooperative launches (all CTAs co-resident: cudaLaunchCooperativeKernel
 // refuses otherwise). The last CTA to arrive resets the arrival count and advances the
 // generation word, which the others poll; polling a word that is written once per barrier,
@@ -442,129 +427,245 @@ __device__ __forceinline__ bool grid_barrier(unsigned* ctl, unsigned nblocks) {
 constexpr int JC_MAXDIM = 1024;             // L M <= 512; the dense direct solver factors n <= 1024
 
 // Cooperative form for 97..1024 columns: one CTA per pair of a round (round-robin ordering,
-// the pairs of a round are disjoint), all sweeps in one launch. Within a sweep the rounds are
-// ordered by data flow, not by a grid barrier: every column carries a version (the rounds
-// that have updated it, ver[]), and the CTA that owns a pair in round r waits only until both
-// of its columns have reached version r, rotates them, and publishes version r + 1. Each
-// column is updated once per round, by the owner of its pair, so these waits order every
-// read after the write it needs; a round then costs one L2 round trip of two flags instead
-// of a barrier over every CTA. One bounded grid barrier per sweep decides convergence (did
-// any CTA rotate). Columns whose squared norm is below negl (1e-36 ||Bm||_F^2) are treated
-// as zero. Each thread holds its rows of both columns and both V columns in registers.
-// GB300 runs an FP64 warp instruction in 16 clocks whatever its active lanes, so only warp 0
-// computes the rotation angle and shares it through shared memory. (Measured alternatives,
-// slower on this part: an 8-CTA thread-block cluster keeping column blocks in shared memory,
-// 25-36 ms per 256 x 256 SVD, FP64-bound on its 8 SMs; block-cyclic cooperative kernels with
-// 2 or 4 columns per block, 31 and 21 ms; this form with a grid barrier per round, 16 ms.)
+// the pairs of a round are disjoint), all sweeps in one launch. A column and its V column
+// travel between the CTAs that own them in consecutive rounds through a mailbox in L2 that
+// carries its own synchronization: every FP64 value is stored as two 8-byte words, each
+// holding 32 bits of the value and the 32-bit version of the column (the rounds that have
+// updated it). Naturally aligned 8-byte accesses are single-copy atomic, so a reader that
+// sees the expected version in both words of an element has that element's new value; the
+// owner of a pair in round r polls its two columns until every word carries version r,
+// rotates them, and stores them back with version r + 1 (the same layout as the low-latency
+// protocol of NCCL). A round then needs no memory fence and no separate flag: one
+// store-to-load trip through L2. Each column is read and written once per round, by the
+// owner of its pair, who is also its next writer, so one mailbox slot per column is
+// enough. One bounded grid barrier per sweep decides convergence (did any CTA rotate).
+// Columns whose squared norm is below negl (1e-36 ||Bm||_F^2) are treated as zero.
+// GB300 runs an FP64 warp instruction in 16 clocks whatever its active lanes, and a
+// dependent FP64 operation takes ~64 clocks (rsqrt ~440, sqrt and division ~650-700;
+// measured), so the three dot products are summed over the block with 6 FP64 additions a
+// warp, and only warp 0 computes the rotation (two reciprocal square roots, see below),
+// shared through shared memory. Per round that chain, not the wait for the partner
+// columns, is most of the time (measured on a 256 x 256 problem: 4.5 us a round with the
+// plain shuffle sums and a division-and-square-root angle, 4.4 us of it without the waits,
+// 1.3 us without the sums and the angle; 3.6 us as written). Exact 128-bit integer dot
+// products in block fixed point, tried in place of the FP64 sums, were 12% slower.
+// (Measured alternatives,
+// slower on this part: an 8-CTA thread-block cluster keeping column blocks in shared
+// memory, 25-36 ms per 256 x 256 SVD, FP64-bound on its 8 SMs; block-cyclic cooperative
+// kernels with 2 or 4 columns per block, 31 and 21 ms; this form with a grid barrier per
+// round, 16 ms; with per-column version counters and fences, 15 ms.)
 // Every wait is bounded: past the limit a CTA sets ctl[3] and every CTA leaves.
-// RPT: rows (and V entries) per thread, the smallest of 2, 4, 8 with 128 RPT >= rows, cols
-// (the FP64 FMAs of the dot products run on every register slot, so a larger RPT than
-// needed costs FP64 issue slots).
-__device__ __forceinline__ bool jc_wait_cols(const unsigned* ver, int p, int q, unsigned gen, unsigned* ctl) {
-    __shared__ int sh_fail;
-    if (threadIdx.x == 0) {
-        volatile const unsigned* vp = ver + p;
-        volatile const unsigned* vq = ver + q;
-        volatile unsigned* err = ctl + 3;
+// RPT: rows (and V entries) per thread, the smallest of 2, 4, 8 with 128 RPT >= rows, cols.
+// Mailbox column j: 128 RPT X elements, then 128 RPT V elements, 16 bytes each, at
+// mb + j 256 RPT.
+__host__ __device__ constexpr int jc_rpt(int mx) { return mx <= 256 ? 2 : mx <= 512 ? 4 : 8; }
+
+size_t jacobi_scratch_words(int dim) {
+    // 64 control words (ctl, one rotation word per sweep), then the mailbox (byte 256 on)
+    return 64 + (size_t)dim * 256 * jc_rpt(dim) * 4;
+}
+
+__device__ __forceinline__ ulonglong2 mb_ld(const ulonglong2* a) {
+    ulonglong2 r;
+    asm volatile("ld.volatile.global.v2.u64 {%0, %1}, [%2];" : "=l"(r.x), "=l"(r.y) : "l"(a) : "memory");
+    return r;
+}
+__device__ __forceinline__ void mb_st(ulonglong2* a, double v, unsigned ver) {
+    const unsigned long long f = (unsigned long long)ver << 32;
+    const unsigned long long hi = f | (unsigned)__double2hiint(v), lo = f | (unsigned)__double2loint(v);
+    asm volatile("st.volatile.global.v2.u64 [%0], {%1, %2};" ::"l"(a), "l"(hi), "l"(lo) : "memory");
+}
+__device__ __forceinline__ bool mb_is(ulonglong2 w, unsigned ver) {
+    return (unsigned)(w.x >> 32) == ver && (unsigned)(w.y >> 32) == ver;
+}
+__device__ __forceinline__ double mb_val(ulonglong2 w) { return __hiloint2double((int)(unsigned)w.x, (int)(unsigned)w.y); }
+
+// Polls this thread's elements of columns p (into a) and q (into b, when two) until all carry
+// version ver. Elements: slot u < RPT is X row threadIdx.x + 128 u, slot RPT + u the V entry.
+// For RPT = 8 the elements are polled in four batches (the registers in flight: 512 columns
+// need 4 co-resident CTAs per SM, 128 registers a thread).
+// Returns nonzero on timeout or when another CTA has set ctl[3].
+template <int RPT>
+__device__ __forceinline__ int mb_wait(const ulonglong2* cp, const ulonglong2* cq, bool two, int rows, int cols,
+                                       unsigned ver, const unsigned* ctl, double (&a)[2 * RPT], double (&b)[2 * RPT]) {
+    constexpr int SLOTS = 2 * RPT, BATCH = RPT >= 8 ? 4 : 2 * RPT;
+#pragma unroll
+    for (int s0 = 0; s0 < SLOTS; s0 += BATCH) {
         long long it = 0;
-        int fail = 0;
-        while ((*vp < gen || *vq < gen)) {
-            if (*err != 0) { fail = 1; break; }
-            if (++it > 20000000LL) { atomicExch(ctl + 3, 1u); fail = 1; break; }   // >= 0.8 s
-            if (it > 2048) __nanosleep(32);
+        for (;;) {
+            ulonglong2 wa[BATCH], wb[BATCH];
+#pragma unroll
+            for (int k = 0; k < BATCH; ++k) {
+                const int sl = s0 + k, u = sl < RPT ? sl : sl - RPT;
+                const int i = threadIdx.x + 128 * u, lim = sl < RPT ? rows : cols;
+                const int off = (sl < RPT ? 0 : 128 * RPT) + i;
+                if (i < lim) {
+                    wa[k] = mb_ld(cp + off);
+                    if (two) wb[k] = mb_ld(cq + off);
+                }
+            }
+            bool ok = true;
+#pragma unroll
+            for (int k = 0; k < BATCH; ++k) {
+                const int sl = s0 + k, u = sl < RPT ? sl : sl - RPT;
+                const int i = threadIdx.x + 128 * u, lim = sl < RPT ? rows : cols;
+                a[sl] = 0.0;
+                b[sl] = 0.0;
+                if (i < lim) {
+                    ok = ok && mb_is(wa[k], ver);
+                    a[sl] = mb_val(wa[k]);
+                    if (two) {
+                        ok = ok && mb_is(wb[k], ver);
+                        b[sl] = mb_val(wb[k]);
+                    }
+                }
+            }
+            if (ok) break;
+            if (++it > 2000000LL) return 1;   // about a second of L2 polls
+            if ((it & 1023) == 0 && *(volatile const unsigned*)(ctl + 3) != 0) return 1;
         }
-        __threadfence();   // the columns' data is read after their versions
-        sh_fail = fail;
     }
+    return 0;
+}
+
+// Sums three values over a 128-thread block with 6 FP64 additions a warp instead of 15: the
+// first two shuffle levels exchange halves of the value set, so lanes 0-7 go on with a, 8-15
+// with b, 16-23 with c; warp 0 then adds the four warps' totals. Fixed order: deterministic.
+// The sums are valid in warp 0 only.
+__device__ __forceinline__ void block_sum3_128_w0(double& a, double& b, double& c, double (*sh)[4]) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const bool h4 = lane & 16, h3 = lane & 8;
+    double k0 = h4 ? c : a, k1 = h4 ? 0.0 : b;
+    const double s0 = h4 ? a : c, s1 = h4 ? b : 0.0;
+    k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+    k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+    double v = h3 ? k1 : k0;
+    v += __shfl_xor_sync(0xffffffffu, h3 ? k0 : k1, 8);
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    if ((lane & 7) == 0 && lane < 24) sh[lane >> 3][w] = v;
     __syncthreads();
-    return sh_fail == 0;
+    if (w == 0) {
+        const int vi = lane < 3 ? lane : 0;
+        const double t = (sh[vi][0] + sh[vi][1]) + (sh[vi][2] + sh[vi][3]);
+        a = __shfl_sync(0xffffffffu, t, 0);
+        b = __shfl_sync(0xffffffffu, t, 1);
+        c = __shfl_sync(0xffffffffu, t, 2);
+    }
 }
 
 template <int RPT>
-__global__ void __launch_bounds__(128) k_jacobi_coop(double* __restrict__ Xc, double* __restrict__ V, int rows, int cols,
-                                                     int np, double tol, const double* __restrict__ fro2, int max_sweeps,
-                                                     unsigned* ctl, unsigned* rot, unsigned* ver) {
+__global__ void __launch_bounds__(128, RPT >= 8 ? 4 : 1) k_jacobi_coop(ulonglong2* __restrict__ mb, double* __restrict__ Xc,
+                                                     double* __restrict__ V, int rows, int cols, int np, double tol,
+                                                     const double* __restrict__ fro2, int max_sweeps, unsigned* ctl,
+                                                     unsigned* rot) {
+    constexpr int CS = 256 * RPT;   // mailbox column stride (elements)
     __shared__ double sh[3][4];
     __shared__ double sh_cs, sh_sn;
     __shared__ int sh_ok;
-    const double negl = 1e-36 * *fro2;
+    // the X columns are scaled by sc = 2^-e (exact) when first loaded, so that the scaled
+    // ||Bm||_F lies in [1/2, 1), and scaled back by 2^e when unpacked
+    const double f2 = *fro2;
+    int e2 = 0;
+    if (f2 > 0.0 && f2 <= 1.7e308) frexp(sqrt(f2), &e2);
+    const double sc = ldexp(1.0, -e2);
+    const double negl = 1e-36 * (f2 * sc * sc);
+    const double tol2 = tol * tol;
     const int k = blockIdx.x;
     int sweep = 0;
+    bool rotated = false;   // this CTA rotated in the current sweep (thread 0)
     for (; sweep < max_sweeps; ++sweep) {
         for (int round = 0; round < np - 1; ++round) {
-            const unsigned gen = (unsigned)(sweep * (np - 1) + round);
+            const unsigned ver = (unsigned)(sweep * (np - 1) + round);
             int p, q;
             if (k == 0) { p = round; q = np - 1; }
             else { p = (round + k) % (np - 1); q = (round - k + (np - 1)) % (np - 1); }
             if (p > q) { const int t = p; p = q; q = t; }
-            // a padding column (np = cols + 1) has no data: its partner only moves on
-            const int pw = p < cols ? p : q, qw = q < cols ? q : p;
-            if (!jc_wait_cols(ver, pw, qw, gen, ctl)) return;
-            if (p < cols && q < cols) {
-                double* xp = Xc + (size_t)p * rows;
-                double* xq = Xc + (size_t)q * rows;
-                double* vp = V + (size_t)p * cols;
-                double* vq = V + (size_t)q * cols;
-                double xa[RPT], xb[RPT], va[RPT], vb[RPT];
+            // p < cols always; q = cols is the padding column (odd cols), which has no data
+            const bool two = q < cols;
+            ulonglong2* cp = mb + (size_t)p * CS;
+            ulonglong2* cq = mb + (size_t)(two ? q : p) * CS;
+            double xa[2 * RPT], xb[2 * RPT];   // [0, RPT): X rows, [RPT, 2 RPT): V entries
+            const int fail = mb_wait<RPT>(cp, cq, two, rows, cols, ver, ctl, xa, xb);
+            if (ver == 0) {   // every column is in exactly one pair of the first round
 #pragma unroll
                 for (int u = 0; u < RPT; ++u) {
-                    const int i = threadIdx.x + 128 * u;
-                    xa[u] = i < rows ? __ldcg(xp + i) : 0.0;
-                    xb[u] = i < rows ? __ldcg(xq + i) : 0.0;
-                    va[u] = i < cols ? __ldcg(vp + i) : 0.0;
-                    vb[u] = i < cols ? __ldcg(vq + i) : 0.0;
+                    xa[u] *= sc;
+                    xb[u] *= sc;
                 }
-                double al = 0.0, be = 0.0, ga = 0.0;
+            }
+            if (__syncthreads_or(fail)) {
+                if (threadIdx.x == 0) atomicExch(ctl + 3, 1u);
+                return;
+            }
+            double cs = 1.0, sn = 0.0;
+            if (two) {
+                double dal = 0.0, dbe = 0.0, dga = 0.0;
 #pragma unroll
                 for (int u = 0; u < RPT; ++u) {
-                    al = __fma_rn(xa[u], xa[u], al);
-                    be = __fma_rn(xb[u], xb[u], be);
-                    ga = __fma_rn(xa[u], xb[u], ga);
+                    dal = __fma_rn(xa[u], xa[u], dal);
+                    dbe = __fma_rn(xb[u], xb[u], dbe);
+                    dga = __fma_rn(xa[u], xb[u], dga);
                 }
-                block_sum3_128(al, be, ga, sh);
+                block_sum3_128_w0(dal, dbe, dga, sh);
                 if (threadIdx.x < 32) {
-                    int ok = fabs(ga) > tol * sqrt(al * be) && al > negl && be > negl;
-                    double cs = 1.0, sn = 0.0;
-                    if (ok) {
-                        const double zeta = (be - al) / (2.0 * ga);
-                        const double tt = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-                        cs = 1.0 / sqrt(1.0 + tt * tt);
-                        sn = cs * tt;
-                    }
+                    // |ga| > tol sqrt(al be), without the square root (the columns are scaled so
+                    // that ||Bm||_F is in [1/2, 1): no overflow here)
+                    const int ok = dga * dga > tol2 * (dal * dbe) && dal > negl && dbe > negl;
+                    // The rotation that zeroes ga: cot(2 theta) = zeta = (be - al) / (2 ga), |theta| <= pi/4,
+                    // tan(theta) = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)). With h = sqrt(d^2 + 4 ga^2),
+                    // d = be - al: cos(2 theta) = |d| / h, sin(2 theta) = sign(zeta) 2 |ga| / h, and the
+                    // half-angle forms cos(theta) = sqrt((1 + cos 2 theta) / 2), sin(theta) =
+                    // sin(2 theta) / (2 cos theta) need two reciprocal square roots and no division,
+                    // a shorter chain of dependent FP64 operations than tan(theta) and 1 / sqrt(1 + t^2).
+                    // Computed unconditionally and selected by ok.
+                    const double d = dbe - dal, g2 = 2.0 * dga;
+                    const double sgn = (d == 0.0 || (d > 0.0) == (dga > 0.0)) ? 1.0 : -1.0;
+                    const double ri = rsqrt(__fma_rn(d, d, g2 * g2));
+                    const double c2 = fabs(d) * ri, s2 = sgn * fabs(g2) * ri;
+                    const double hc = __fma_rn(c2, 0.5, 0.5), w = rsqrt(hc);
+                    const double c = ok ? hc * w : 1.0, sg = ok ? 0.5 * s2 * w : 0.0;
                     if (threadIdx.x == 0) {
                         sh_ok = ok;
-                        sh_cs = cs;
-                        sh_sn = sn;
+                        sh_cs = c;
+                        sh_sn = sg;
+                        rotated = rotated || ok;
                     }
                 }
                 __syncthreads();
                 if (sh_ok) {
-                    const double cs = sh_cs, sn = sh_sn;
-#pragma unroll
-                    for (int u = 0; u < RPT; ++u) {
-                        const int i = threadIdx.x + 128 * u;
-                        if (i < rows) {
-                            __stcg(xp + i, cs * xa[u] - sn * xb[u]);
-                            __stcg(xq + i, sn * xa[u] + cs * xb[u]);
-                        }
-                        if (i < cols) {
-                            __stcg(vp + i, cs * va[u] - sn * vb[u]);
-                            __stcg(vq + i, sn * va[u] + cs * vb[u]);
-                        }
-                    }
-                    if (threadIdx.x == 0) atomicExch(rot + sweep, 1u);
+                    cs = sh_cs;
+                    sn = sh_sn;
                 }
             }
-            // publish: the columns' new data before their new versions
-            __threadfence();
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                if (p < cols) atomicExch(ver + p, gen + 1);
-                if (q < cols) atomicExch(ver + q, gen + 1);
+            // publish version ver + 1 (unchanged values when no rotation)
+#pragma unroll
+            for (int sl = 0; sl < 2 * RPT; ++sl) {
+                const int u = sl < RPT ? sl : sl - RPT;
+                const int i = threadIdx.x + 128 * u, lim = sl < RPT ? rows : cols;
+                if (i < lim) {
+                    const int off = (sl < RPT ? 0 : 128 * RPT) + i;
+                    if (two) {
+                        mb_st(cp + off, cs * xa[sl] - sn * xb[sl], ver + 1);
+                        mb_st(cq + off, sn * xa[sl] + cs * xb[sl], ver + 1);
+                    } else {
+                        mb_st(cp + off, xa[sl], ver + 1);
+                    }
+                }
             }
         }
+        if (threadIdx.x == 0 && rotated) atomicExch(rot + sweep, 1u);
+        rotated = false;
         if (!grid_barrier(ctl, gridDim.x)) return;   // every rotation of the sweep is counted
         if (*(volatile unsigned*)(rot + sweep) == 0) { ++sweep; break; }
+    }
+    // the barrier above ordered every final store before these loads
+    const double usc = ldexp(1.0, e2);
+    for (int j = k; j < cols; j += gridDim.x) {
+        const ulonglong2* c = mb + (size_t)j * CS;
+        for (int i = threadIdx.x; i < rows; i += 128) Xc[(size_t)j * rows + i] = usc * mb_val(mb_ld(c + i));
+        for (int i = threadIdx.x; i < cols; i += 128) V[(size_t)j * cols + i] = mb_val(mb_ld(c + 128 * RPT + i));
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) ctl[2] = sweep;
 }
@@ -593,17 +694,23 @@ __global__ void __launch_bounds__(1024) k_jacobi_finish(const double* __restrict
 // Rotates the columns of Bm (trans = 0; Bm V = Xc) or of Bm^T (trans = 1; Bm^T V = Xc,
 // so Bm = V diag(sv) (Xc / sv)^T: V holds the LEFT singular vectors of Bm). Applying
 // the method to the transpose of the R factors met here roughly halves the sweeps.
+// With a mailbox (mb != nullptr, the cooperative form) Xc and V are written there, version 0.
 __global__ void k_jacobi_init_t(const double* __restrict__ Bm, int brows, int bcols, int trans, double* __restrict__ Xc,
-                                double* __restrict__ V, double* __restrict__ fro2) {
+                                double* __restrict__ V, double* __restrict__ fro2, ulonglong2* __restrict__ mb, int rpt) {
     const int rows = trans ? bcols : brows, cols = trans ? brows : bcols;
     const int64_t nt = (int64_t)gridDim.x * blockDim.x;
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (int64_t e = t0; e < (int64_t)brows * bcols; e += nt) {
         const int i = (int)(e / bcols), j = (int)(e % bcols);     // Bm(i, j)
-        if (trans) Xc[(size_t)i * rows + j] = Bm[e];             // column i of Bm^T, row j
-        else Xc[(size_t)j * rows + i] = Bm[e];
+        const int c = trans ? i : j, r = trans ? j : i;          // column c, row r of the rotated matrix
+        if (mb) mb_st(mb + (size_t)c * 256 * rpt + r, Bm[e], 0u);
+        else Xc[(size_t)c * rows + r] = Bm[e];
     }
-    for (int64_t e = t0; e < (int64_t)cols * cols; e += nt) V[e] = (e / cols == e % cols) ? 1.0 : 0.0;
+    for (int64_t e = t0; e < (int64_t)cols * cols; e += nt) {
+        const double v = (e / cols == e % cols) ? 1.0 : 0.0;
+        if (mb) mb_st(mb + (size_t)(e / cols) * 256 * rpt + 128 * rpt + e % cols, v, 0u);
+        else V[e] = v;
+    }
     if (blockIdx.x == 0) {
         __shared__ double sh[32];
         double acc = 0.0;
@@ -624,9 +731,12 @@ int jacobi_svd(const double* Bm, int brows, int bcols, int trans, double* Xc, do
     cudaStream_t s = ctx->s;
     const int rows = trans ? bcols : brows, cols = trans ? brows : bcols;
     double* fro2 = (double*)(flag2 + 2);   // flag2: 16 bytes of scratch (int rotated, pad, double)
+    if (rows > JC_MAXDIM || cols > JC_MAXDIM) { set_error("Jacobi SVD supports at most %d rows and columns", JC_MAXDIM); return CMSVD_NOT_SUPPORTED; }
+    // jac_ctl: 64 control words, then the mailbox of the cooperative form (16-byte aligned)
+    ulonglong2* mb = cols > 96 ? reinterpret_cast<ulonglong2*>(jac_ctl + 64) : nullptr;
     {
         ProfScope ps(CMSVD_PROF_JACOBI, s, 16.0 * rows * cols + 8.0 * cols * cols, 0.0);
-        k_jacobi_init_t<<<64, 256, 0, s>>>(Bm, brows, bcols, trans, Xc, V, fro2);
+        k_jacobi_init_t<<<64, 256, 0, s>>>(Bm, brows, bcols, trans, Xc, V, fro2, mb, jc_rpt(rows > cols ? rows : cols));
         CM_LAUNCH();
     }
     const int np = (cols + 1) / 2 * 2;
@@ -637,14 +747,11 @@ int jacobi_svd(const double* Bm, int brows, int bcols, int trans, double* Xc, do
         CM_LAUNCH();
         return CMSVD_OK;
     }
-    // all sweeps in one launch; ctl (4 words), rot (one word per sweep) and the column versions
-    // (JC_MAXDIM words from word 64) live in jac_ctl
+    // all sweeps in one launch; ctl (4 words) and rot (one word per sweep) lead jac_ctl
     unsigned* ctl = jac_ctl;
     unsigned* rot = jac_ctl + 4;
-    unsigned* ver = jac_ctl + 64;
     const int max_sweeps = 40;
-    CM_CUDA(cudaMemsetAsync(ctl, 0, sizeof(unsigned) * (64 + JC_MAXDIM), s));
-    if (rows > JC_MAXDIM || cols > JC_MAXDIM) { set_error("Jacobi SVD supports at most %d rows and columns", JC_MAXDIM); return CMSVD_NOT_SUPPORTED; }
+    CM_CUDA(cudaMemsetAsync(ctl, 0, sizeof(unsigned) * 64, s));
     const int grid = np / 2;
     {
         const int mx = rows > cols ? rows : cols;
@@ -654,8 +761,8 @@ int jacobi_svd(const double* Bm, int brows, int bcols, int trans, double* Xc, do
         CM_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 128, 0));
         if (per_sm * ctx->sm_count < grid) { set_error("Jacobi grid of %d CTAs cannot be co-resident", grid); return CMSVD_NOT_SUPPORTED; }
         ProfScope ps(CMSVD_PROF_JACOBI, s, 0.0, 0.0, 1);
-        void* args[] = {&Xc, &V, (void*)&rows, (void*)&cols, (void*)&np, (void*)&tol, &fro2, (void*)&max_sweeps, &ctl, &rot,
-                        &ver};
+        void* args[] = {&mb, &Xc, &V, (void*)&rows, (void*)&cols, (void*)&np, (void*)&tol, &fro2, (void*)&max_sweeps, &ctl,
+                        &rot};
         CM_CUDA(cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(128), args, 0, s));
         note_launch();
     }
@@ -663,7 +770,7 @@ int jacobi_svd(const double* Bm, int brows, int bcols, int trans, double* Xc, do
     CM_CUDA(cudaMemcpyAsync(ctx->pinned, ctl, sizeof(unsigned) * 4, cudaMemcpyDeviceToHost, s));
     CM_CUDA(cudaStreamSynchronize(s));
     memcpy(h, ctx->pinned, sizeof(h));
-    if (h[3]) { set_error("Jacobi grid barrier timed out"); return CMSVD_CUDA_ERROR; }
+    if (h[3]) { set_error("Jacobi SVD: a wait between rounds timed out"); return CMSVD_CUDA_ERROR; }
     // account the work of the sweeps that ran
     {
         Profiler& pr = prof();

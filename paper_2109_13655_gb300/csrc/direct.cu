@@ -403,7 +403,7 @@ static void dense_alloc(DenseBufs& b, Arena& ws, int64_t m, int n, int L, int Mk
     b.part = ws.take<double>(b.pcap);
     b.perm = ws.take<int>(n);
     b.ints = ws.take<int>(16);
-    b.jctl = ws.take<unsigned>(64 + 1024);   // Jacobi control words and column versions
+    b.jctl = ws.take<unsigned>(jacobi_scratch_words(n));   // Jacobi control words and mailbox
 }
 
 size_t dense_workspace(const cmsvd_matrix* M, const cmsvd_params* p) {

@@ -317,7 +317,9 @@ int orth_qr(const double* X, int64_t ldx, int64_t n, int c, double* Q, double* R
 // left singular vectors of Bm. sv_j = ||Xc_j||, perm sorts sv descending.
 // flag2: 16 bytes of device scratch (8-byte aligned + 8).
 // tol > 0 overrides the rotation threshold max(1e-15, rows u) (loose sweeps for the deflation).
-// jac_ctl: 64 + 1024 device words of scratch for the cooperative sweeps.
+// jac_ctl: jacobi_scratch_words(d) device words, d >= both dimensions (256-byte aligned):
+// control words and the mailbox of the cooperative sweeps.
+size_t jacobi_scratch_words(int d);
 int jacobi_svd(const double* Bm, int brows, int bcols, int trans, double* Xc, double* V, double* sv, int* perm,
                int* flag2, cmsvd_context* ctx, double tol, unsigned* jac_ctl);
 

@@ -281,7 +281,7 @@ static void ritz_alloc(RitzBufs& b, Arena& ws, int64_t m, int64_t n, int c, int 
     b.permB = ws.take<int>(c);
     b.cand = ws.take<int>(c);
     b.ints = ws.take<int>(32);
-    b.jctl = ws.take<unsigned>(64 + 1024);   // Jacobi control words and column versions
+    b.jctl = ws.take<unsigned>(jacobi_scratch_words(c));   // Jacobi control words and mailbox
 }
 
 size_t ritz_workspace(int64_t m, int64_t n, int c, int sm_count) {
