@@ -30,6 +30,7 @@ constexpr int OZ_S = 8;          // slices
 constexpr int OZ_BITS = 7;       // bits per slice
 constexpr int OZ_KMAX = 1024;    // products per exact FP32 sum
 constexpr int OZ_CHUNK = 128;    // Gram: rows per chunk (8 stacked slices x 128 <= 1024)
+static_assert(OZ_S == 8 && OZ_BITS == 7, "the epilogues combine levels 2..5 and 6..9");
 
 // ----------------------------------------------------------------------------- scales
 // ilogb of the largest |x| of each column (cols of an n x c row-major block) / each row.
@@ -132,22 +133,36 @@ __global__ void k_oz_slice_w(const double* __restrict__ W, int64_t ldw, int c1, 
 }
 
 // ----------------------------------------------------------------------------- epilogues
+// The FP32 slice-GEMM outputs are exact integers below 2^24 in magnitude. The epilogues add
+// them in integer arithmetic (FP32 -> int32 conversions and integer adds run off the FP64
+// pipe, which GB300 issues at 2 lanes per clock per SM) and convert once: the levels 2..5 and
+// 6..9 are combined into two int64 sums on the scales 2^-35 and 2^-63,
+//   th = sum_{k=2..5} s_k 2^(7 (5 - k)),   tl = sum_{k=6..9} s_k 2^(7 (9 - k)),
+// each below 2^53 in magnitude for level sums |s_k| < 2^28, so that
+// sum_k s_k 2^(-7 k) = th 2^-35 + tl 2^-63 is formed by one FMA of two exact doubles with a
+// single rounding.
+__device__ __forceinline__ double oz_combine(long long th, long long tl) {
+    return __fma_rn((double)th, 0x1p-35, (double)tl * 0x1p-63);
+}
+
 // Gram, pass 1: P[part][j + k c1] = sum_lvl 2^(-7 lvl) sum_{b in part} C[lvl][b][j + k c1] over a
-// part of OZ_PART chunks of the current group (blockIdx.y); the FP32 chunk sums are exact
-// integers and are added in FP64.
+// part of OZ_PART chunks of the current group (blockIdx.y); a level sum over a part is below
+// 16 2^24 = 2^28.
 constexpr int OZ_PART = 16;
 __global__ void k_oz_gram_part(const float* __restrict__ C, int nb, int64_t cnt, double* __restrict__ P) {
     const int part = blockIdx.y;
     const int b0 = part * OZ_PART, b1 = b0 + OZ_PART < nb ? b0 + OZ_PART : nb;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * blockDim.x) {
-        double v = 0.0;
+        long long th = 0, tl = 0;
+#pragma unroll
         for (int lvl = 2; lvl <= OZ_S + 1; ++lvl) {
             const float* Cl = C + (int64_t)(lvl - 2) * nb * cnt;
-            double s = 0.0;
-            for (int b = b0; b < b1; ++b) s += (double)Cl[(int64_t)b * cnt + e];
-            v = __fma_rn(s, ldexp(1.0, -OZ_BITS * lvl), v);   // exact scaling by a power of two
+            int sk = 0;
+            for (int b = b0; b < b1; ++b) sk += __float2int_rz(__ldcs(Cl + (int64_t)b * cnt + e));
+            if (lvl <= 5) th += (long long)sk << (OZ_BITS * (5 - lvl));
+            else tl += (long long)sk << (OZ_BITS * (9 - lvl));
         }
-        P[(int64_t)part * cnt + e] = v;
+        P[(int64_t)part * cnt + e] = oz_combine(th, tl);
     }
 }
 
@@ -163,18 +178,23 @@ __global__ void k_oz_gram_fin(const double* __restrict__ P, int nparts, int c1, 
     }
 }
 
-// Product: Z[i][l] = sum_g 2^(ex_i + 1 + fw_l + 1 - 7 lvl_g) C[g][l + i c2] over the ng GEMM
-// outputs of a row block (exact FP32 integers), summed in FP64 and written once.
-struct OzLevels { int lvl[64]; double scale[64]; };   // level of each GEMM output and 2^(-7 level)
+// Product: Z[i][l] = 2^(ex_i + 1 + fw_l + 1) sum_g 2^(-7 lvl_g) C[g][l + i c2] over the ng GEMM
+// outputs of a row block (a level has at most 8 outputs: |s_k| < 2^27), written once.
+struct OzLevels { int lvl[64]; };   // level of each GEMM output
 __global__ void k_oz_gemm_epi(const float* __restrict__ C, int ng, OzLevels lv, int64_t n, int c2,
                               const int* __restrict__ ex, const int* __restrict__ ew, double* __restrict__ Z, int64_t ldz) {
     const int64_t cnt = n * c2;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * blockDim.x) {
         const int64_t i = e / c2;
         const int l = (int)(e % c2);
-        double v = 0.0;
-        for (int g = 0; g < ng; ++g) v = __fma_rn((double)C[(int64_t)g * cnt + e], lv.scale[g], v);
-        Z[i * ldz + l] = ldexp(v, oz_shift(ex[i]) + oz_shift(ew[l]));
+        long long th = 0, tl = 0;
+        for (int g = 0; g < ng; ++g) {
+            const int lvl = lv.lvl[g];
+            const long long sk = __float2int_rz(__ldcs(C + (int64_t)g * cnt + e));
+            if (lvl <= 5) th += sk << (OZ_BITS * (5 - lvl));
+            else tl += sk << (OZ_BITS * (9 - lvl));
+        }
+        Z[i * ldz + l] = ldexp(oz_combine(th, tl), oz_shift(ex[i]) + oz_shift(ew[l]));
     }
 }
 
@@ -313,7 +333,6 @@ int gemm_ozaki(cmsvd_context* ctx, const double* X, int64_t ldx, const double* W
     for (int lvl = 2; lvl <= OZ_S + 1; ++lvl)
         for (int p0 = 0; p0 < lvl - 1; p0 += g) {
             lv.lvl[ng] = lvl;
-            lv.scale[ng] = ldexp(1.0, -OZ_BITS * lvl);
             p0s[ng] = p0;
             nps[ng] = (lvl - 1) - p0 < g ? (lvl - 1) - p0 : g;
             ++ng;
