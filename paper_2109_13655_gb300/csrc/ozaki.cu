@@ -9,9 +9,10 @@
 // column (product). A slice value d is an integer below 128, so it is exact in bf16, every product
 // of two slices is an integer below 2^14, and any sum of at most 1024 such products is an integer
 // below 2^24: the FP32 accumulation of the tensor cores is then exact whatever its order. The
-// products of one level k = p + q share the scale 2^(-7k), so up to 1024 / K products of a level
-// are stacked along the contraction and formed by one GEMM. The level sums are added into the
-// FP64 result, scaled by 2^(e_i + f_j - 7k), in FP64. Pairs with p + q > S + 1 are dropped: per
+// Gram forms one GEMM output per slice pair and block of 1024 rows (a batched GEMM over the
+// blocks with K = 1024); the product stacks up to 1024 / c1 slice pairs of a level along the
+// contraction. The exact outputs are added per level k = p + q (scale 2^(-7k)) in integer
+// arithmetic and the level sums combined into the FP64 result, scaled by 2^(e_i + f_j). Pairs with p + q > S + 1 are dropped: per
 // product their sum is below 2^-53 of 2^(e_i + f_j). With the truncation of the operands to 56
 // bits below their scales, each emulated product is within a few 2^-53 of 2^(e_i + f_j), that is
 // of the products of the largest entries sharing the scales: FP64 accuracy for operands whose
@@ -29,7 +30,8 @@ namespace cmsvd {
 constexpr int OZ_S = 8;          // slices
 constexpr int OZ_BITS = 7;       // bits per slice
 constexpr int OZ_KMAX = 1024;    // products per exact FP32 sum
-constexpr int OZ_CHUNK = 128;    // Gram: rows per chunk (8 stacked slices x 128 <= 1024)
+constexpr int OZ_CHUNK = 1024;   // Gram: rows per block (one slice pair of a block: 1024 products)
+constexpr int OZ_PAIRS = 36;     // slice pairs (p, q), p + q <= S + 1 (levels 2..9)
 static_assert(OZ_S == 8 && OZ_BITS == 7, "the epilogues combine levels 2..5 and 6..9");
 
 // ----------------------------------------------------------------------------- scales
@@ -82,22 +84,24 @@ __device__ __forceinline__ void oz_slices(double x, int e, float (&d)[OZ_S]) {
     for (int p = 0; p < OZ_S; ++p) d[p] = sg * (float)((V >> (OZ_BITS * (OZ_S - 1 - p))) & 127ull);
 }
 
-// Gram operand: X (n x c row-major) -> per chunk b of 128 rows, S slices of c x 128 column-major
-// (ld c), slice p at block position p (rev = 0) or S-1-p (rev = 1).
+// Gram operand: X (n x c row-major) -> per block b of OZ_CHUNK rows, S slices of c x OZ_CHUNK
+// column-major (ld c), slice p at block position p in fw and at position S-1-p in rv (either
+// may be null). One CTA row at a time (threads over columns).
 __global__ void k_oz_slice_gram(const double* __restrict__ X, int64_t ld, int64_t n, int c, const int* __restrict__ ex,
-                                int rev, __nv_bfloat16* __restrict__ out) {
-    const int64_t total = n * c;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = e / c;
-        const int j = (int)(e % c);
-        float d[OZ_S];
-        oz_slices(X[i * ld + j], oz_e(ex[j]), d);
+                                __nv_bfloat16* __restrict__ fw, __nv_bfloat16* __restrict__ rv) {
+    const int64_t bs = (int64_t)OZ_S * c * OZ_CHUNK, ss = (int64_t)c * OZ_CHUNK;
+    for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
         const int64_t b = i / OZ_CHUNK, il = i % OZ_CHUNK;
-        __nv_bfloat16* blk = out + b * (int64_t)OZ_S * c * OZ_CHUNK;
+        for (int j = threadIdx.x; j < c; j += blockDim.x) {
+            float d[OZ_S];
+            oz_slices(X[i * ld + j], oz_e(ex[j]), d);
+            const int64_t o = b * bs + il * c + j;
 #pragma unroll
-        for (int p = 0; p < OZ_S; ++p) {
-            const int pos = rev ? OZ_S - 1 - p : p;
-            blk[(int64_t)pos * c * OZ_CHUNK + il * c + j] = __float2bfloat16_rn(d[p]);
+            for (int p = 0; p < OZ_S; ++p) {
+                const __nv_bfloat16 v = __float2bfloat16_rn(d[p]);
+                if (fw) fw[o + p * ss] = v;
+                if (rv) rv[o + (OZ_S - 1 - p) * ss] = v;
+            }
         }
     }
 }
@@ -145,10 +149,10 @@ __device__ __forceinline__ double oz_combine(long long th, long long tl) {
     return __fma_rn((double)th, 0x1p-35, (double)tl * 0x1p-63);
 }
 
-// Gram, pass 1: P[part][j + k c1] = sum_lvl 2^(-7 lvl) sum_{b in part} C[lvl][b][j + k c1] over a
-// part of OZ_PART chunks of the current group (blockIdx.y); a level sum over a part is below
-// 16 2^24 = 2^28.
-constexpr int OZ_PART = 16;
+// Gram, pass 1: P[part][j + k c1] = sum_lvl 2^(-7 lvl) sum_{pairs of lvl} sum_{b in part}
+// C[pair][b][j + k c1] over a part of OZ_PART blocks of the current group (blockIdx.y); a level
+// sum over a part has at most 8 x 8 terms below 2^24: |s_k| < 2^30.
+constexpr int OZ_PART = 8;
 __global__ void k_oz_gram_part(const float* __restrict__ C, int nb, int64_t cnt, double* __restrict__ P) {
     const int part = blockIdx.y;
     const int b0 = part * OZ_PART, b1 = b0 + OZ_PART < nb ? b0 + OZ_PART : nb;
@@ -156,11 +160,13 @@ __global__ void k_oz_gram_part(const float* __restrict__ C, int nb, int64_t cnt,
         long long th = 0, tl = 0;
 #pragma unroll
         for (int lvl = 2; lvl <= OZ_S + 1; ++lvl) {
-            const float* Cl = C + (int64_t)(lvl - 2) * nb * cnt;
-            int sk = 0;
-            for (int b = b0; b < b1; ++b) sk += __float2int_rz(__ldcs(Cl + (int64_t)b * cnt + e));
-            if (lvl <= 5) th += (long long)sk << (OZ_BITS * (5 - lvl));
-            else tl += (long long)sk << (OZ_BITS * (9 - lvl));
+            long long sk = 0;
+            for (int t = 0; t < lvl - 1; ++t) {
+                const float* Cp = C + (int64_t)((lvl - 2) * (lvl - 1) / 2 + t) * nb * cnt;
+                for (int b = b0; b < b1; ++b) sk += __float2int_rz(__ldcs(Cp + (int64_t)b * cnt + e));
+            }
+            if (lvl <= 5) th += sk << (OZ_BITS * (5 - lvl));
+            else tl += sk << (OZ_BITS * (9 - lvl));
         }
         P[(int64_t)part * cnt + e] = oz_combine(th, tl);
     }
@@ -246,76 +252,75 @@ int gram_ozaki(cmsvd_context* ctx, const double* X, int64_t ldx, int c1, const d
     CM_TRY(oz_handle(ctx, &h));
     const int64_t nb = (n + OZ_CHUNK - 1) / OZ_CHUNK;
     const bool same = X == Y && c1 == c2 && ldx == ldy;
-    // chunk results of all levels of a group of chunks: at most 256 MB of FP32 at a time
-    int64_t nbg = (int64_t)((256ll << 20) / ((int64_t)c1 * c2 * 4 * OZ_S));
-    if (nbg < 1) nbg = 1;
+    const int64_t ce = (int64_t)c1 * c2;
+    // GEMM outputs of a group of blocks: about 1 GB of FP32 at a time, whole parts per group
+    int64_t nbg = (int64_t)((1ll << 30) / (OZ_PAIRS * ce * 4)) / OZ_PART * OZ_PART;
+    if (nbg < OZ_PART) nbg = OZ_PART;
     if (nbg > nb) nbg = nb;
+    const int64_t ngroups = (nb + nbg - 1) / nbg, ppg = (nbg + OZ_PART - 1) / OZ_PART, nparts = ngroups * ppg;
     const size_t bx = align256((size_t)nb * OZ_S * c1 * OZ_CHUNK * 2);
-    const size_t by = 0;
     const size_t byr = align256((size_t)nb * OZ_S * c2 * OZ_CHUNK * 2);
-    nbg = (nbg + OZ_PART - 1) / OZ_PART * OZ_PART;           // whole parts per group
-    const size_t bc = align256((size_t)OZ_S * nbg * c1 * c2 * 4);
-    const int64_t nparts = (nb + OZ_PART - 1) / OZ_PART;
-    const size_t bp = align256((size_t)nparts * c1 * c2 * 8);
+    const size_t bc = align256((size_t)OZ_PAIRS * nbg * ce * 4);
+    const size_t bp = align256((size_t)nparts * ce * 8);
     const size_t be = align256(sizeof(int) * (c1 + c2));
     char* buf = nullptr;
-    CM_TRY(oz_scratch(ctx, bx + by + byr + bc + bp + be, &buf));
+    CM_TRY(oz_scratch(ctx, bx + byr + bc + bp + be, &buf));
     __nv_bfloat16* xs = (__nv_bfloat16*)buf;
-    __nv_bfloat16* ys = (__nv_bfloat16*)(buf + bx + by);      // reversed slice order (the B operand)
-    float* Cb = (float*)(buf + bx + by + byr);
-    double* Pp = (double*)(buf + bx + by + byr + bc);
-    int* ex = (int*)(buf + bx + by + byr + bc + bp);
+    __nv_bfloat16* ys = (__nv_bfloat16*)(buf + bx);      // reversed slice order (the B operand)
+    float* Cb = (float*)(buf + bx + byr);
+    double* Pp = (double*)(buf + bx + byr + bc);
+    int* ex = (int*)(buf + bx + byr + bc + bp);
     int* ey = ex + c1;
     ProfScope ps(CMSVD_PROF_GRAM, s, 8.0 * n * (same ? c1 : c1 + c2) + 8.0 * c1 * c2,
                  2.0 * n * c1 * c2);
-    // the rows past n in the last chunk must be zero slices
+    // the rows past n in the last block must be zero slices; parts of a short last group stay 0
     if (n % OZ_CHUNK) {
         const int64_t b = nb - 1;
         CM_CUDA(cudaMemsetAsync(xs + b * (int64_t)OZ_S * c1 * OZ_CHUNK, 0, (size_t)OZ_S * c1 * OZ_CHUNK * 2, s));
         CM_CUDA(cudaMemsetAsync(ys + b * (int64_t)OZ_S * c2 * OZ_CHUNK, 0, (size_t)OZ_S * c2 * OZ_CHUNK * 2, s));
     }
+    CM_CUDA(cudaMemsetAsync(Pp, 0, (size_t)nparts * ce * 8, s));
     CM_CUDA(cudaMemsetAsync(ex, 0x80, sizeof(int) * (c1 + c2), s));   // OZ_NONE, below any ilogb
     const int grid = ctx->sm_count * 4;
     k_oz_col_exp<<<grid, 256, 0, s>>>(X, ldx, n, c1, ex);
     CM_LAUNCH();
-    k_oz_slice_gram<<<grid, 256, 0, s>>>(X, ldx, n, c1, ex, 0, xs);
-    CM_LAUNCH();
-    if (!same) {
-        k_oz_col_exp<<<grid, 256, 0, s>>>(Y, ldy, n, c2, ey);
+    if (same) {
+        CM_CUDA(cudaMemcpyAsync(ey, ex, sizeof(int) * c1, cudaMemcpyDeviceToDevice, s));
+        k_oz_slice_gram<<<ctx->sm_count * 8, 256, 0, s>>>(X, ldx, n, c1, ex, xs, ys);
         CM_LAUNCH();
     } else {
-        CM_CUDA(cudaMemcpyAsync(ey, ex, sizeof(int) * c1, cudaMemcpyDeviceToDevice, s));
+        k_oz_col_exp<<<grid, 256, 0, s>>>(Y, ldy, n, c2, ey);
+        CM_LAUNCH();
+        k_oz_slice_gram<<<ctx->sm_count * 8, 256, 0, s>>>(X, ldx, n, c1, ex, xs, nullptr);
+        CM_LAUNCH();
+        k_oz_slice_gram<<<ctx->sm_count * 8, 256, 0, s>>>(Y, ldy, n, c2, ey, nullptr, ys);
+        CM_LAUNCH();
     }
-    k_oz_slice_gram<<<grid, 256, 0, s>>>(Y, ldy, n, c2, ey, 1, ys);
-    CM_LAUNCH();
     const float one = 1.f, zero = 0.f;
-    for (int64_t b0 = 0; b0 < nb; b0 += nbg) {
-        const int64_t cnt = nb - b0 < nbg ? nb - b0 : nbg;
+    for (int64_t g = 0; g < ngroups; ++g) {
+        const int64_t b0 = g * nbg, cnt = nb - b0 < nbg ? nb - b0 : nbg;
         for (int lvl = 2; lvl <= OZ_S + 1; ++lvl) {
-            const int pairs = lvl - 1;                       // (p, q) = (1, lvl-1) .. (lvl-1, 1)
-            // A = X slices 0..pairs-1 of each chunk (c1 x pairs*128, column-major, ld c1);
-            // B = Y slices stored in reverse, the last `pairs` of each chunk (slices pairs-1 .. 0).
-            const __nv_bfloat16* A = xs + b0 * (int64_t)OZ_S * c1 * OZ_CHUNK;
-            const __nv_bfloat16* Bm = ys + b0 * (int64_t)OZ_S * c2 * OZ_CHUNK + (int64_t)(OZ_S - pairs) * c2 * OZ_CHUNK;
-            float* Cl = Cb + (int64_t)(lvl - 2) * cnt * c1 * c2;
-            CM_TRY(blas_ok(cublasGemmStridedBatchedEx(h, CUBLAS_OP_N, CUBLAS_OP_T, c1, c2, pairs * OZ_CHUNK, &one,
-                                                      A, CUDA_R_16BF, c1, (int64_t)OZ_S * c1 * OZ_CHUNK,
-                                                      Bm, CUDA_R_16BF, c2, (int64_t)OZ_S * c2 * OZ_CHUNK, &zero,
-                                                      Cl, CUDA_R_32F, c1, (int64_t)c1 * c2, (int)cnt,
-                                                      CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT),
-                           "cublasGemmStridedBatchedEx (Gram slices)"));
+            const int pairs = lvl - 1;
+            for (int t = 0; t < pairs; ++t) {
+                // X slice t against Y slice pairs-1-t (reversed storage: block position S-pairs+t)
+                const int pi = (lvl - 2) * (lvl - 1) / 2 + t;
+                const __nv_bfloat16* A = xs + (b0 * OZ_S + t) * (int64_t)c1 * OZ_CHUNK;
+                const __nv_bfloat16* Bm = ys + (b0 * OZ_S + OZ_S - pairs + t) * (int64_t)c2 * OZ_CHUNK;
+                CM_TRY(blas_ok(cublasGemmStridedBatchedEx(h, CUBLAS_OP_N, CUBLAS_OP_T, c1, c2, OZ_CHUNK, &one,
+                                                          A, CUDA_R_16BF, c1, (int64_t)OZ_S * c1 * OZ_CHUNK,
+                                                          Bm, CUDA_R_16BF, c2, (int64_t)OZ_S * c2 * OZ_CHUNK, &zero,
+                                                          Cb + (int64_t)pi * cnt * ce, CUDA_R_32F, c1, ce, (int)cnt,
+                                                          CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT),
+                               "cublasGemmStridedBatchedEx (Gram slices)"));
+            }
         }
-        const int64_t ce = (int64_t)c1 * c2;
         dim3 pg((unsigned)((ce + 255) / 256 < 64 ? (ce + 255) / 256 : 64), (unsigned)((cnt + OZ_PART - 1) / OZ_PART));
-        k_oz_gram_part<<<pg, 256, 0, s>>>(Cb, (int)cnt, ce, Pp + (b0 / OZ_PART) * ce);
+        k_oz_gram_part<<<pg, 256, 0, s>>>(Cb, (int)cnt, ce, Pp + g * ppg * ce);
         CM_LAUNCH();
     }
-    {
-        const int64_t ce = (int64_t)c1 * c2;
-        k_oz_gram_fin<<<(int)((ce + 255) / 256 < ctx->sm_count * 4 ? (ce + 255) / 256 : ctx->sm_count * 4), 256, 0, s>>>(
-            Pp, (int)nparts, c1, c2, ex, ey, G, ldg);
-        CM_LAUNCH();
-    }
+    k_oz_gram_fin<<<(int)((ce + 255) / 256 < ctx->sm_count * 4 ? (ce + 255) / 256 : ctx->sm_count * 4), 256, 0, s>>>(
+        Pp, (int)nparts, c1, c2, ex, ey, G, ldg);
+    CM_LAUNCH();
     return CMSVD_OK;
 }
 
