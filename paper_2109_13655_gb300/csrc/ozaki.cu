@@ -84,18 +84,23 @@ __device__ __forceinline__ void oz_slices(double x, int e, float (&d)[OZ_S]) {
     for (int p = 0; p < OZ_S; ++p) d[p] = sg * (float)((V >> (OZ_BITS * (OZ_S - 1 - p))) & 127ull);
 }
 
-// Gram operand: X (n x c row-major) -> per block b of OZ_CHUNK rows, S slices of c x OZ_CHUNK
-// column-major (ld c), slice p at block position p in fw and at position S-1-p in rv (either
-// may be null). One CTA row at a time (threads over columns).
-__global__ void k_oz_slice_gram(const double* __restrict__ X, int64_t ld, int64_t n, int c, const int* __restrict__ ex,
-                                __nv_bfloat16* __restrict__ fw, __nv_bfloat16* __restrict__ rv) {
-    const int64_t bs = (int64_t)OZ_S * c * OZ_CHUNK, ss = (int64_t)c * OZ_CHUNK;
+// Gram operand: X (n x c row-major) -> per block b of OZ_CHUNK rows, S slices of cp x OZ_CHUNK
+// column-major (ld cp, cp = c rounded up to 8: the pad entries are zero, and the GEMMs see
+// 16-byte aligned operands), slice p at block position p in fw and at position S-1-p in rv
+// (either may be null). One CTA row at a time (threads over columns).
+__global__ void k_oz_slice_gram(const double* __restrict__ X, int64_t ld, int64_t n, int c, int cp,
+                                const int* __restrict__ ex, __nv_bfloat16* __restrict__ fw, __nv_bfloat16* __restrict__ rv) {
+    const int64_t bs = (int64_t)OZ_S * cp * OZ_CHUNK, ss = (int64_t)cp * OZ_CHUNK;
     for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
         const int64_t b = i / OZ_CHUNK, il = i % OZ_CHUNK;
-        for (int j = threadIdx.x; j < c; j += blockDim.x) {
+        for (int j = threadIdx.x; j < cp; j += blockDim.x) {
             float d[OZ_S];
-            oz_slices(X[i * ld + j], oz_e(ex[j]), d);
-            const int64_t o = b * bs + il * c + j;
+            if (j < c) oz_slices(X[i * ld + j], oz_e(ex[j]), d);
+            else {
+#pragma unroll
+                for (int p = 0; p < OZ_S; ++p) d[p] = 0.f;
+            }
+            const int64_t o = b * bs + il * cp + j;
 #pragma unroll
             for (int p = 0; p < OZ_S; ++p) {
                 const __nv_bfloat16 v = __float2bfloat16_rn(d[p]);
@@ -106,33 +111,42 @@ __global__ void k_oz_slice_gram(const double* __restrict__ X, int64_t ld, int64_
     }
 }
 
-// Product operands. X (n x c1, row-major, row scale): column-major (S c1) x n, ld S c1, slice p of
-// row i at rows p c1 .. p c1 + c1 - 1 of column i. W (c1 x c2, row-major, column scale):
-// S column-major c2 x c1 blocks (ld c2), slice q at block S-1-q (reversed).
-__global__ void k_oz_slice_rows(const double* __restrict__ X, int64_t ld, int64_t n, int c1, const int* __restrict__ ex,
-                                __nv_bfloat16* __restrict__ out) {
-    const int64_t total = n * c1;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = e / c1;
-        const int j = (int)(e % c1);
-        float d[OZ_S];
-        oz_slices(X[i * ld + j], oz_e(ex[i]), d);
-        __nv_bfloat16* col = out + i * (int64_t)OZ_S * c1;
+// Product operands (c1p, c2p: c1, c2 rounded up to 8, pads zero). X (n x c1, row-major, row
+// scale): column-major (S c1p) x n, ld S c1p, slice p of row i at rows p c1p .. p c1p + c1 - 1 of
+// column i (one CTA row at a time). W (c1 x c2, row-major, column scale): S column-major
+// c2p x c1p blocks (ld c2p), slice q at block S-1-q (reversed).
+__global__ void k_oz_slice_rows(const double* __restrict__ X, int64_t ld, int64_t n, int c1, int c1p,
+                                const int* __restrict__ ex, __nv_bfloat16* __restrict__ out) {
+    for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+        __nv_bfloat16* col = out + i * (int64_t)OZ_S * c1p;
+        const int e = oz_e(ex[i]);
+        for (int j = threadIdx.x; j < c1p; j += blockDim.x) {
+            float d[OZ_S];
+            if (j < c1) oz_slices(X[i * ld + j], e, d);
+            else {
 #pragma unroll
-        for (int p = 0; p < OZ_S; ++p) col[(int64_t)p * c1 + j] = __float2bfloat16_rn(d[p]);
+                for (int p = 0; p < OZ_S; ++p) d[p] = 0.f;
+            }
+#pragma unroll
+            for (int p = 0; p < OZ_S; ++p) col[(int64_t)p * c1p + j] = __float2bfloat16_rn(d[p]);
+        }
     }
 }
 
-__global__ void k_oz_slice_w(const double* __restrict__ W, int64_t ldw, int c1, int c2, const int* __restrict__ ex,
-                             __nv_bfloat16* __restrict__ out) {
-    const int64_t total = (int64_t)c1 * c2;
+__global__ void k_oz_slice_w(const double* __restrict__ W, int64_t ldw, int c1, int c2, int c1p, int c2p,
+                             const int* __restrict__ ex, __nv_bfloat16* __restrict__ out) {
+    const int64_t total = (int64_t)c1p * c2p;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int k = (int)(e / c2), l = (int)(e % c2);
+        const int k = (int)(e / c2p), l = (int)(e % c2p);
         float d[OZ_S];
-        oz_slices(W[(int64_t)k * ldw + l], oz_e(ex[l]), d);
+        if (k < c1 && l < c2) oz_slices(W[(int64_t)k * ldw + l], oz_e(ex[l]), d);
+        else {
+#pragma unroll
+            for (int q = 0; q < OZ_S; ++q) d[q] = 0.f;
+        }
 #pragma unroll
         for (int q = 0; q < OZ_S; ++q)
-            out[(int64_t)(OZ_S - 1 - q) * c2 * c1 + (int64_t)k * c2 + l] = __float2bfloat16_rn(d[q]);
+            out[(int64_t)(OZ_S - 1 - q) * c2p * c1p + (int64_t)k * c2p + l] = __float2bfloat16_rn(d[q]);
     }
 }
 
@@ -172,35 +186,37 @@ __global__ void k_oz_gram_part(const float* __restrict__ C, int nb, int64_t cnt,
     }
 }
 
-// Gram, pass 2: G[j][k] = 2^(ex_j + 1 + ey_k + 1) sum_part P[part][j + k c1], parts in order.
-__global__ void k_oz_gram_fin(const double* __restrict__ P, int nparts, int c1, int c2, const int* __restrict__ ex,
-                              const int* __restrict__ ey, double* __restrict__ G, int64_t ldg) {
+// Gram, pass 2: G[j][k] = 2^(ex_j + 1 + ey_k + 1) sum_part P[part][j + k c1p], parts in order.
+__global__ void k_oz_gram_fin(const double* __restrict__ P, int nparts, int c1, int c2, int c1p, int64_t cep,
+                              const int* __restrict__ ex, const int* __restrict__ ey, double* __restrict__ G, int64_t ldg) {
     const int64_t cnt = (int64_t)c1 * c2;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * blockDim.x) {
         const int j = (int)(e % c1), k = (int)(e / c1);
         double v = 0.0;
-        for (int q = 0; q < nparts; ++q) v += P[(int64_t)q * cnt + e];
+        for (int q = 0; q < nparts; ++q) v += P[(int64_t)q * cep + j + (int64_t)k * c1p];
         G[(int64_t)j * ldg + k] = ldexp(v, oz_shift(ex[j]) + oz_shift(ey[k]));
     }
 }
 
-// Product: Z[i][l] = 2^(ex_i + 1 + fw_l + 1) sum_g 2^(-7 lvl_g) C[g][l + i c2] over the ng GEMM
-// outputs of a row block (a level has at most 8 outputs: |s_k| < 2^27), written once.
+// Product: Z[i][l] = 2^(ex_i + 1 + fw_l + 1) sum_g 2^(-7 lvl_g) C[g][l + i c2p] over the ng GEMM
+// outputs of a row block (a level has at most 8 outputs: |s_k| < 2^27), written once. One CTA
+// row at a time.
 struct OzLevels { int lvl[64]; };   // level of each GEMM output
-__global__ void k_oz_gemm_epi(const float* __restrict__ C, int ng, OzLevels lv, int64_t n, int c2,
+__global__ void k_oz_gemm_epi(const float* __restrict__ C, int ng, OzLevels lv, int64_t n, int c2, int c2p,
                               const int* __restrict__ ex, const int* __restrict__ ew, double* __restrict__ Z, int64_t ldz) {
-    const int64_t cnt = n * c2;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = e / c2;
-        const int l = (int)(e % c2);
-        long long th = 0, tl = 0;
-        for (int g = 0; g < ng; ++g) {
-            const int lvl = lv.lvl[g];
-            const long long sk = __float2int_rz(__ldcs(C + (int64_t)g * cnt + e));
-            if (lvl <= 5) th += sk << (OZ_BITS * (5 - lvl));
-            else tl += sk << (OZ_BITS * (9 - lvl));
+    const int64_t gs = n * c2p;
+    for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+        const int si = oz_shift(ex[i]);
+        for (int l = threadIdx.x; l < c2; l += blockDim.x) {
+            long long th = 0, tl = 0;
+            for (int g = 0; g < ng; ++g) {
+                const int lvl = lv.lvl[g];
+                const long long sk = __float2int_rz(__ldcs(C + (int64_t)g * gs + i * c2p + l));
+                if (lvl <= 5) th += sk << (OZ_BITS * (5 - lvl));
+                else tl += sk << (OZ_BITS * (9 - lvl));
+            }
+            Z[i * ldz + l] = ldexp(oz_combine(th, tl), si + oz_shift(ew[l]));
         }
-        Z[i * ldz + l] = ldexp(oz_combine(th, tl), oz_shift(ex[i]) + oz_shift(ew[l]));
     }
 }
 
@@ -252,14 +268,15 @@ int gram_ozaki(cmsvd_context* ctx, const double* X, int64_t ldx, int c1, const d
     CM_TRY(oz_handle(ctx, &h));
     const int64_t nb = (n + OZ_CHUNK - 1) / OZ_CHUNK;
     const bool same = X == Y && c1 == c2 && ldx == ldy;
-    const int64_t ce = (int64_t)c1 * c2;
+    const int c1p = (c1 + 7) / 8 * 8, c2p = (c2 + 7) / 8 * 8;
+    const int64_t ce = (int64_t)c1p * c2p;   // GEMM outputs, padded
     // GEMM outputs of a group of blocks: about 1 GB of FP32 at a time, whole parts per group
     int64_t nbg = (int64_t)((1ll << 30) / (OZ_PAIRS * ce * 4)) / OZ_PART * OZ_PART;
     if (nbg < OZ_PART) nbg = OZ_PART;
     if (nbg > nb) nbg = nb;
     const int64_t ngroups = (nb + nbg - 1) / nbg, ppg = (nbg + OZ_PART - 1) / OZ_PART, nparts = ngroups * ppg;
-    const size_t bx = align256((size_t)nb * OZ_S * c1 * OZ_CHUNK * 2);
-    const size_t byr = align256((size_t)nb * OZ_S * c2 * OZ_CHUNK * 2);
+    const size_t bx = align256((size_t)nb * OZ_S * c1p * OZ_CHUNK * 2);
+    const size_t byr = align256((size_t)nb * OZ_S * c2p * OZ_CHUNK * 2);
     const size_t bc = align256((size_t)OZ_PAIRS * nbg * ce * 4);
     const size_t bp = align256((size_t)nparts * ce * 8);
     const size_t be = align256(sizeof(int) * (c1 + c2));
@@ -276,8 +293,8 @@ int gram_ozaki(cmsvd_context* ctx, const double* X, int64_t ldx, int c1, const d
     // the rows past n in the last block must be zero slices; parts of a short last group stay 0
     if (n % OZ_CHUNK) {
         const int64_t b = nb - 1;
-        CM_CUDA(cudaMemsetAsync(xs + b * (int64_t)OZ_S * c1 * OZ_CHUNK, 0, (size_t)OZ_S * c1 * OZ_CHUNK * 2, s));
-        CM_CUDA(cudaMemsetAsync(ys + b * (int64_t)OZ_S * c2 * OZ_CHUNK, 0, (size_t)OZ_S * c2 * OZ_CHUNK * 2, s));
+        CM_CUDA(cudaMemsetAsync(xs + b * (int64_t)OZ_S * c1p * OZ_CHUNK, 0, (size_t)OZ_S * c1p * OZ_CHUNK * 2, s));
+        CM_CUDA(cudaMemsetAsync(ys + b * (int64_t)OZ_S * c2p * OZ_CHUNK, 0, (size_t)OZ_S * c2p * OZ_CHUNK * 2, s));
     }
     CM_CUDA(cudaMemsetAsync(Pp, 0, (size_t)nparts * ce * 8, s));
     CM_CUDA(cudaMemsetAsync(ex, 0x80, sizeof(int) * (c1 + c2), s));   // OZ_NONE, below any ilogb
@@ -286,14 +303,14 @@ int gram_ozaki(cmsvd_context* ctx, const double* X, int64_t ldx, int c1, const d
     CM_LAUNCH();
     if (same) {
         CM_CUDA(cudaMemcpyAsync(ey, ex, sizeof(int) * c1, cudaMemcpyDeviceToDevice, s));
-        k_oz_slice_gram<<<ctx->sm_count * 8, 256, 0, s>>>(X, ldx, n, c1, ex, xs, ys);
+        k_oz_slice_gram<<<ctx->sm_count * 8, 256, 0, s>>>(X, ldx, n, c1, c1p, ex, xs, ys);
         CM_LAUNCH();
     } else {
         k_oz_col_exp<<<grid, 256, 0, s>>>(Y, ldy, n, c2, ey);
         CM_LAUNCH();
-        k_oz_slice_gram<<<ctx->sm_count * 8, 256, 0, s>>>(X, ldx, n, c1, ex, xs, nullptr);
+        k_oz_slice_gram<<<ctx->sm_count * 8, 256, 0, s>>>(X, ldx, n, c1, c1p, ex, xs, nullptr);
         CM_LAUNCH();
-        k_oz_slice_gram<<<ctx->sm_count * 8, 256, 0, s>>>(Y, ldy, n, c2, ey, nullptr, ys);
+        k_oz_slice_gram<<<ctx->sm_count * 8, 256, 0, s>>>(Y, ldy, n, c2, c2p, ey, nullptr, ys);
         CM_LAUNCH();
     }
     const float one = 1.f, zero = 0.f;
@@ -304,12 +321,12 @@ int gram_ozaki(cmsvd_context* ctx, const double* X, int64_t ldx, int c1, const d
             for (int t = 0; t < pairs; ++t) {
                 // X slice t against Y slice pairs-1-t (reversed storage: block position S-pairs+t)
                 const int pi = (lvl - 2) * (lvl - 1) / 2 + t;
-                const __nv_bfloat16* A = xs + (b0 * OZ_S + t) * (int64_t)c1 * OZ_CHUNK;
-                const __nv_bfloat16* Bm = ys + (b0 * OZ_S + OZ_S - pairs + t) * (int64_t)c2 * OZ_CHUNK;
-                CM_TRY(blas_ok(cublasGemmStridedBatchedEx(h, CUBLAS_OP_N, CUBLAS_OP_T, c1, c2, OZ_CHUNK, &one,
-                                                          A, CUDA_R_16BF, c1, (int64_t)OZ_S * c1 * OZ_CHUNK,
-                                                          Bm, CUDA_R_16BF, c2, (int64_t)OZ_S * c2 * OZ_CHUNK, &zero,
-                                                          Cb + (int64_t)pi * cnt * ce, CUDA_R_32F, c1, ce, (int)cnt,
+                const __nv_bfloat16* A = xs + (b0 * OZ_S + t) * (int64_t)c1p * OZ_CHUNK;
+                const __nv_bfloat16* Bm = ys + (b0 * OZ_S + OZ_S - pairs + t) * (int64_t)c2p * OZ_CHUNK;
+                CM_TRY(blas_ok(cublasGemmStridedBatchedEx(h, CUBLAS_OP_N, CUBLAS_OP_T, c1p, c2p, OZ_CHUNK, &one,
+                                                          A, CUDA_R_16BF, c1p, (int64_t)OZ_S * c1p * OZ_CHUNK,
+                                                          Bm, CUDA_R_16BF, c2p, (int64_t)OZ_S * c2p * OZ_CHUNK, &zero,
+                                                          Cb + (int64_t)pi * cnt * ce, CUDA_R_32F, c1p, ce, (int)cnt,
                                                           CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT),
                                "cublasGemmStridedBatchedEx (Gram slices)"));
             }
@@ -319,7 +336,7 @@ int gram_ozaki(cmsvd_context* ctx, const double* X, int64_t ldx, int c1, const d
         CM_LAUNCH();
     }
     k_oz_gram_fin<<<(int)((ce + 255) / 256 < ctx->sm_count * 4 ? (ce + 255) / 256 : ctx->sm_count * 4), 256, 0, s>>>(
-        Pp, (int)nparts, c1, c2, ex, ey, G, ldg);
+        Pp, (int)nparts, c1, c2, c1p, ce, ex, ey, G, ldg);
     CM_LAUNCH();
     return CMSVD_OK;
 }
@@ -330,7 +347,8 @@ int gemm_ozaki(cmsvd_context* ctx, const double* X, int64_t ldx, const double* W
     cudaStream_t s = ctx->s;
     cublasHandle_t h;
     CM_TRY(oz_handle(ctx, &h));
-    const int g = OZ_KMAX / c1 < 1 ? 1 : OZ_KMAX / c1;     // slice pairs per exact FP32 sum
+    const int c1p = (c1 + 7) / 8 * 8, c2p = (c2 + 7) / 8 * 8;   // padded: 16-byte aligned GEMM operands
+    const int g = OZ_KMAX / c1p < 1 ? 1 : OZ_KMAX / c1p;     // slice pairs per exact FP32 sum
     // the GEMMs of every level (pairs split into runs of at most g) and their levels
     OzLevels lv;
     int ng = 0;
@@ -343,13 +361,13 @@ int gemm_ozaki(cmsvd_context* ctx, const double* X, int64_t ldx, const double* W
             ++ng;
         }
     // row blocks: the FP32 outputs of one block take at most 512 MB
-    int64_t nblk = (int64_t)((512ll << 20) / ((int64_t)ng * c2 * 4));
+    int64_t nblk = (int64_t)((512ll << 20) / ((int64_t)ng * c2p * 4));
     nblk = nblk / 256 * 256;
     if (nblk < 256) nblk = 256;
     if (nblk > n) nblk = n;
-    const size_t bx = align256((size_t)n * OZ_S * c1 * 2);
-    const size_t bw = align256((size_t)OZ_S * c1 * c2 * 2);
-    const size_t bc = align256((size_t)ng * nblk * c2 * 4);
+    const size_t bx = align256((size_t)n * OZ_S * c1p * 2);
+    const size_t bw = align256((size_t)OZ_S * c1p * c2p * 2);
+    const size_t bc = align256((size_t)ng * nblk * c2p * 4);
     const size_t be = align256(sizeof(int) * (n + c2));
     char* buf = nullptr;
     CM_TRY(oz_scratch(ctx, bx + bw + bc + be, &buf));
@@ -363,30 +381,28 @@ int gemm_ozaki(cmsvd_context* ctx, const double* X, int64_t ldx, const double* W
     const int grid = ctx->sm_count * 4;
     k_oz_row_exp<<<grid, 256, 0, s>>>(X, ldx, n, c1, ex);
     CM_LAUNCH();
-    k_oz_slice_rows<<<grid, 256, 0, s>>>(X, ldx, n, c1, ex, xs);
+    k_oz_slice_rows<<<ctx->sm_count * 8, 256, 0, s>>>(X, ldx, n, c1, c1p, ex, xs);
     CM_LAUNCH();
     k_oz_col_exp<<<grid, 256, 0, s>>>(W, ldw, c1, c2, ew);
     CM_LAUNCH();
-    k_oz_slice_w<<<grid, 256, 0, s>>>(W, ldw, c1, c2, ew, ws);
+    k_oz_slice_w<<<grid, 256, 0, s>>>(W, ldw, c1, c2, c1p, c2p, ew, ws);
     CM_LAUNCH();
     const float one = 1.f, zero = 0.f;
     for (int64_t r0 = 0; r0 < n; r0 += nblk) {
         const int64_t nr = n - r0 < nblk ? n - r0 : nblk;
         for (int gi = 0; gi < ng; ++gi) {
             const int lvl = lv.lvl[gi], p0 = p0s[gi], np = nps[gi];
-            // X slices p0 .. p0+np-1 (rows p0 c1 .. of each column, ld S c1) against W slices
+            // X slices p0 .. p0+np-1 (rows p0 c1p .. of each column, ld S c1p) against W slices
             // lvl-2-p0 .. lvl-1-p0-np (reversed storage: contiguous, block S-1-q for slice q)
-            const __nv_bfloat16* Bm = xs + r0 * (int64_t)OZ_S * c1 + (int64_t)p0 * c1;
+            const __nv_bfloat16* Bm = xs + r0 * (int64_t)OZ_S * c1p + (int64_t)p0 * c1p;
             const int qhi = lvl - 2 - p0;                    // W slice paired with X slice p0
-            const __nv_bfloat16* A = ws + (int64_t)(OZ_S - 1 - qhi) * c2 * c1;
-            CM_TRY(blas_ok(cublasGemmEx(h, CUBLAS_OP_N, CUBLAS_OP_N, c2, (int)nr, np * c1, &one, A, CUDA_R_16BF, c2,
-                                        Bm, CUDA_R_16BF, OZ_S * c1, &zero, Cb + (int64_t)gi * nr * c2, CUDA_R_32F, c2,
+            const __nv_bfloat16* A = ws + (int64_t)(OZ_S - 1 - qhi) * c2p * c1p;
+            CM_TRY(blas_ok(cublasGemmEx(h, CUBLAS_OP_N, CUBLAS_OP_N, c2p, (int)nr, np * c1p, &one, A, CUDA_R_16BF, c2p,
+                                        Bm, CUDA_R_16BF, OZ_S * c1p, &zero, Cb + (int64_t)gi * nr * c2p, CUDA_R_32F, c2p,
                                         CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT),
                            "cublasGemmEx (product slices)"));
         }
-        const int64_t cnt = nr * c2;
-        const int eg = (int)((cnt + 255) / 256 < ctx->sm_count * 8 ? (cnt + 255) / 256 : ctx->sm_count * 8);
-        k_oz_gemm_epi<<<eg, 256, 0, s>>>(Cb, ng, lv, nr, c2, ex + r0, ew, Z + r0 * ldz, ldz);
+        k_oz_gemm_epi<<<ctx->sm_count * 8, 256, 0, s>>>(Cb, ng, lv, nr, c2, c2p, ex + r0, ew, Z + r0 * ldz, ldz);
         CM_LAUNCH();
     }
     return CMSVD_OK;
