@@ -291,13 +291,18 @@ __global__ void __launch_bounds__(1024) k_chol(const double* __restrict__ G, int
 
 // Ri = R^{-1} for upper-triangular R (row-major): one 128-thread CTA per column j,
 // back substitution x_i = -(sum_{k=i+1..j} R_ik x_k) / R_ii with a block reduction per i.
+// The reciprocals of the diagonal are formed first, in parallel (an FP64 division is ~650
+// clocks of latency on GB300; the substitution then multiplies).
 __global__ void __launch_bounds__(128) k_trinv(const double* __restrict__ R, int c, double* __restrict__ Ri) {
     __shared__ double x[1024];
+    __shared__ double rinv[1024];
     __shared__ double sh[4];
     const int j = blockIdx.x, t = threadIdx.x;
     if (j >= c) return;
     for (int i = t; i < c; i += 128) Ri[(size_t)i * c + j] = 0.0;
-    if (t == 0) x[j] = 1.0 / R[(size_t)j * c + j];
+    for (int i = t; i <= j; i += 128) rinv[i] = 1.0 / R[(size_t)i * c + i];
+    __syncthreads();
+    if (t == 0) x[j] = rinv[j];
     __syncthreads();
     for (int i = j - 1; i >= 0; --i) {
         double s = 0.0;
@@ -305,13 +310,14 @@ __global__ void __launch_bounds__(128) k_trinv(const double* __restrict__ R, int
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if ((t & 31) == 0) sh[t >> 5] = s;
         __syncthreads();
-        if (t == 0) x[i] = -((sh[0] + sh[1]) + (sh[2] + sh[3])) / R[(size_t)i * c + i];
+        if (t == 0) x[i] = -((sh[0] + sh[1]) + (sh[2] + sh[3])) * rinv[i];
         __syncthreads();
     }
     for (int i = t; i <= j; i += 128) Ri[(size_t)i * c + j] = x[i];
 }
 
 // ----------------------------------------------------------------------------- one-sided Jacobi SVD
+constexpr int JC_MAXDIM = 1024;             // L M <= 512; the dense direct solver factors n <= 1024
 // The cols columns (length rows) of Bm (rows x cols, row-major) are copied to Xc
 // (column-major) and rotated pairwise until mutually orthogonal (Hestenes):
 // Bm V = Xc, so sv_j = ||Xc_j|| are the singular values (zero when cols > rows),
@@ -382,14 +388,17 @@ __global__ void __launch_bounds__(1024) k_jacobi(double* __restrict__ Xc, int ro
         if (lane == 0) sv[j] = sqrt(s2);
     }
     __syncthreads();
-    if (t == 0) {
-        for (int i = 0; i < cols; ++i) perm[i] = i;
-        for (int i = 1; i < cols; ++i) {
-            const int key = perm[i];
-            int j = i - 1;
-            while (j >= 0 && sv[perm[j]] < sv[key]) { perm[j + 1] = perm[j]; --j; }
-            perm[j + 1] = key;
-        }
+    // perm: descending sv, ties by index (a stable sort), each position found by counting. A
+    // nonnegative double orders like its bit pattern, so the comparisons are integer ones (a
+    // serial insertion sort with FP64 compares took ~1 ms at 256 columns on GB300).
+    __shared__ long long key[JC_MAXDIM];
+    for (int i = t; i < cols; i += blockDim.x) key[i] = __double_as_longlong(sv[i]);
+    __syncthreads();
+    for (int i = t; i < cols; i += blockDim.x) {
+        const long long ki = key[i];
+        int r = 0;
+        for (int j = 0; j < cols; ++j) r += key[j] > ki || (key[j] == ki && j < i);
+        perm[r] = i;
     }
 }
 
@@ -424,7 +433,6 @@ __device__ __forceinline__ bool grid_barrier(unsigned* ctl, unsigned nblocks) {
     return *(volatile unsigned*)(ctl + 3) == 0;
 }
 
-constexpr int JC_MAXDIM = 1024;             // L M <= 512; the dense direct solver factors n <= 1024
 
 // Cooperative form for 97..1024 columns: one CTA per pair of a round (round-robin ordering,
 // the pairs of a round are disjoint), all sweeps in one launch. A column and its V column
@@ -680,14 +688,17 @@ __global__ void __launch_bounds__(1024) k_jacobi_finish(const double* __restrict
         if (lane == 0) sv[j] = sqrt(s2);
     }
     __syncthreads();
-    if (t == 0) {
-        for (int i = 0; i < cols; ++i) perm[i] = i;
-        for (int i = 1; i < cols; ++i) {
-            const int key = perm[i];
-            int j = i - 1;
-            while (j >= 0 && sv[perm[j]] < sv[key]) { perm[j + 1] = perm[j]; --j; }
-            perm[j + 1] = key;
-        }
+    // perm: descending sv, ties by index (a stable sort), each position found by counting. A
+    // nonnegative double orders like its bit pattern, so the comparisons are integer ones (a
+    // serial insertion sort with FP64 compares took ~1 ms at 256 columns on GB300).
+    __shared__ long long key[JC_MAXDIM];
+    for (int i = t; i < cols; i += blockDim.x) key[i] = __double_as_longlong(sv[i]);
+    __syncthreads();
+    for (int i = t; i < cols; i += blockDim.x) {
+        const long long ki = key[i];
+        int r = 0;
+        for (int j = 0; j < cols; ++j) r += key[j] > ki || (key[j] == ki && j < i);
+        perm[r] = i;
     }
 }
 
@@ -817,7 +828,7 @@ __global__ void __launch_bounds__(256) k_chol_coop(const double* __restrict__ G,
     for (int k0 = 0; k0 < c; k0 += CB) {
         const int b = min(CB, c - k0), w = c - k0 - b;
         if (blockIdx.x == 0) {   // diagonal block, right-looking in place
-            __shared__ double sh_piv;
+            __shared__ double sh_rpiv;
             for (int kk = k0; kk < k0 + b; ++kk) {
                 if (t == 0) {
                     double p = R[(size_t)kk * c + kk];
@@ -827,11 +838,11 @@ __global__ void __launch_bounds__(256) k_chol_coop(const double* __restrict__ G,
                     }
                     p = sqrt(p);
                     R[(size_t)kk * c + kk] = p;
-                    sh_piv = p;
+                    sh_rpiv = 1.0 / p;
                 }
                 __syncthreads();
-                const double piv = sh_piv;
-                for (int j = kk + 1 + t; j < k0 + b; j += blockDim.x) R[(size_t)kk * c + j] /= piv;
+                const double rpiv = sh_rpiv;
+                for (int j = kk + 1 + t; j < k0 + b; j += blockDim.x) R[(size_t)kk * c + j] *= rpiv;
                 __syncthreads();
                 const int wb = k0 + b - kk - 1;
                 for (int e = t; e < wb * wb; e += blockDim.x) {
@@ -843,13 +854,19 @@ __global__ void __launch_bounds__(256) k_chol_coop(const double* __restrict__ G,
         }
         if (!grid_barrier(ctl, gridDim.x)) return;
         if (w == 0) break;
-        // panel row: column j of R12 solves R11^T x = A12(:, j) (forward substitution)
-        for (int64_t jj = gtid; jj < w; jj += gthreads) {
-            const int j = k0 + b + (int)jj;
-            for (int i = k0; i < k0 + b; ++i) {
-                double acc = R[(size_t)i * c + j];
-                for (int q = k0; q < i; ++q) acc = __fma_rn(-R[(size_t)q * c + i], R[(size_t)q * c + j], acc);
-                R[(size_t)i * c + j] = acc / R[(size_t)i * c + i];
+        // panel row: column j of R12 solves R11^T x = A12(:, j) (forward substitution, with the
+        // reciprocals of the panel's diagonal formed once per CTA)
+        {
+            __shared__ double rdiag[CB];
+            for (int i = t; i < b; i += blockDim.x) rdiag[i] = 1.0 / R[(size_t)(k0 + i) * c + k0 + i];
+            __syncthreads();
+            for (int64_t jj = gtid; jj < w; jj += gthreads) {
+                const int j = k0 + b + (int)jj;
+                for (int i = k0; i < k0 + b; ++i) {
+                    double acc = R[(size_t)i * c + j];
+                    for (int q = k0; q < i; ++q) acc = __fma_rn(-R[(size_t)q * c + i], R[(size_t)q * c + j], acc);
+                    R[(size_t)i * c + j] = acc * rdiag[i - k0];
+                }
             }
         }
         if (!grid_barrier(ctl, gridDim.x)) return;
@@ -878,9 +895,9 @@ __global__ void __launch_bounds__(1024) k_pchol_deflate(const double* __restrict
                                                         double* __restrict__ W, double* __restrict__ L,
                                                         double* __restrict__ R3, int* __restrict__ cp_out) {
     __shared__ int perm[512];
-    __shared__ double rv[32];
+    __shared__ long long rv[32];
     __shared__ int ri[32];
-    __shared__ double sh_d0, sh_piv;
+    __shared__ double sh_d0, sh_piv, sh_lkk, sh_rl;
     __shared__ int sh_j;
     const int t = threadIdx.x, nt = blockDim.x, lane = t & 31, warp = t >> 5, nw = nt >> 5;
     for (int e = t; e < c * c; e += nt) {
@@ -892,27 +909,33 @@ __global__ void __launch_bounds__(1024) k_pchol_deflate(const double* __restrict
     int k = 0;
     for (; k <= c; ++k) {
         // argmax of the remaining diagonal (k == 0 also gives max diag(G))
-        double best = -1.0;
+        // (on the bit patterns: a positive double orders like its bits, a negative one below
+        // every positive; FP64 compares cost 16 clocks a warp instruction on GB300)
+        long long best = LLONG_MIN;
         int bi = c;
         for (int i = k + t; i < c; i += nt) {
-            const double d = W[(size_t)i * c + i];
+            const long long d = __double_as_longlong(W[(size_t)i * c + i]);
             if (d > best) { best = d; bi = i; }
         }
         for (int o = 16; o > 0; o >>= 1) {
-            const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+            const long long ov = __shfl_xor_sync(0xffffffffu, best, o);
             const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
             if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
         }
         if (lane == 0) { rv[warp] = best; ri[warp] = bi; }
         __syncthreads();
         if (t == 0) {
-            double bv = rv[0];
+            long long bv = rv[0];
             int bj = ri[0];
             for (int w = 1; w < nw; ++w)
                 if (rv[w] > bv || (rv[w] == bv && ri[w] < bj)) { bv = rv[w]; bj = ri[w]; }
-            if (k == 0) sh_d0 = bv;
-            sh_piv = bv;
+            const double dv = bj < c ? __longlong_as_double(bv) : -1.0;
+            if (k == 0) sh_d0 = dv;
+            sh_piv = dv;
             sh_j = bj;
+            const double l = sqrt(dv);
+            sh_lkk = l;
+            sh_rl = 1.0 / l;
         }
         __syncthreads();
         const int j = sh_j;
@@ -942,8 +965,8 @@ __global__ void __launch_bounds__(1024) k_pchol_deflate(const double* __restrict
             }
             __syncthreads();
         }
-        const double lkk = sqrt(d);
-        for (int i = k + t; i < c; i += nt) L[(size_t)i * c + k] = i == k ? lkk : W[(size_t)k * c + i] / lkk;
+        const double lkk = sh_lkk, rl = sh_rl;
+        for (int i = k + t; i < c; i += nt) L[(size_t)i * c + k] = i == k ? lkk : W[(size_t)k * c + i] * rl;
         __syncthreads();
         const int w = c - k - 1;
         for (int e = t; e < w * w; e += nt) {

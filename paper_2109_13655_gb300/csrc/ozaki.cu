@@ -35,13 +35,18 @@ constexpr int OZ_PAIRS = 36;     // slice pairs (p, q), p + q <= S + 1 (levels 2
 static_assert(OZ_S == 8 && OZ_BITS == 7, "the epilogues combine levels 2..5 and 6..9");
 
 // ----------------------------------------------------------------------------- scales
-// ilogb of the largest |x| of each column (cols of an n x c row-major block) / each row.
+// ilogb of the largest |x| of each column (cols of an n x c row-major block) / each row, from the
+// exponent field (integer work: a subnormal counts as 2^-1023, an upper bound of its ilogb,
+// which the slicing accepts as a scale).
+__device__ __forceinline__ int oz_ilogb(double v) {
+    return (int)((__double_as_longlong(v) >> 52) & 0x7ff) - 1023;
+}
 __global__ void k_oz_col_exp(const double* __restrict__ X, int64_t ld, int64_t n, int c, int* __restrict__ ex) {
     for (int j = threadIdx.x; j < c; j += blockDim.x) {
         int best = INT_MIN;
         for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
             const double v = X[i * ld + j];
-            if (v != 0.0) best = max(best, ilogb(v));
+            if ((__double_as_longlong(v) << 1) != 0) best = max(best, oz_ilogb(v));
         }
         if (best != INT_MIN) atomicMax(ex + j, best);
     }
@@ -54,7 +59,7 @@ __global__ void k_oz_row_exp(const double* __restrict__ X, int64_t ld, int64_t n
         int best = INT_MIN;
         for (int j = lane; j < c; j += 32) {
             const double v = X[i * ld + j];
-            if (v != 0.0) best = max(best, ilogb(v));
+            if ((__double_as_longlong(v) << 1) != 0) best = max(best, oz_ilogb(v));
         }
         for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(0xffffffffu, best, o));
         if (lane == 0) ex[i] = best;
@@ -78,10 +83,10 @@ __device__ __forceinline__ void oz_slices(double x, int e, float (&d)[OZ_S]) {
     // |x| = m 2^(Ee-1075); scale 2^(e+1): V = floor(|x| 2^(56-e-1)) = m >> (1075 - Ee + e + 1 - 56),
     // below 2^56 since |x| < 2^(e+1); the shift is -3 for the largest value of a normal scale group
     const int sh = 1075 - Ee + e + 1 - OZ_BITS * OZ_S;
-    const unsigned long long V = (x == 0.0 || sh >= 64) ? 0ull : (sh >= 0 ? (m >> sh) : (m << (-sh)));
+    const unsigned long long V = ((b << 1) == 0 || sh >= 64) ? 0ull : (sh >= 0 ? (m >> sh) : (m << (-sh)));
     const float sg = (b >> 63) ? -1.f : 1.f;
 #pragma unroll
-    for (int p = 0; p < OZ_S; ++p) d[p] = sg * (float)((V >> (OZ_BITS * (OZ_S - 1 - p))) & 127ull);
+    for (int p = 0; p < OZ_S; ++p) d[p] = sg * (float)(int)((V >> (OZ_BITS * (OZ_S - 1 - p))) & 127ull);
 }
 
 // Gram operand: X (n x c row-major) -> per block b of OZ_CHUNK rows, S slices of cp x OZ_CHUNK
