@@ -294,6 +294,115 @@ __global__ void __launch_bounds__(32) k_direct(DirectArgs a) {
     }
 }
 
+// Components of at most DS_MAX columns: 32 components per warp. The per-component scalar work
+// (H_c, its cyclic Jacobi eigendecomposition and the filter-moment coefficients) runs one
+// component per lane, so that every FP64 warp instruction does 32 lanes of work (GB300 issues
+// FP64 at 2 lanes per clock per SM whatever the active lanes; one warp per component left 28
+// of 32 lanes idle on 4-column components). Then the warp goes through its components with
+// lanes over the L columns of X for P = W^T X_c and the S rows, as k_direct does. The same
+// operations in the same order per component as k_direct. Shared memory, interleaved by
+// lane (entry e of lane t at [e 32 + t]): H, W (s x s) and coef (Mk x s) per lane.
+constexpr int DS_MAX = 8;
+__global__ void __launch_bounds__(32) k_direct_small(DirectArgs a) {
+    extern __shared__ double sm[];
+    const int s = a.s, L = a.L, lane = threadIdx.x, Mk = a.Mk;
+    double* sH = sm;
+    double* sW = sH + s * s * 32;
+    double* sC = sW + s * s * 32;
+    const int64_t q0 = a.comp0 + (int64_t)blockIdx.x * 32;
+    const int64_t qend = a.comp0 + a.ncomp;
+    const int64_t q = q0 + lane;
+#define DS_H(i, j) sH[((i) * s + (j)) * 32 + lane]
+#define DS_W(i, j) sW[((i) * s + (j)) * 32 + lane]
+    if (q < qend) {
+        for (int e = 0; e < s * s; ++e) {
+            sH[e * 32 + lane] = 0.0;
+            sW[e * 32 + lane] = (e / s == e % s) ? 1.0 : 0.0;
+        }
+        // H_c = sum over the component's rows of row^T row (rows in ascending order)
+        for (int64_t rp = a.comp_row_ptr[q]; rp < a.comp_row_ptr[q + 1]; ++rp) {
+            const int64_t r = a.comp_rows[rp];
+            const int64_t b = a.rowptr[r], e = a.rowptr[r + 1];
+            for (int64_t p1 = b; p1 < e; ++p1) {
+                const int i = a.col_local[a.colidx[p1]];
+                const double v1 = a.vals[p1];
+                for (int64_t p2 = b; p2 < e; ++p2) {
+                    const int j = a.col_local[a.colidx[p2]];
+                    DS_H(i, j) = __fma_rn(v1, a.vals[p2], DS_H(i, j));
+                }
+            }
+        }
+        // cyclic Jacobi: H = W diag(lambda) W^T
+        for (int sweep = 0; sweep < 40; ++sweep) {
+            double off = 0.0, dg = 0.0;
+            for (int i = 0; i < s; ++i)
+                for (int j = 0; j < s; ++j) {
+                    const double h = DS_H(i, j);
+                    if (i < j) off += h * h;
+                    if (i == j) dg += h * h;
+                }
+            if (off <= 1e-34 * dg || off == 0.0) break;
+            for (int p = 0; p < s - 1; ++p) {
+                for (int qq = p + 1; qq < s; ++qq) {
+                    const double apq = DS_H(p, qq);
+                    const double app = DS_H(p, p), aqq = DS_H(qq, qq);
+                    if (fabs(apq) <= 1e-300 || fabs(apq) <= 1e-18 * sqrt(fabs(app * aqq))) continue;
+                    const double theta = (aqq - app) / (2.0 * apq);
+                    const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                    const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+                    for (int k = 0; k < s; ++k) {
+                        if (k != p && k != qq) {
+                            const double hkp = DS_H(k, p), hkq = DS_H(k, qq);
+                            const double np_ = c * hkp - sn * hkq, nq_ = sn * hkp + c * hkq;
+                            DS_H(k, p) = np_;
+                            DS_H(p, k) = np_;
+                            DS_H(k, qq) = nq_;
+                            DS_H(qq, k) = nq_;
+                        }
+                        const double wkp = DS_W(k, p), wkq = DS_W(k, qq);
+                        DS_W(k, p) = c * wkp - sn * wkq;
+                        DS_W(k, qq) = sn * wkp + c * wkq;
+                    }
+                    DS_H(p, p) = app - t * apq;
+                    DS_H(qq, qq) = aqq + t * apq;
+                    DS_H(p, qq) = 0.0;
+                    DS_H(qq, p) = 0.0;
+                }
+            }
+        }
+        // filter-moment coefficients per eigenvalue: coef(m, i) at sC[(m s + i) 32 + lane]
+        for (int i = 0; i < s; ++i) filter_coefs(DS_H(i, i), a.quad, a.J, Mk, a.ell, sC + i * 32 + lane, s * 32);
+    }
+#undef DS_H
+#undef DS_W
+    __syncwarp();
+    // P = W^T X_c (s values per column l), then S rows = W diag(coef_m) P, component by component
+    const int nq = (int)(qend - q0 < 32 ? qend - q0 : 32);
+    for (int cq = 0; cq < nq; ++cq) {
+        const int32_t* cols = a.cols + a.comp_first[q0 + cq];
+        for (int l = lane; l < L; l += 32) {
+            double pv[DS_MAX];
+#pragma unroll
+            for (int i = 0; i < DS_MAX; ++i) {
+                double acc = 0.0;
+                if (i < s)
+                    for (int k = 0; k < s; ++k) acc = __fma_rn(sW[(k * s + i) * 32 + cq], a.X[(int64_t)cols[k] * a.ldx + l], acc);
+                pv[i] = acc;
+            }
+            for (int k = 0; k < s; ++k) {
+                double* srow = a.S + (int64_t)cols[k] * a.lds + l;
+                for (int m = 0; m < Mk; ++m) {
+                    double acc = 0.0;
+#pragma unroll
+                    for (int i = 0; i < DS_MAX; ++i)
+                        if (i < s) acc = __fma_rn(sW[(k * s + i) * 32 + cq] * sC[(m * s + i) * 32 + cq], pv[i], acc);
+                    srow[(int64_t)m * L] = acc;
+                }
+            }
+        }
+    }
+}
+
 int direct_moments(cmsvd_matrix* M, const cmsvd_params* p, const double2* quad, int Mk, const double* X, int64_t ldx,
                    double* S, int64_t lds, Arena& ws) {
     if (!M->comp.ready) CM_TRY(components_build(M));
@@ -337,6 +446,23 @@ int direct_moments(cmsvd_matrix* M, const cmsvd_params* p, const double2* quad, 
         a.s = C.group_size[g];
         a.comp0 = C.group_col_off[g];
         a.ncomp = C.group_count[g];
+        if (a.s <= DS_MAX && a.ncomp >= 64) {   // 32 components a warp
+            const size_t smem = sizeof(double) * 32 * (2 * a.s * a.s + (size_t)Mk * a.s);
+            if (smem > 48 * 1024)
+                CM_CUDA(cudaFuncSetAttribute(k_direct_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            const int64_t blocks = (a.ncomp + 31) / 32;
+            int64_t done = 0;
+            while (done < blocks) {
+                const int64_t chunk = blocks - done < 2147483647 ? blocks - done : 2147483647;
+                DirectArgs b = a;
+                b.comp0 = a.comp0 + done * 32;
+                b.ncomp = a.ncomp - done * 32;
+                k_direct_small<<<(unsigned)chunk, 32, smem, M->ctx->s>>>(b);
+                CM_LAUNCH();
+                done += chunk;
+            }
+            continue;
+        }
         const size_t smem = sizeof(double) * (2 * a.s * a.s + a.s + (size_t)Mk * a.s + (size_t)a.s * a.L);
         if (smem > 48 * 1024) CM_CUDA(cudaFuncSetAttribute(k_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int64_t left = a.ncomp;
