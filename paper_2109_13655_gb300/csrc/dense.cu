@@ -272,18 +272,17 @@ __global__ void __launch_bounds__(1024) k_chol(const double* __restrict__ G, int
                 atomicOr(flag, 1);
                 p = floor_;
             }
-            p = sqrt(p);
-            R[(size_t)k * c + k] = p;
-            sh_piv = p;
+            const double rp = rsqrt(p);
+            R[(size_t)k * c + k] = p * rp;
+            sh_piv = rp;
         }
         __syncthreads();
-        const double piv = sh_piv;
-        for (int j = k + 1 + t; j < c; j += nt) R[(size_t)k * c + j] /= piv;
+        const double rpiv = sh_piv;
+        for (int j = k + 1 + t; j < c; j += nt) R[(size_t)k * c + j] *= rpiv;
         __syncthreads();
-        const int w = c - k - 1;
-        for (int e = t; e < w * w; e += nt) {
-            const int i = k + 1 + e / w, j = k + 1 + e % w;
-            if (j >= i) R[(size_t)i * c + j] = __fma_rn(-R[(size_t)k * c + i], R[(size_t)k * c + j], R[(size_t)i * c + j]);
+        for (int i = k + 1 + (t >> 5); i < c; i += nt >> 5) {
+            const double rki = R[(size_t)k * c + i];
+            for (int j = i + (t & 31); j < c; j += 32) R[(size_t)i * c + j] = __fma_rn(-rki, R[(size_t)k * c + j], R[(size_t)i * c + j]);
         }
         __syncthreads();
     }
@@ -836,18 +835,18 @@ __global__ void __launch_bounds__(256) k_chol_coop(const double* __restrict__ G,
                         atomicOr(flag, 1);
                         p = floor_;
                     }
-                    p = sqrt(p);
-                    R[(size_t)kk * c + kk] = p;
-                    sh_rpiv = 1.0 / p;
+                    const double rp = rsqrt(p);
+                    R[(size_t)kk * c + kk] = p * rp;
+                    sh_rpiv = rp;
                 }
                 __syncthreads();
                 const double rpiv = sh_rpiv;
                 for (int j = kk + 1 + t; j < k0 + b; j += blockDim.x) R[(size_t)kk * c + j] *= rpiv;
                 __syncthreads();
-                const int wb = k0 + b - kk - 1;
-                for (int e = t; e < wb * wb; e += blockDim.x) {
-                    const int i = kk + 1 + e / wb, j = kk + 1 + e % wb;
-                    if (j >= i) R[(size_t)i * c + j] = __fma_rn(-R[(size_t)kk * c + i], R[(size_t)kk * c + j], R[(size_t)i * c + j]);
+                for (int i = kk + 1 + (t >> 5); i < k0 + b; i += blockDim.x >> 5) {
+                    const double rki = R[(size_t)kk * c + i];
+                    for (int j = i + (t & 31); j < k0 + b; j += 32)
+                        R[(size_t)i * c + j] = __fma_rn(-rki, R[(size_t)kk * c + j], R[(size_t)i * c + j]);
                 }
                 __syncthreads();
             }
@@ -870,13 +869,14 @@ __global__ void __launch_bounds__(256) k_chol_coop(const double* __restrict__ G,
             }
         }
         if (!grid_barrier(ctl, gridDim.x)) return;
-        // trailing update of the upper triangle
-        for (int64_t e = gtid; e < (int64_t)w * w; e += gthreads) {
-            const int i = k0 + b + (int)(e / w), j = k0 + b + (int)(e % w);
-            if (j < i) continue;
-            double acc = R[(size_t)i * c + j];
-            for (int q = k0; q < k0 + b; ++q) acc = __fma_rn(-R[(size_t)q * c + i], R[(size_t)q * c + j], acc);
-            R[(size_t)i * c + j] = acc;
+        // trailing update of the upper triangle: a warp per row, lanes over its columns
+        for (int64_t gw = gtid >> 5; gw < w; gw += gthreads >> 5) {
+            const int i = k0 + b + (int)gw;
+            for (int j = i + (t & 31); j < c; j += 32) {
+                double acc = R[(size_t)i * c + j];
+                for (int q = k0; q < k0 + b; ++q) acc = __fma_rn(-R[(size_t)q * c + i], R[(size_t)q * c + j], acc);
+                R[(size_t)i * c + j] = acc;
+            }
         }
         if (!grid_barrier(ctl, gridDim.x)) return;
     }
@@ -933,9 +933,9 @@ __global__ void __launch_bounds__(1024) k_pchol_deflate(const double* __restrict
             if (k == 0) sh_d0 = dv;
             sh_piv = dv;
             sh_j = bj;
-            const double l = sqrt(dv);
-            sh_lkk = l;
-            sh_rl = 1.0 / l;
+            const double rl = rsqrt(dv);   // one reciprocal square root: 1/l and l = d / l
+            sh_lkk = dv * rl;
+            sh_rl = rl;
         }
         __syncthreads();
         const int j = sh_j;
@@ -968,11 +968,12 @@ __global__ void __launch_bounds__(1024) k_pchol_deflate(const double* __restrict
         const double lkk = sh_lkk, rl = sh_rl;
         for (int i = k + t; i < c; i += nt) L[(size_t)i * c + k] = i == k ? lkk : W[(size_t)k * c + i] * rl;
         __syncthreads();
-        const int w = c - k - 1;
-        for (int e = t; e < w * w; e += nt) {
-            const int i = k + 1 + e / w, jj = k + 1 + e % w;
-            if (jj >= i)
-                W[(size_t)i * c + jj] = __fma_rn(-L[(size_t)i * c + k], L[(size_t)jj * c + k], W[(size_t)i * c + jj]);
+        // trailing upper triangle: a warp per row, lanes over its columns (no index division,
+        // no idle lanes below the diagonal)
+        for (int i = k + 1 + warp; i < c; i += nw) {
+            const double lik = L[(size_t)i * c + k];
+            for (int jj = i + lane; jj < c; jj += 32)
+                W[(size_t)i * c + jj] = __fma_rn(-lik, L[(size_t)jj * c + k], W[(size_t)i * c + jj]);
         }
         __syncthreads();
     }
