@@ -8,15 +8,24 @@ def _prof(ms, launches, byts, flops):
     return {"ms": ms, "launches": launches, "bytes": byts, "flops": flops}
 
 
-def test_roofline_alu_bound_gemm_with_measured_traffic():
-    prof = {"gemm": _prof(45.6, 12, 1.93e9, 4.81e10)}
-    r = bench.roofline("gemm", prof, [], {"name": "block_permuted_200000x100000"})
+def test_roofline_alu_bound_fp64_class():
+    prof = {"jacobi": _prof(162.5, 60, 3.98e10, 2.25e10)}
+    r = bench.roofline("jacobi", prof, [], {"name": "block_permuted_200000x100000"})
     assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
-    assert abs(r["achieved"] - 4.81e10 / 0.0456 / 1e12) < 1e-9
+    assert abs(r["achieved"] - 2.25e10 / 0.1625 / 1e12) < 1e-9
     assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
-    assert r["traffic"] == 154.6e6
-    # another workload has no measured traffic for this class
-    assert bench.roofline("gemm", prof, [], {"name": "random_sparse_2000x1000"})["traffic"] is None
+    assert r["traffic"] == bench.MEASURED_TRAFFIC.get(("block_permuted_200000x100000", "jacobi"))
+
+
+def test_roofline_tensor_class_counts_slice_products():
+    """The Gram and product classes run as 36 BF16 slice products per FP64 product: the
+    roofline is against the BF16 tensor peak, with the FP64-equivalent rate beside it."""
+    prof = {"gram": _prof(77.1, 70, 1.16e10, 7.04e11)}
+    r = bench.roofline("gram", prof, [], {"name": "block_permuted_200000x100000"})
+    assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
+    assert abs(r["fp64_equivalent_tflops"] - 7.04e11 / 0.0771 / 1e12) < 1e-9
+    assert abs(r["achieved"] - 36 * r["fp64_equivalent_tflops"]) < 1e-9
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
 
 
 def test_roofline_hbm_bound_when_intensity_is_low():
