@@ -168,6 +168,39 @@ __device__ __forceinline__ double oz_combine(long long th, long long tl) {
     return __fma_rn((double)th, 0x1p-35, (double)tl * 0x1p-63);
 }
 
+// (th 2^-35 + tl 2^-63) 2^sc rounded once to the nearest double (ties to even), in integer
+// operations only (the product epilogue touches every output entry, and on GB300 its FP64
+// conversions and scaling kept the FP64 pipe 61% busy); results below the normal range
+// flush to zero, above it to infinity.
+__device__ __forceinline__ double oz_to_double(long long th, long long tl, int sc) {
+    const __int128 T = (__int128)th * (1ll << 28) + tl;   // value = T 2^(sc - 63), |T| < 2^78
+    if (T == 0) return 0.0;
+    const bool neg = T < 0;
+    const unsigned __int128 a = neg ? (unsigned __int128)(-T) : (unsigned __int128)T;
+    const unsigned long long hi = (unsigned long long)(a >> 64), lo = (unsigned long long)a;
+    const int msb = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+    const int sh = msb - 52;
+    unsigned long long m;
+    if (sh > 0) {
+        m = (unsigned long long)(a >> sh);
+        const unsigned __int128 rem = a & ((((unsigned __int128)1) << sh) - 1);
+        const unsigned __int128 half = ((unsigned __int128)1) << (sh - 1);
+        if (rem > half || (rem == half && (m & 1))) ++m;
+    } else {
+        m = lo << (-sh);
+    }
+    int e = sh + sc - 63;   // value = m 2^e, m in [2^52, 2^53]
+    if (m == (1ull << 53)) {
+        m >>= 1;
+        ++e;
+    }
+    const int field = e + 52 + 1023;
+    const unsigned long long sign = (unsigned long long)neg << 63;
+    if (field <= 0) return __longlong_as_double((long long)sign);
+    if (field >= 2047) return __longlong_as_double((long long)(sign | (0x7ffull << 52)));
+    return __longlong_as_double((long long)(sign | ((unsigned long long)field << 52) | (m & 0xfffffffffffffull)));
+}
+
 // Gram, pass 1: P[part][j + k c1] = sum_lvl 2^(-7 lvl) sum_{pairs of lvl} sum_{b in part}
 // C[pair][b][j + k c1] over a part of OZ_PART blocks of the current group (blockIdx.y); a level
 // sum over a part has at most 8 x 8 terms below 2^24: |s_k| < 2^30.
@@ -220,7 +253,7 @@ __global__ void k_oz_gemm_epi(const float* __restrict__ C, int ng, OzLevels lv, 
                 if (lvl <= 5) th += sk << (OZ_BITS * (5 - lvl));
                 else tl += sk << (OZ_BITS * (9 - lvl));
             }
-            Z[i * ldz + l] = ldexp(oz_combine(th, tl), si + oz_shift(ew[l]));
+            Z[i * ldz + l] = oz_to_double(th, tl, si + oz_shift(ew[l]));
         }
     }
 }
