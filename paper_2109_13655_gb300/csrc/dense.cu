@@ -239,6 +239,11 @@ int gemm_nn(const double* X, int64_t ldx, const double* W, int64_t ldw, double* 
     double work = 0.0;   // multiply-adds actually performed per row
     for (int cc0 = 0; cc0 < c2; cc0 += GT) work += (double)(upper ? min(c1, cc0 + GT) : c1) * min(GT, c2 - cc0);
     ProfScope ps(CMSVD_PROF_GEMM, s, 8.0 * ((double)n * c1 + (double)c1 * c2 + (double)n * c2), 2.0 * n * work);
+    // few output tiles and a long contraction (the c x c products): the library GEMM spreads
+    // the contraction over the GPU (dense arithmetic 1 keeps the tiled kernel throughout)
+    if (ctx && ctx->s == s && ctx->dense_arith == 0 && !upper && c1 >= 128 && (int64_t)grid.x * grid.y < ctx->sm_count &&
+        n < (1ll << 31) && ldx < (1ll << 31) && ldw < (1ll << 31) && ldz < (1ll << 31))
+        return gemm_fp64_small(ctx, X, ldx, W, ldw, Z, ldz, n, c1, c2);
     k_gemm_nn<<<grid, 256, 0, s>>>(X, ldx, W, ldw, Z, ldz, n, c1, c2, upper);
     CM_LAUNCH();
     return CMSVD_OK;

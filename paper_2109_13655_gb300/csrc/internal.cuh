@@ -170,6 +170,8 @@ int gram_ozaki(cmsvd_context* ctx, const double* X, int64_t ldx, int c1, const d
                int64_t n, double* G, int64_t ldg);
 int gemm_ozaki(cmsvd_context* ctx, const double* X, int64_t ldx, const double* W, int64_t ldw, double* Z, int64_t ldz,
                int64_t n, int c1, int c2);
+int gemm_fp64_small(cmsvd_context* ctx, const double* X, int64_t ldx, const double* W, int64_t ldw, double* Z,
+                    int64_t ldz, int64_t n, int c1, int c2);
 void ozaki_release(cmsvd_context* ctx);
 
 // ----------------------------------------------------------------------------- entry-point session

@@ -446,6 +446,22 @@ int gemm_ozaki(cmsvd_context* ctx, const double* X, int64_t ldx, const double* W
     return CMSVD_OK;
 }
 
+// Z (n x c2, ldz) = X (n x c1, ldx) W (c1 x c2, ldw), row-major, in FP64 on cuBLAS's DGEMM: for
+// the small square products of the orthogonalization (c x c times c x c), whose 64 x 64 output
+// tiles are fewer than the SMs, so the tiled FP64 kernel ran on 16 of 152 SMs; the library
+// splits the contraction over the GPU. Deterministic (cuBLAS's GEMMs are run to run).
+int gemm_fp64_small(cmsvd_context* ctx, const double* X, int64_t ldx, const double* W, int64_t ldw, double* Z,
+                    int64_t ldz, int64_t n, int c1, int c2) {
+    cublasHandle_t h;
+    CM_TRY(oz_handle(ctx, &h));
+    const double one = 1.0, zero = 0.0;
+    // column-major view: Z^T (c2 x n) = W^T (c2 x c1) X^T (c1 x n)
+    CM_TRY(blas_ok(cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, c2, (int)n, c1, &one, W, (int)ldw, X, (int)ldx, &zero, Z,
+                               (int)ldz),
+                   "cublasDgemm (small product)"));
+    return CMSVD_OK;
+}
+
 void ozaki_release(cmsvd_context* ctx) {
     if (ctx->blas) cublasDestroy((cublasHandle_t)ctx->blas);
     ctx->blas = nullptr;
