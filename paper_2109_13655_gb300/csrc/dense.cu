@@ -293,30 +293,50 @@ __global__ void __launch_bounds__(1024) k_chol(const double* __restrict__ G, int
     }
 }
 
-// Ri = R^{-1} for upper-triangular R (row-major): one 128-thread CTA per column j,
-// back substitution x_i = -(sum_{k=i+1..j} R_ik x_k) / R_ii with a block reduction per i.
-// The reciprocals of the diagonal are formed first, in parallel (an FP64 division is ~650
-// clocks of latency on GB300; the substitution then multiplies).
+// Ri = R^{-1} for upper-triangular R (row-major, c <= 1024): one 128-thread CTA per column j
+// solves R x = e_j in the column (axpy) form: for k = j, j-1, .., 0, x_k is final once the
+// columns right of it have been subtracted, x_k *= 1/R_kk, and every row i < k takes
+// x_i -= R_ik x_k (each thread owns rows t + 128 u). A step is one FP64 multiply, one FMA per
+// owned row and one barrier, rather than a block reduction (an FP64 add costs ~64 clocks of
+// latency on GB300); the next column of R is loaded during the current step, and the
+// reciprocals of the diagonal are formed first, in parallel.
+constexpr int TI_RPT = 8;   // rows per thread
 __global__ void __launch_bounds__(128) k_trinv(const double* __restrict__ R, int c, double* __restrict__ Ri) {
-    __shared__ double x[1024];
-    __shared__ double rinv[1024];
-    __shared__ double sh[4];
+    __shared__ double x[128 * TI_RPT];
+    __shared__ double rinv[128 * TI_RPT];
     const int j = blockIdx.x, t = threadIdx.x;
     if (j >= c) return;
     for (int i = t; i < c; i += 128) Ri[(size_t)i * c + j] = 0.0;
-    for (int i = t; i <= j; i += 128) rinv[i] = 1.0 / R[(size_t)i * c + i];
-    __syncthreads();
-    if (t == 0) x[j] = rinv[j];
-    __syncthreads();
-    for (int i = j - 1; i >= 0; --i) {
-        double s = 0.0;
-        for (int k = i + 1 + t; k <= j; k += 128) s = __fma_rn(R[(size_t)i * c + k], x[k], s);
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if ((t & 31) == 0) sh[t >> 5] = s;
-        __syncthreads();
-        if (t == 0) x[i] = -((sh[0] + sh[1]) + (sh[2] + sh[3])) * rinv[i];
-        __syncthreads();
+    for (int i = t; i <= j; i += 128) {
+        rinv[i] = 1.0 / R[(size_t)i * c + i];
+        x[i] = i == j ? 1.0 : 0.0;
     }
+    double rc[TI_RPT];   // R[i][k] of the owned rows for the current k
+#pragma unroll
+    for (int u = 0; u < TI_RPT; ++u) {
+        const int i = t + 128 * u;
+        rc[u] = i < j ? R[(size_t)i * c + j] : 0.0;
+    }
+    __syncthreads();
+    for (int k = j; k >= 0; --k) {
+        const double xk = x[k] * rinv[k];
+        double rn[TI_RPT];
+#pragma unroll
+        for (int u = 0; u < TI_RPT; ++u) {
+            const int i = t + 128 * u;
+            rn[u] = i < k - 1 ? __ldg(R + (size_t)i * c + (k - 1)) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < TI_RPT; ++u) {
+            const int i = t + 128 * u;
+            if (i < k) x[i] = __fma_rn(-rc[u], xk, x[i]);
+        }
+        __syncthreads();   // every thread has read x[k] and updated its rows
+        if (t == 0) x[k] = xk;
+#pragma unroll
+        for (int u = 0; u < TI_RPT; ++u) rc[u] = rn[u];
+    }
+    __syncthreads();
     for (int i = t; i <= j; i += 128) Ri[(size_t)i * c + j] = x[i];
 }
 
