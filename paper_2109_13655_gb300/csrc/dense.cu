@@ -825,81 +825,109 @@ int jacobi_svd(const double* Bm, int brows, int bcols, int trans, double* Xc, do
 
 // min over max of the diagonal of an upper-triangular R (condition estimate of CholeskyQR)
 // Cooperative blocked form of k_chol for larger c (same result up to rounding order):
-// panels of CB = 32 rows. Per panel: CTA 0 factors the diagonal block; every thread of the
-// grid solves one column of the panel row R12 = R11^{-T} A12; the grid updates the upper
-// triangle of the trailing block, A22 -= R12^T R12. GB300 issues only 2 FP64 FMA per clock
-// per SM, so the c^3/6 multiply-adds are spread over the whole grid. The grid barrier
-// between phases is bounded (ctl[3] = 1 on timeout; every CTA then returns).
+// panels of CB = 32 rows. Per panel: CTA 0 factors the diagonal block in shared memory;
+// every thread of the grid solves one column of the panel row R12 = R11^{-T} A12 in
+// registers, against the diagonal block staged in each CTA's shared memory (column form:
+// one dependent multiply-add per step instead of a dot-product chain per row); the grid
+// updates the upper triangle of the trailing block, A22 -= R12^T R12. GB300 issues only 2
+// FP64 FMA per clock per SM and a dependent FP64 operation takes ~64 clocks, so the c^3/6
+// multiply-adds are spread over the whole grid and the serial steps kept out of L2. The
+// grid barrier between phases is bounded (ctl[3] = 1 on timeout; every CTA then returns).
 constexpr int CB = 32;
 __global__ void __launch_bounds__(256) k_chol_coop(const double* __restrict__ G, int c, double shift_coef,
                                                    double* __restrict__ R, int* flag, unsigned* ctl) {
-    __shared__ double sh_tr;
-    const int t = threadIdx.x;
+    __shared__ double sh_tr, sh_rpiv;
+    __shared__ double Ds[CB][CB + 1];   // the panel's diagonal block (upper triangle)
+    __shared__ double rdiag[CB];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5, nw = blockDim.x >> 5;
     const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + t, gthreads = (int64_t)gridDim.x * blockDim.x;
-    if (t == 0) {
+    if (wid == 0) {   // trace of G: lanes over the diagonal, then a fixed shuffle tree
         double tr = 0.0;
-        for (int i = 0; i < c; ++i) tr += G[(size_t)i * c + i];
-        sh_tr = tr;
+        for (int i = lane; i < c; i += 32) tr += G[(size_t)i * c + i];
+        for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(0xffffffffu, tr, o);
+        if (lane == 0) sh_tr = tr;
     }
     __syncthreads();
     const double shift = shift_coef * sh_tr;
     const double floor_ = 1e-300 + 1e-32 * sh_tr;
-    for (int64_t e = gtid; e < (int64_t)c * c; e += gthreads) {
-        const int i = (int)(e / c), j = (int)(e % c);
+    for (int e = (int)gtid; e < c * c; e += (int)gthreads) {
+        const int i = e / c, j = e % c;
         R[e] = j >= i ? G[e] + (i == j ? shift : 0.0) : 0.0;
     }
     if (!grid_barrier(ctl, gridDim.x)) return;
+    // R is written by other CTAs between the barriers: it is read with __ldcg (from L2)
     for (int k0 = 0; k0 < c; k0 += CB) {
         const int b = min(CB, c - k0), w = c - k0 - b;
-        if (blockIdx.x == 0) {   // diagonal block, right-looking in place
-            __shared__ double sh_rpiv;
-            for (int kk = k0; kk < k0 + b; ++kk) {
+        if (blockIdx.x == 0) {   // diagonal block, right-looking, in shared memory
+            for (int e = t; e < b * b; e += blockDim.x) {
+                const int i = e / b, j = e % b;
+                Ds[i][j] = j >= i ? __ldcg(R + (size_t)(k0 + i) * c + k0 + j) : 0.0;
+            }
+            __syncthreads();
+            for (int kk = 0; kk < b; ++kk) {
                 if (t == 0) {
-                    double p = R[(size_t)kk * c + kk];
+                    double p = Ds[kk][kk];
                     if (!(p > floor_)) {
                         atomicOr(flag, 1);
                         p = floor_;
                     }
                     const double rp = rsqrt(p);
-                    R[(size_t)kk * c + kk] = p * rp;
+                    Ds[kk][kk] = p * rp;
                     sh_rpiv = rp;
                 }
                 __syncthreads();
                 const double rpiv = sh_rpiv;
-                for (int j = kk + 1 + t; j < k0 + b; j += blockDim.x) R[(size_t)kk * c + j] *= rpiv;
+                for (int j = kk + 1 + t; j < b; j += blockDim.x) Ds[kk][j] *= rpiv;
                 __syncthreads();
-                for (int i = kk + 1 + (t >> 5); i < k0 + b; i += blockDim.x >> 5) {
-                    const double rki = R[(size_t)kk * c + i];
-                    for (int j = i + (t & 31); j < k0 + b; j += 32)
-                        R[(size_t)i * c + j] = __fma_rn(-rki, R[(size_t)kk * c + j], R[(size_t)i * c + j]);
+                for (int i = kk + 1 + wid; i < b; i += nw) {
+                    const double rki = Ds[kk][i];
+                    for (int j = i + lane; j < b; j += 32) Ds[i][j] = __fma_rn(-rki, Ds[kk][j], Ds[i][j]);
                 }
                 __syncthreads();
+            }
+            for (int e = t; e < b * b; e += blockDim.x) {
+                const int i = e / b, j = e % b;
+                if (j >= i) R[(size_t)(k0 + i) * c + k0 + j] = Ds[i][j];
             }
         }
         if (!grid_barrier(ctl, gridDim.x)) return;
         if (w == 0) break;
-        // panel row: column j of R12 solves R11^T x = A12(:, j) (forward substitution, with the
-        // reciprocals of the panel's diagonal formed once per CTA)
-        {
-            __shared__ double rdiag[CB];
-            for (int i = t; i < b; i += blockDim.x) rdiag[i] = 1.0 / R[(size_t)(k0 + i) * c + k0 + i];
-            __syncthreads();
-            for (int64_t jj = gtid; jj < w; jj += gthreads) {
-                const int j = k0 + b + (int)jj;
-                for (int i = k0; i < k0 + b; ++i) {
-                    double acc = R[(size_t)i * c + j];
-                    for (int q = k0; q < i; ++q) acc = __fma_rn(-R[(size_t)q * c + i], R[(size_t)q * c + j], acc);
-                    R[(size_t)i * c + j] = acc * rdiag[i - k0];
+        // panel row: column j of R12 solves R11^T x = A12(:, j) by forward substitution in
+        // registers, in column (axpy) form: x_i = a_i / R_ii, then a_q -= R_iq x_i for q > i
+        // (the same multiply-adds, in the same order, as the row form)
+        for (int e = t; e < b * b; e += blockDim.x) {
+            const int i = e / b, j = e % b;
+            Ds[i][j] = j >= i ? __ldcg(R + (size_t)(k0 + i) * c + k0 + j) : 0.0;
+        }
+        __syncthreads();
+        for (int i = t; i < b; i += blockDim.x) rdiag[i] = 1.0 / Ds[i][i];
+        __syncthreads();
+        for (int64_t jj = gtid; jj < w; jj += gthreads) {
+            const int j = k0 + b + (int)jj;
+            double av[CB];
+#pragma unroll
+            for (int u = 0; u < CB; ++u) av[u] = u < b ? __ldcg(R + (size_t)(k0 + u) * c + j) : 0.0;
+#pragma unroll
+            for (int i = 0; i < CB; ++i) {
+                if (i < b) {
+                    const double x = av[i] * rdiag[i];
+                    av[i] = x;
+#pragma unroll
+                    for (int q = i + 1; q < CB; ++q) av[q] = __fma_rn(-Ds[i][q], x, av[q]);
                 }
             }
+#pragma unroll
+            for (int u = 0; u < CB; ++u)
+                if (u < b) R[(size_t)(k0 + u) * c + j] = av[u];
         }
         if (!grid_barrier(ctl, gridDim.x)) return;
         // trailing update of the upper triangle: a warp per row, lanes over its columns
         for (int64_t gw = gtid >> 5; gw < w; gw += gthreads >> 5) {
             const int i = k0 + b + (int)gw;
-            for (int j = i + (t & 31); j < c; j += 32) {
-                double acc = R[(size_t)i * c + j];
-                for (int q = k0; q < k0 + b; ++q) acc = __fma_rn(-R[(size_t)q * c + i], R[(size_t)q * c + j], acc);
+            for (int j = i + lane; j < c; j += 32) {
+                double acc = __ldcg(R + (size_t)i * c + j);
+                for (int q = k0; q < k0 + b; ++q)
+                    acc = __fma_rn(-__ldcg(R + (size_t)q * c + i), __ldcg(R + (size_t)q * c + j), acc);
                 R[(size_t)i * c + j] = acc;
             }
         }
