@@ -948,6 +948,7 @@ __global__ void __launch_bounds__(1024) k_pchol_deflate(const double* __restrict
                                                         double* __restrict__ W, double* __restrict__ L,
                                                         double* __restrict__ R3, int* __restrict__ cp_out) {
     __shared__ int perm[512];
+    __shared__ double lcol[512];
     __shared__ long long rv[32];
     __shared__ int ri[32];
     __shared__ double sh_d0, sh_piv, sh_lkk, sh_rl;
@@ -1019,14 +1020,18 @@ __global__ void __launch_bounds__(1024) k_pchol_deflate(const double* __restrict
             __syncthreads();
         }
         const double lkk = sh_lkk, rl = sh_rl;
-        for (int i = k + t; i < c; i += nt) L[(size_t)i * c + k] = i == k ? lkk : W[(size_t)k * c + i] * rl;
+        for (int i = k + t; i < c; i += nt) {
+            const double v = i == k ? lkk : W[(size_t)k * c + i] * rl;
+            L[(size_t)i * c + k] = v;
+            lcol[i] = v;   // column k of L, staged for the update (its global copy is strided)
+        }
         __syncthreads();
         // trailing upper triangle: a warp per row, lanes over its columns (no index division,
         // no idle lanes below the diagonal)
         for (int i = k + 1 + warp; i < c; i += nw) {
-            const double lik = L[(size_t)i * c + k];
+            const double lik = lcol[i];
             for (int jj = i + lane; jj < c; jj += 32)
-                W[(size_t)i * c + jj] = __fma_rn(-lik, L[(size_t)jj * c + k], W[(size_t)i * c + jj]);
+                W[(size_t)i * c + jj] = __fma_rn(-lik, lcol[jj], W[(size_t)i * c + jj]);
         }
         __syncthreads();
     }
