@@ -22,25 +22,20 @@
 // The slice products are plain BF16 GEMMs with FP32 outputs and run on cuBLAS; slicing and the
 // FP64 epilogue are this file's kernels.
 #include "internal.cuh"
+#include "ozaki_math.cuh"
 #include <cublas_v2.h>
 #include <climits>
 
 namespace cmsvd {
 
-constexpr int OZ_S = 8;          // slices
-constexpr int OZ_BITS = 7;       // bits per slice
 constexpr int OZ_KMAX = 1024;    // products per exact FP32 sum
 constexpr int OZ_CHUNK = 1024;   // Gram: rows per block (one slice pair of a block: 1024 products)
 constexpr int OZ_PAIRS = 36;     // slice pairs (p, q), p + q <= S + 1 (levels 2..9)
 static_assert(OZ_S == 8 && OZ_BITS == 7, "the epilogues combine levels 2..5 and 6..9");
 
 // ----------------------------------------------------------------------------- scales
-// ilogb of the largest |x| of each column (cols of an n x c row-major block) / each row, from the
-// exponent field (integer work: a subnormal counts as 2^-1023, an upper bound of its ilogb,
-// which the slicing accepts as a scale).
-__device__ __forceinline__ int oz_ilogb(double v) {
-    return (int)((__double_as_longlong(v) >> 52) & 0x7ff) - 1023;
-}
+// ilogb of the largest |x| of each column (cols of an n x c row-major block) / each row
+// (oz_ilogb: from the exponent field).
 __global__ void k_oz_col_exp(const double* __restrict__ X, int64_t ld, int64_t n, int c, int* __restrict__ ex) {
     for (int j = threadIdx.x; j < c; j += blockDim.x) {
         int best = INT_MIN;
@@ -66,28 +61,11 @@ __global__ void k_oz_row_exp(const double* __restrict__ X, int64_t ld, int64_t n
     }
 }
 
-// The S slices of x relative to the scale 2^(e+1) (e = ilogb of the largest |x| it shares a
-// scale with): the magnitude as a fixed-point integer with 7 S = 56 fractional bits, cut into
-// 7-bit fields (exact integer arithmetic), each carrying the sign of x.
 // scale exponents are initialised to OZ_NONE (all-zero column or row)
 constexpr int OZ_NONE = (int)0x80808080;
 __device__ __forceinline__ int oz_e(int e) { return e == OZ_NONE || e == INT_MIN ? 0 : e; }
 __device__ __forceinline__ int oz_shift(int e) { return e == OZ_NONE || e == INT_MIN ? 0 : e + 1; }
 
-__device__ __forceinline__ void oz_slices(double x, int e, float (&d)[OZ_S]) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const int E = (int)((b >> 52) & 0x7ff);
-    unsigned long long m = b & ((1ull << 52) - 1);
-    int Ee = E;
-    if (E == 0) Ee = 1; else m |= 1ull << 52;
-    // |x| = m 2^(Ee-1075); scale 2^(e+1): V = floor(|x| 2^(56-e-1)) = m >> (1075 - Ee + e + 1 - 56),
-    // below 2^56 since |x| < 2^(e+1); the shift is -3 for the largest value of a normal scale group
-    const int sh = 1075 - Ee + e + 1 - OZ_BITS * OZ_S;
-    const unsigned long long V = ((b << 1) == 0 || sh >= 64) ? 0ull : (sh >= 0 ? (m >> sh) : (m << (-sh)));
-    const float sg = (b >> 63) ? -1.f : 1.f;
-#pragma unroll
-    for (int p = 0; p < OZ_S; ++p) d[p] = sg * (float)(int)((V >> (OZ_BITS * (OZ_S - 1 - p))) & 127ull);
-}
 
 // Gram operand: X (n x c row-major) -> per block b of OZ_CHUNK rows, S slices of cp x OZ_CHUNK
 // column-major (ld cp, cp = c rounded up to 8: the pad entries are zero, and the GEMMs see
@@ -168,38 +146,6 @@ __device__ __forceinline__ double oz_combine(long long th, long long tl) {
     return __fma_rn((double)th, 0x1p-35, (double)tl * 0x1p-63);
 }
 
-// (th 2^-35 + tl 2^-63) 2^sc rounded once to the nearest double (ties to even), in integer
-// operations only (the product epilogue touches every output entry, and on GB300 its FP64
-// conversions and scaling kept the FP64 pipe 61% busy); results below the normal range
-// flush to zero, above it to infinity.
-__device__ __forceinline__ double oz_to_double(long long th, long long tl, int sc) {
-    const __int128 T = (__int128)th * (1ll << 28) + tl;   // value = T 2^(sc - 63), |T| < 2^78
-    if (T == 0) return 0.0;
-    const bool neg = T < 0;
-    const unsigned __int128 a = neg ? (unsigned __int128)(-T) : (unsigned __int128)T;
-    const unsigned long long hi = (unsigned long long)(a >> 64), lo = (unsigned long long)a;
-    const int msb = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
-    const int sh = msb - 52;
-    unsigned long long m;
-    if (sh > 0) {
-        m = (unsigned long long)(a >> sh);
-        const unsigned __int128 rem = a & ((((unsigned __int128)1) << sh) - 1);
-        const unsigned __int128 half = ((unsigned __int128)1) << (sh - 1);
-        if (rem > half || (rem == half && (m & 1))) ++m;
-    } else {
-        m = lo << (-sh);
-    }
-    int e = sh + sc - 63;   // value = m 2^e, m in [2^52, 2^53]
-    if (m == (1ull << 53)) {
-        m >>= 1;
-        ++e;
-    }
-    const int field = e + 52 + 1023;
-    const unsigned long long sign = (unsigned long long)neg << 63;
-    if (field <= 0) return __longlong_as_double((long long)sign);
-    if (field >= 2047) return __longlong_as_double((long long)(sign | (0x7ffull << 52)));
-    return __longlong_as_double((long long)(sign | ((unsigned long long)field << 52) | (m & 0xfffffffffffffull)));
-}
 
 // Gram, pass 1: P[part][j + k c1] = sum_lvl 2^(-7 lvl) sum_{pairs of lvl} sum_{b in part}
 // C[pair][b][j + k c1] over a part of OZ_PART blocks of the current group (blockIdx.y); a level
