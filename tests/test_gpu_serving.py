@@ -83,3 +83,40 @@ def test_serving_rejects_oversized_and_unknown(B):
     with pytest.raises(RuntimeError):
         srv.wait(12345)
     srv.close()
+
+
+def test_serving_matches_the_oracle(B):
+    """Two requests served side by side on one resident matrix, each against the oracle's solve
+    of the same problem (same A, interval, N, L, M and V_in): the exact count, sigma within
+    1e-10, residuals <= 1e-10, and U, V within residual / gap of the oracle's vectors."""
+    from oracle import cmsvd_oracle as O
+    bp = synth.block_permuted(300, 16, 8, seed=41, dist="uniform_bf16")
+    s = bp.sigmas_desc()
+    p = B.params(N=32, L=32, M=4)
+    reqs = []
+    for k, (first, t) in enumerate(((60, 20), (900, 25))):
+        a, b, _ = synth.window_interval(s, first, t, min_rel_gap=1e-6, max_shift=10)
+        reqs.append((a, b, t, 700 + k))
+    srv = B.Server(slots=2, hbm_budget=1 << 30)
+    mid = srv.add_matrix(bp.A)
+    tickets = [srv.submit(mid, a, b, p, synth.gaussian_block(bp.A.n, 32, seed)) for (a, b, t, seed) in reqs]
+    results = []
+    for tk in tickets:
+        done, nt, st, lat, q = srv.wait(tk)
+        assert done and st == B.OK
+        results.append(srv.take(tk, mid, nt, st))
+    srv.close()
+    sp = np.sort(s)
+    for (a, b, t, seed), r in zip(reqs, results):
+        ref = O.solve_interval(bp.A, a, b, 32, 32, 4, synth.gaussian_block(bp.A.n, 32, seed), norm_A=s[0])
+        assert r.sigma.size == ref.sigma.size == t
+        assert np.max(np.abs(r.sigma - ref.sigma) / ref.sigma) <= 1e-10
+        assert r.res_u.max() <= 1e-10 and r.res_v.max() <= 1e-10
+        for i, sig in enumerate(ref.sigma):
+            k = np.searchsorted(sp, sig)
+            nb = sp[max(k - 2, 0):k + 2]
+            nb = nb[np.abs(nb - sig) > 1e-13 * sig]
+            gap = np.min(np.abs(nb - sig)) if nb.size else sig
+            tol = max(1e-7, 10 * s[0] * (r.res_u[i] + ref.res_u[i] + 1e-16) / gap)
+            assert np.max(np.abs(r.V[:, i] - ref.V[:, i])) <= tol
+            assert np.max(np.abs(r.U[:, i] - ref.U[:, i])) <= tol
