@@ -64,7 +64,9 @@ OZ_HD void oz_slices(double x, int e, float (&d)[OZ_S]) {
     const int sh = 1075 - Ee + e + 1 - OZ_BITS * OZ_S;
     const uint64_t V = ((b << 1) == 0 || sh >= 64) ? 0ull : (sh >= 0 ? (m >> sh) : (m << (-sh)));
     const float sg = (b >> 63) ? -1.f : 1.f;
+#ifdef __CUDA_ARCH__
 #pragma unroll
+#endif
     for (int p = 0; p < OZ_S; ++p) d[p] = sg * (float)(int)((V >> (OZ_BITS * (OZ_S - 1 - p))) & 127ull);
 }
 
