@@ -446,8 +446,9 @@ int direct_moments(cmsvd_matrix* M, const cmsvd_params* p, const double2* quad, 
         a.s = C.group_size[g];
         a.comp0 = C.group_col_off[g];
         a.ncomp = C.group_count[g];
-        if (a.s <= DS_MAX && a.ncomp >= 64) {   // 32 components a warp
-            const size_t smem = sizeof(double) * 32 * (2 * a.s * a.s + (size_t)Mk * a.s);
+        const size_t smem_small = sizeof(double) * 32 * (2 * a.s * a.s + (size_t)Mk * a.s);
+        if (a.s <= DS_MAX && a.ncomp >= 64 && smem_small <= 160 * 1024) {   // 32 components a warp
+            const size_t smem = smem_small;
             if (smem > 48 * 1024)
                 CM_CUDA(cudaFuncSetAttribute(k_direct_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             const int64_t blocks = (a.ncomp + 31) / 32;
