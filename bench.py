@@ -695,7 +695,11 @@ def aggregate_profile(stats):
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, mean over the launches
 # of one solve of the 200000 x 100000 workload, one ncu capture) for the kernels whose code
 # has not changed since; None elsewhere.
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {
+    # k_jacobi_coop, first SVD of a solve (238 columns): 1.92 MB read + 0.58 MB written; the
+    # class's algorithmic bytes are its L2 traffic (the columns move through L2 every round)
+    ("block_permuted_200000x100000", "jacobi"): 2.50e6,
+}
 
 
 def roofline(dom, prof, stats, w):
