@@ -308,7 +308,9 @@ int cmsvd_gram_noalloc(cmsvd_context* ctx, int64_t n, int32_t c1, int32_t c2, co
  * Z n x c2 (ldz >= c2), all row-major FP64: the product that forms the orthonormal bases of the
  * rank truncation (Alg. 1 step 3) and the Ritz vectors (step 5). For n >= 16384 and
  * 32 <= c1 <= 1024, c2 >= 32 it follows the context's dense arithmetic
- * (cmsvd_context_set_dense_arith). 1 <= c1, c2 <= 4096.
+ * (cmsvd_context_set_dense_arith); with dense arithmetic 0, a product with c1 >= 128 and fewer
+ * 64 x 64 output tiles than the GPU has SMs runs on cuBLAS's FP64 GEMM, which splits the
+ * contraction over the GPU. Deterministic in every case. 1 <= c1, c2 <= 4096.
  */
 int cmsvd_gemm(cmsvd_context* ctx, int64_t n, int32_t c1, int32_t c2, const double* X, int64_t ldx,
                const double* W, int64_t ldw, double* Z, int64_t ldz);
